@@ -1,0 +1,254 @@
+"""Adaptive Partition Scanning and multi-level search (oracle; test infrastructure only).
+
+Follows Sec. 5 (geometric model Eq. 7, half-space caps, Eq. 8-9, Algorithm 1)
+and Sec. 3 ("Index Structure", top-down search).  Readings of the paper where
+it is silent or garbled (each applied identically, but independently, in the
+library):
+
+  R1  rho is the Euclidean (not squared) distance from q to the current k-th
+      result.  For inner product it is the Euclidean distance from q to that
+      result's vector, ||q - x_k||.
+  R2  t_i, the distance from q to the bisector of c_0 and c_i, is
+      (D_i - D_0) / (2 ||c_i - c_0||) for L2 with D = squared distance, and
+      (D_i - D_0) / ||c_i - c_0|| for inner product with D = -<q, c>
+      (the bisector of the max-inner-product cells passes through the
+      origin).  Coincident centroids give t_i = 0.
+  R3  p_0 = prod_j (1 - u_j) over the raw cap fractions u_j; the remaining
+      mass 1 - p_0 is spread in proportion to the normalised v_i = u_i / sum u
+      (Eq. 8-9).  With sum u = 0, p_0 = 1 and every p_i = 0.
+  R4  Until R holds k results the estimator is not used: partitions are
+      scanned in centroid-distance order.  When R first holds k results, rho is
+      set and every p is computed.
+  R5  r = p_0 + sum of p_i over the scanned candidates i >= 1, always with the
+      current p values (the garbled update line of Algorithm 1 read as a sum
+      over scanned candidates).
+  R6  The next candidate is the unscanned one with the largest p_i; equal p_i
+      go to the nearer centroid (lower position in S).
+  R7  After each scan rho' is the new k-th distance; if |rho' - rho| > tau_rho
+      rho, rho <- rho' and all p (including p_0) are recomputed.
+  R8  The loop stops when r >= tau_R or S is exhausted.  nprobe counts the
+      scanned candidates (empty partitions included).  If S runs out before R
+      holds k results, r is reported as 1.
+  R9  |S| = M = ceil(f_M * N_l) computed in double precision, clamped to
+      [1, N_l].  Upper levels run APS with k' = M of the level below and the
+      fixed recall target (0.99 in Sec. 5); the k' results, sorted by
+      (distance, index), are the next level's S.
+  R10 Fixed-nprobe search (Faiss-IVF style, used for the plain-IVF workload)
+      scans the first nprobe candidates of S in centroid order.
+"""
+
+import math
+
+import numpy as np
+
+from .capvol import beta_table, cap_fraction, cap_fraction_table
+from .knn import L2, distances
+
+
+class Params:
+    """Search parameters (defaults from Sec. 5 and Sec. 8.1)."""
+
+    def __init__(self, k=10, recall_target=0.9, nprobe=0, f_M=(0.1, 0.25),
+                 tau_rho=0.01, upper_recall=0.99, beta_mode="table"):
+        self.k = k
+        self.recall_target = recall_target
+        self.nprobe = nprobe
+        self.f_M = tuple(f_M)
+        self.tau_rho = tau_rho
+        self.upper_recall = upper_recall
+        self.beta_mode = beta_mode
+
+
+def n_candidates(f, n):
+    """M = ceil(f * n) in double precision, clamped to [1, n] (R9)."""
+    return int(max(1, min(n, math.ceil(f * n))))
+
+
+def bisector_distances(D, C, metric):
+    """t_i for every candidate (R2); D[0] and C[0] belong to the nearest centroid."""
+    D = np.asarray(D, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64)
+    diff = C - C[0][None, :]
+    cd = np.sqrt((diff * diff).sum(axis=1))
+    num = D - D[0]
+    den = 2.0 * cd if metric == L2 else cd
+    t = np.zeros_like(D)
+    nz = den > 0.0
+    t[nz] = num[nz] / den[nz]
+    return np.maximum(t, 0.0)
+
+
+def probabilities(t, rho, d, mode="table", table=None):
+    """p_0..p_{M-1} from Eq. 8-9 with raw caps for p_0 (R3).  t[0] is unused."""
+    t = np.asarray(t, dtype=np.float64)
+    M = t.shape[0]
+    p = np.zeros(M)
+    if M == 1:
+        p[0] = 1.0
+        return p
+    if mode == "exact":
+        u = cap_fraction(t[1:], rho, d)
+    else:
+        u = cap_fraction_table(t[1:], rho, table)
+    p0 = float(np.prod(1.0 - u))
+    U = float(u.sum())
+    p[0] = p0
+    if U > 0.0:
+        p[1:] = (1.0 - p0) * (u / U)
+    return p
+
+
+class _TopK:
+    """The result set R of Algorithm 1: the k smallest (dist, id) pairs seen."""
+
+    def __init__(self, k):
+        self.k = k
+        self.dist = np.zeros(0)
+        self.ids = np.zeros(0, dtype=np.int64)
+        self.rows = np.zeros((0, 0))
+
+    def add(self, dist, ids, rows):
+        if dist.shape[0] == 0:
+            return
+        if self.rows.shape[0] == 0:
+            self.rows = np.zeros((0, rows.shape[1]))
+        dd = np.concatenate([self.dist, dist])
+        ii = np.concatenate([self.ids, ids])
+        rr = np.concatenate([self.rows, np.asarray(rows, np.float64)])
+        order = np.lexsort((ii, dd))[: self.k]
+        self.dist, self.ids, self.rows = dd[order], ii[order], rr[order]
+
+    def full(self):
+        return self.dist.shape[0] >= self.k
+
+
+def kth_radius(R, q, metric):
+    """rho from the current k-th result (R1)."""
+    if metric == L2:
+        return math.sqrt(max(R.dist[R.k - 1], 0.0))
+    diff = np.asarray(q, np.float64) - R.rows[R.k - 1]
+    return math.sqrt(float((diff * diff).sum()))
+
+
+def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
+              fixed_nprobe=0):
+    """Algorithm 1 on one level.
+
+    q        query vector
+    level    kmeans.Level whose partitions are scanned
+    cand     candidate partition indices S, nearest first (position 0 = c_0)
+    cand_D   their centroid distances D_i (same convention as the scan)
+    Returns a dict: dist, ids (R sorted), scanned (positions in scan order),
+    r (final estimate), trace (decision margins for parity checks).
+    """
+    q = np.asarray(q, dtype=np.float64)
+    M = len(cand)
+    R = _TopK(k)
+    scanned = np.zeros(M, dtype=bool)
+    order = []
+    trace = []
+
+    def scan(pos):
+        j = cand[pos]
+        rows = level.vectors[j]
+        R.add(distances(q, rows, metric), level.ids[j], rows)
+        scanned[pos] = True
+        order.append(pos)
+
+    if fixed_nprobe > 0:
+        for pos in range(min(fixed_nprobe, M)):
+            scan(pos)
+        return dict(dist=R.dist, ids=R.ids, scanned=order, r=float("nan"), trace=trace)
+
+    t = bisector_distances(cand_D, level.centroids[np.asarray(cand)], metric)
+
+    scan(0)
+    while not R.full() and not scanned.all():                       # R4
+        scan(int(np.argmin(scanned)))
+    if not R.full():
+        return dict(dist=R.dist, ids=R.ids, scanned=order, r=1.0, trace=trace)
+
+    rho = kth_radius(R, q, metric)
+    p = probabilities(t, rho, d, params.beta_mode, table)
+    r = p[0] + p[1:][scanned[1:]].sum()                                # R5
+    while True:
+        trace.append(("stop", len(order), r - tau_R))
+        if not (r < tau_R) or scanned.all():                          # R8
+            break
+        un = np.nonzero(~scanned)[0]
+        pu = p[un]
+        best = un[int(np.argmax(pu))]                                  # R6 (first max = nearest)
+        if un.shape[0] > 1:
+            s = np.sort(pu)[::-1]
+            gap = (s[0] - s[1]) / max(s[0], 1e-300)
+        else:
+            gap = float("inf")
+        trace.append(("choose", len(order), gap))
+        scan(int(best))
+        rho_new = kth_radius(R, q, metric)
+        dev = abs(rho_new - rho) - params.tau_rho * rho
+        trace.append(("recompute", len(order), dev / max(rho, 1e-300)))
+        if abs(rho_new - rho) > params.tau_rho * rho:                 # R7
+            rho = rho_new
+            p = probabilities(t, rho, d, params.beta_mode, table)
+        r = p[0] + p[1:][scanned[1:]].sum()
+    return dict(dist=R.dist, ids=R.ids, scanned=order, r=float(r), trace=trace)
+
+
+def root_candidates(q, top_level, f, metric):
+    """Score the single top partition (all centroids of the top level) and keep M."""
+    D = distances(q, top_level.centroids, metric)
+    idx = np.arange(D.shape[0], dtype=np.int64)
+    M = n_candidates(f, D.shape[0])
+    order = np.lexsort((idx, D))[:M]
+    return idx[order], D[order]
+
+
+def search(levels, Q, params, metric=L2):
+    """Top-down Quake search of every query (Sec. 3, Sec. 5).
+
+    levels[0] holds the base vectors; levels[1] (optional) holds the leaf
+    centroids grouped under parent centroids.  Returns a dict of arrays
+    dist (nq, k), ids (nq, k), nprobe (nq,), r (nq,), plus per-query lists
+    scanned[l] (partition indices per level, in scan order) and traces.
+    """
+    Q = np.atleast_2d(np.asarray(Q))
+    nq, d = Q.shape
+    k = params.k
+    table = beta_table(d) if params.beta_mode == "table" else None
+    L = len(levels)
+    out_D = np.full((nq, k), np.inf)
+    out_I = np.full((nq, k), -1, dtype=np.int64)
+    out_np = np.zeros(nq, dtype=np.int64)
+    out_r = np.zeros(nq)
+    scanned = [[None] * nq for _ in range(L)]
+    traces = [[None] * nq for _ in range(L)]
+    fixed = params.nprobe if params.recall_target <= 0 else 0
+    for j in range(nq):
+        q = Q[j]
+        top = levels[L - 1]
+        if L == 1:
+            if fixed:                                                    # R10
+                cand, cD = root_candidates(q, top, 1.0, metric)
+                cand, cD = cand[:fixed], cD[:fixed]
+            else:
+                cand, cD = root_candidates(q, top, params.f_M[0], metric)
+        else:
+            cand1, cD1 = root_candidates(q, top, params.f_M[1], metric)
+            k1 = n_candidates(params.f_M[0], levels[0].n_part)
+            res1 = aps_level(q, levels[1], list(cand1), cD1, k1, params.upper_recall,
+                             params, d, metric, table)
+            scanned[1][j] = [int(cand1[p]) for p in res1["scanned"]]
+            traces[1][j] = res1["trace"]
+            cand, cD = res1["ids"], res1["dist"]
+        res = aps_level(q, levels[0], list(cand), cD, k, params.recall_target,
+                        params, d, metric, table, fixed_nprobe=fixed)
+        n = res["ids"].shape[0]
+        out_D[j, :n] = res["dist"]
+        out_I[j, :n] = res["ids"]
+        out_np[j] = len(res["scanned"])
+        out_r[j] = res["r"]
+        scanned[0][j] = [int(cand[p]) for p in res["scanned"]]
+        traces[0][j] = res["trace"]
+    return dict(dist=out_D, ids=out_I, nprobe=out_np, r=out_r, scanned=scanned,
+                traces=traces)

@@ -1,0 +1,116 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws random numbers; it holds none of the method's
+arithmetic, so both the CUDA library's tests and the CPU oracle can take their
+inputs from it.  Every generator uses numpy's PCG64 with an explicit seed.
+
+Workload shapes (the paper's datasets are not available; these stand in):
+  plain IVF      10,000 x 64 from a 50-component isotropic Gaussian mixture,
+                 centres ~ N(0, I), sigma 0.2; 100 queries from the mixture.
+  APS search     1,000,000 x 128 from a 1,000-component mixture (Sift1M-like
+                 scale), 10,000 queries whose component is drawn Zipf(1.1).
+  batching       5,000,000 x 256 in 20,000 components with Zipf(1.0) sizes
+                 clipped to [10, 100,000]; each query has its own nprobe.
+"""
+
+import numpy as np
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def mixture_centers(n_comp, d, seed):
+    """Component centres ~ N(0, I)."""
+    return rng(seed).standard_normal((n_comp, d)).astype(np.float32)
+
+
+def mixture_samples(centers, n, sigma, seed, labels=None, chunk=1 << 18):
+    """n rows = centre[label] + sigma * N(0, I); labels uniform unless given."""
+    g = rng(seed)
+    n_comp, d = centers.shape
+    if labels is None:
+        labels = g.integers(0, n_comp, size=n)
+    X = np.empty((n, d), dtype=np.float32)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        X[s:e] = centers[labels[s:e]] + np.float32(sigma) * g.standard_normal((e - s, d), dtype=np.float32)
+    return X, labels
+
+
+def zipf_labels(n_comp, n, a, seed):
+    """Component per sample with P(rank r) ~ r^-a over a seeded permutation of components."""
+    g = rng(seed)
+    w = np.arange(1, n_comp + 1, dtype=np.float64) ** (-a)
+    w /= w.sum()
+    perm = g.permutation(n_comp)
+    ranks = g.choice(n_comp, size=n, p=w)
+    return perm[ranks]
+
+
+def zipf_sizes(n_part, total, a, lo, hi):
+    """Partition sizes ~ r^-a, clipped to [lo, hi] and rescaled to sum to `total`."""
+    w = np.arange(1, n_part + 1, dtype=np.float64) ** (-a)
+    s = w / w.sum() * total
+    for _ in range(100):
+        s = np.clip(s, lo, hi)
+        free = (s > lo) & (s < hi)
+        deficit = total - s.sum()
+        if abs(deficit) < 0.5 or not free.any():
+            break
+        s[free] *= 1.0 + deficit / s[free].sum()
+    s = np.clip(np.floor(s).astype(np.int64), lo, hi)
+    i = 0
+    while s.sum() < total:
+        if s[i % n_part] < hi:
+            s[i % n_part] += 1
+        i += 1
+    while s.sum() > total:
+        if s[i % n_part] > lo:
+            s[i % n_part] -= 1
+        i += 1
+    return s
+
+
+def unit_rows(X):
+    n = np.linalg.norm(X, axis=1, keepdims=True)
+    n[n == 0] = 1
+    return (X / n).astype(np.float32)
+
+
+# ----------------------------------------------------------------- workloads
+
+def plain_ivf(seed=1235, n=10_000, d=64, n_comp=50, sigma=0.2, nq=100):
+    """Single-level plain IVF workload (10k x 64, 50 components, sigma 0.2)."""
+    C = mixture_centers(n_comp, d, seed)
+    X, _ = mixture_samples(C, n, sigma, seed + 1)
+    Q, _ = mixture_samples(C, nq, sigma, seed + 2)
+    return X, np.arange(n, dtype=np.int64), Q
+
+
+def aps_search(seed=1236, n=1_000_000, d=128, n_comp=1000, sigma=1.0, nq=10_000, zipf=1.1):
+    """Two-level APS workload (1M x 128, 1,000 components, Zipf(1.1) queries)."""
+    C = mixture_centers(n_comp, d, seed)
+    X, _ = mixture_samples(C, n, sigma, seed + 1)
+    lab = zipf_labels(n_comp, nq, zipf, seed + 2)
+    Q, _ = mixture_samples(C, nq, sigma, seed + 3, labels=lab)
+    return X, np.arange(n, dtype=np.int64), Q
+
+
+def zipf_partitions(seed=1238, n=5_000_000, d=256, n_part=20_000, a=1.0, lo=10, hi=100_000,
+                    spread=0.3, nq=4096, nprobe_lo=1, nprobe_hi=500):
+    """Batching workload: rows grouped in Zipf-sized components, per-query nprobe.
+
+    Returns X, ids, labels (the component of each row, which is its partition),
+    queries, and one log-uniform nprobe per query.
+    """
+    sizes = zipf_sizes(n_part, n, a, lo, hi)
+    C = mixture_centers(n_part, d, seed)
+    lab = np.repeat(np.arange(n_part, dtype=np.int64), sizes)
+    X, _ = mixture_samples(C, n, spread, seed + 1, labels=lab)
+    g = rng(seed + 2)
+    qlab = g.integers(0, n_part, size=nq)
+    Q, _ = mixture_samples(C, nq, spread, seed + 3, labels=qlab)
+    u = g.uniform(np.log(nprobe_lo), np.log(nprobe_hi + 1), size=nq)
+    nprobe = np.clip(np.floor(np.exp(u)).astype(np.int32), nprobe_lo, nprobe_hi)
+    return X, np.arange(n, dtype=np.int64), lab, Q, nprobe
