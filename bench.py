@@ -1,0 +1,323 @@
+"""Benchmark of the query-time hot path: APS search over a two-level index.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (seeded, synthetic): 1,000,000 x 128 FP32 vectors from a 1,000-component
+Gaussian mixture, a two-level index (1,000 leaf partitions under 32 parents,
+10 Lloyd iterations), 10,000 queries per step whose component is Zipf(1.1),
+L2, k = 10, APS with recall target 0.9 (raised in steps of 0.01 until mean
+recall@10 against an FP64 brute force reaches 0.9).  One step = one search of
+the 10,000 queries: root scoring, APS at both levels and the fused scan, all in
+the library's kernels.  The arena (640 MB) is larger than L2, so no flush is
+needed between steps.
+
+With N > 1 (torchrun) every rank holds a replica of the index and searches its
+own 10,000 queries: weak scaling, no collective on the data path.
+
+--impl reference times the CPU oracle (FP64 numpy) on a bounded sample of the
+same workload on the host cores.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2506_03437_b300 import synth  # noqa: E402
+
+D, SIGMA, K = 128, 1.0, 10
+ITERS, SEED = 10, 1234
+N, N_COMP, NQ, N_LEAF, N_PARENT = 1_000_000, 1000, 10_000, 1000, 32   # set from the flags in main()
+F_M_LEAF, F_M_PARENT = 0.1, 0.25
+METRIC = "QPS at recall@10>=0.9 vs FP64 brute force (APS, two-level index)"
+WORKLOAD = "aps_search_1Mx128_1000leaf_32parent_10kq_zipf1.1_k10"
+ORACLE_BUILD_ITERS = 3   # Lloyd iterations of the index the CPU-baseline leg searches
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def gt_fp64(torch, Xd, Qd, k, chunk=512):
+    """Exact top-k by FP64 brute force on the device (evaluation only)."""
+    X64 = Xd.double()
+    xn = (X64 * X64).sum(1)
+    outD = torch.empty((Qd.shape[0], k), dtype=torch.float64, device=Xd.device)
+    for s in range(0, Qd.shape[0], chunk):
+        Q64 = Qd[s:s + chunk].double()
+        Dm = (Q64 * Q64).sum(1, keepdim=True) - 2.0 * (Q64 @ X64.T) + xn[None, :]
+        v, _ = torch.topk(Dm, k, dim=1, largest=False, sorted=True)
+        outD[s:s + chunk] = v
+        del Dm
+    return outD, X64
+
+
+def recall(torch, X64, Qd, ids, gtD, k, rtol=1e-5):
+    """Recall@k with distance ties counted (a returned id within the k-th GT distance)."""
+    Q64 = Qd.double()
+    ok = ids >= 0
+    rows = X64[ids.clamp(min=0)]
+    dist = ((rows - Q64[:, None, :]) ** 2).sum(-1)
+    kth = gtD[:, k - 1]
+    thr = kth + rtol * kth.abs() + rtol
+    hit = ok & (dist <= thr[:, None])
+    return (hit.sum(1).double() / k).mean().item()
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2506_03437_b300 import index as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    X, ids, Q = synth.aps_search(n=N, d=D, n_comp=N_COMP, sigma=SIGMA, nq=NQ)
+    if rank > 0:   # each rank searches its own queries from the same mixture
+        Q = synth.aps_queries(1236, D, N_COMP, SIGMA, NQ, stream=rank)
+    Xd = torch.from_numpy(X).to(dev)
+    idd = torch.from_numpy(ids).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    ix = I.Index(D, n_leaf=N_LEAF, n_parent=N_PARENT, kmeans_iters=ITERS, seed=SEED,
+                 f_M_leaf=F_M_LEAF, f_M_parent=F_M_PARENT)
+    t0 = time.time()
+    ix.build(Xd, idd)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+
+    gtD, X64 = gt_fp64(torch, Xd, Qd, K)
+    stream = torch.cuda.current_stream()
+
+    # recall target: 0.9, raised by 0.01 until mean recall@10 >= 0.9
+    tau = 0.90
+    while True:
+        oi, od, on, orr = ix.search(Qd, K, recall_target=tau, stream=stream)
+        ix.check(stream)
+        bad = int(((oi < -1) | (oi >= N)).sum().item())
+        if bad:
+            raise RuntimeError(f"search returned {bad} out-of-range ids")
+        rec = recall(torch, X64, Qd, oi, gtD, K)
+        if rec >= 0.9 or tau >= 0.999:
+            break
+        tau = round(tau + 0.01, 2)
+    mean_nprobe = on.double().mean().item()
+    del X64
+
+    sizes0, _, _ = ix.export_level(0)
+    sizes1, _, _ = ix.export_level(1)
+    out = (oi, od, on, orr)
+    for _ in range(args.warmup):
+        ix.search(Qd, K, recall_target=tau, out=out, stream=stream)
+    torch.cuda.synchronize()
+    ix.hits(0, reset=True)
+    ix.hits(1, reset=True)
+    peak, peak_kind = peaks()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            ix.search(Qd, K, recall_target=tau, out=out, stream=stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ix.check(stream)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(launch_ms) / 1e3
+    if world > 1:
+        dist.barrier()
+    h0 = ix.hits(0)
+    h1 = ix.hits(1)
+    # algorithmic bytes: every (query, partition) item reads the partition's rows once,
+    # plus the top partition (32 parent centroids) per query
+    bytes_total = (float((h0 * sizes0).sum()) + float((h1 * sizes1).sum())) * D * 4 + args.steps * NQ * N_PARENT * D * 4
+    bytes_per_launch = bytes_total / args.steps
+    avg_launch_s = dev_s / args.steps
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    Qh = torch.from_numpy(Q).pin_memory()
+    oh = (torch.empty((NQ, K), dtype=torch.int64).pin_memory(), torch.empty((NQ, K), dtype=torch.float32).pin_memory(),
+          torch.empty(NQ, dtype=torch.int32).pin_memory(), torch.empty(NQ, dtype=torch.float32).pin_memory())
+    ix.search(Qh, K, recall_target=tau, out=oh, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ix.search(Qh, K, recall_target=tau, out=oh, stream=stream)
+    e2e_s = time.perf_counter() - t0
+
+    t = torch.tensor([dev_s, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_s, e2e_s = t.tolist()
+    qps = world * NQ * args.steps / dev_s
+    e2e_qps = world * NQ * args.steps / e2e_s
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(qps, 1), "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dev_s / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Gaussian mixture; stands in for Sift1M-shaped data)",
+            "config": {"workload": WORKLOAD, "n": N, "d": D, "n_leaf": N_LEAF, "n_parent": N_PARENT,
+                       "queries_per_step": NQ, "k": K, "recall_target": tau, "recall_at_10": round(rec, 4),
+                       "mean_nprobe": round(mean_nprobe, 2), "f_M": [F_M_LEAF, F_M_PARENT],
+                       "tau_rho": 0.01, "upper_recall": 0.99, "beta": "table", "build_s": round(build_s, 2),
+                       "l2": "no flush: 640 MB arena > 126 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": round(e2e_qps, 1), "unit": "queries/s",
+                    "h2d_bytes_per_step": NQ * D * 4,
+                    "d2h_bytes_per_step": NQ * K * (8 + 4) + NQ * 8},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_kind": peak_kind,
+                         "note": "achieved = per-(query, partition) scan bytes / aps_search_kernel time"},
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(X, ids, Q, tau, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def oracle_index(X, ids):
+    from oracle import kmeans
+    return kmeans.build_index(X, ids, N_LEAF, N_PARENT, iters=ORACLE_BUILD_ITERS, seed=SEED)
+
+
+def cpu_baseline(X, ids, Q, tau, seconds, levels=None):
+    """The oracle's APS search timed on a bounded sample of the same queries (1 host thread)."""
+    from oracle import aps
+    if levels is None:
+        levels = oracle_index(X, ids)
+    prm = aps.Params(k=K, recall_target=tau, f_M=(F_M_LEAF, F_M_PARENT))
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds and done < Q.shape[0]:
+        aps.search(levels, Q[done:done + 1], prm)
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": round(done / el, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": (f"first {done} of {Q.shape[0]} queries, FP64 numpy APS search on 1 thread, over an index "
+                       f"the oracle built itself ({ORACLE_BUILD_ITERS} Lloyd iterations)")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    X, ids, Q = synth.aps_search(n=N, d=D, n_comp=N_COMP, sigma=SIGMA, nq=NQ)
+    levels = oracle_index(X, ids)
+    from oracle import aps
+    prm = aps.Params(k=K, recall_target=0.9, f_M=(F_M_LEAF, F_M_PARENT))
+    per_step = max(1, args.ref_queries)
+    for w in range(args.warmup):
+        aps.search(levels, Q[:1], prm)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        lo = (s * per_step) % NQ
+        aps.search(levels, Q[lo:lo + per_step], prm)
+    el = time.perf_counter() - t0
+    qps = per_step * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": round(qps, 3), "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Gaussian mixture)",
+            "config": {"workload": WORKLOAD, "n": N, "d": D, "n_leaf": N_LEAF, "n_parent": N_PARENT,
+                       "queries_per_step": per_step, "k": K, "recall_target": 0.9},
+            "cpu_baseline": {"value": round(qps, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} queries per step of the {NQ}-query batch"},
+            "e2e": {"value": round(qps, 3), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-queries", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=1_000_000, help="vectors (smaller for profiling runs)")
+    ap.add_argument("--nq", type=int, default=10_000, help="queries per step")
+    ap.add_argument("--leaves", type=int, default=1000)
+    ap.add_argument("--parents", type=int, default=32)
+    args = ap.parse_args()
+    global N, N_COMP, NQ, N_LEAF, N_PARENT, WORKLOAD
+    N, NQ, N_LEAF, N_PARENT = args.n, args.nq, args.leaves, args.parents
+    N_COMP = max(1, N // 1000)
+    if (N, NQ, N_LEAF, N_PARENT) != (1_000_000, 10_000, 1000, 32):
+        WORKLOAD = f"aps_search_{N}x128_{N_LEAF}leaf_{N_PARENT}parent_{NQ}q_zipf1.1_k10"
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

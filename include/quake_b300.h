@@ -1,0 +1,195 @@
+/*
+ * quake_b300.h -- C ABI of a single-GPU (B300, sm_103a) implementation of the
+ * query-time hot path of Quake's adaptive partitioned vector index
+ * (Mohoney et al., "Quake: Adaptive Indexing for Vector Search", OSDI'25).
+ *
+ * Conventions shared by every entry point
+ *  - Every buffer argument may be a host or a device pointer; the library asks
+ *    the CUDA driver which one it is.  Host buffers are copied in and out inside
+ *    the call, which then returns only once the results are in host memory.
+ *    With device buffers the call is stream-ordered on `stream` (a
+ *    cudaStream_t; NULL = the legacy default stream) and may return before the
+ *    GPU has finished.
+ *  - The caller owns every buffer it passes; the index owns all of its device
+ *    state and frees it in qk_destroy.
+ *  - Vectors are row-major FP32, `d` values per row.  Ids are int64.
+ *  - Distances: metric L2 reports the squared Euclidean distance; metric IP
+ *    reports the NEGATED inner product, so smaller is nearer for both.  Results
+ *    are ordered by (distance, id) ascending.  Unfilled result slots hold
+ *    id = -1 and distance = +inf.
+ *  - Supported dimensions: 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024.
+ *  - No C++ exception crosses the ABI.  A failing call returns a non-zero
+ *    qk_status and leaves a message for qk_last_error() (thread-local).
+ *  - Calls on one index are not thread-safe; use one index per host thread or
+ *    serialise the calls.
+ */
+#ifndef QUAKE_B300_H
+#define QUAKE_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qk_index qk_index;
+
+typedef enum {
+  QK_OK = 0,
+  QK_ERR_ARG = 1,         /* invalid argument (sizes, pointers, NaN input, unsupported d) */
+  QK_ERR_OOM = 2,         /* device memory exhausted */
+  QK_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  QK_ERR_TIMEOUT = 4,     /* a bounded device wait expired; results are not valid */
+  QK_ERR_DUP_ID = 5,      /* insert of an id that is already present; nothing applied */
+  QK_ERR_STATE = 6,       /* call not valid in the index's current state (e.g. search before build) */
+  QK_ERR_UNSUPPORTED = 7, /* configuration not supported by this build */
+  QK_ERR_INTERNAL = 8     /* a kernel's own consistency check failed; results are not valid */
+} qk_status;
+
+enum { QK_METRIC_L2 = 0, QK_METRIC_IP = 1 };
+enum { QK_BETA_TABLE = 0, QK_BETA_EXACT = 1 };
+
+/*
+ * Index configuration.  Paper parameters (Sec. 3, Sec. 5, Sec. 8.1):
+ *   n_leaf, n_parent   partitions at level 0 and level 1 (n_parent = 0: one level).
+ *   f_M_leaf, f_M_parent  initial candidate fractions f_M (Algorithm 1): the
+ *                      search keeps M = ceil(f_M * N_l) candidates, computed in
+ *                      double precision and clamped to [1, N_l].
+ *   tau_rho            recompute threshold of Algorithm 1 (paper: 1%).
+ *   upper_recall       fixed recall target of the upper level (paper: 99%).
+ *   beta_mode          QK_BETA_TABLE: regularised incomplete beta from a
+ *                      1024-point table at x_j = j/1023 with linear
+ *                      interpolation (Sec. 5, "Performance Optimizations");
+ *                      QK_BETA_EXACT: evaluated per candidate.
+ *   kmeans_iters, seed Lloyd iterations and the SplitMix64 seed of the build.
+ */
+typedef struct {
+  int32_t d;
+  int32_t metric;
+  int32_t n_leaf;
+  int32_t n_parent;
+  int32_t kmeans_iters;
+  int32_t beta_mode;
+  uint64_t seed;
+  double f_M_leaf;
+  double f_M_parent;
+  double tau_rho;
+  double upper_recall;
+} qk_config;
+
+/* Fills `cfg` with the paper's defaults: L2, one level, f_M = 0.1 / 0.25,
+ * tau_rho = 0.01, upper_recall = 0.99, table mode, 10 Lloyd iterations. */
+void qk_config_default(qk_config* cfg);
+
+/* Creates an empty index on the current CUDA device.  Errors: QK_ERR_ARG for
+ * an unsupported d or metric, QK_ERR_CUDA / QK_ERR_OOM. */
+qk_status qk_create(const qk_config* cfg, qk_index** out);
+
+/* Frees all device and host state of the index.  NULL is accepted. */
+void qk_destroy(qk_index* index);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* qk_last_error(void);
+
+/*
+ * Builds the index from n vectors x (n x d) with ids (Sec. 3, "Index
+ * Structure"): Lloyd k-means into n_leaf partitions (seeded rows chosen by a
+ * SplitMix64 partial Fisher-Yates shuffle; assignment to the nearest
+ * centroid with ties to the lower index; FP64 member means rounded to FP32;
+ * empty clusters keep their centroid), then, if n_parent > 0, k-means of the
+ * leaf centroids into n_parent parents.  Every row is finally placed in the
+ * partition of its nearest final centroid.  Ids must be unique (QK_ERR_DUP_ID).
+ * Synchronous: returns after the index is ready.
+ */
+qk_status qk_build(qk_index* index, const float* x, const int64_t* ids, int64_t n, void* stream);
+
+/*
+ * Installs a given partitioning instead of clustering: leaf_centroids
+ * (n_leaf x d), leaf_of_row[n] in [0, n_leaf); for two levels also
+ * parent_centroids (n_parent x d) and parent_of_leaf[n_leaf] in [0, n_parent)
+ * (both NULL / 0 for one level).  The counts must match the configuration.
+ * Synchronous.
+ */
+qk_status qk_load(qk_index* index, const float* x, const int64_t* ids, int64_t n,
+                  const float* leaf_centroids, const int32_t* leaf_of_row,
+                  const float* parent_centroids, const int32_t* parent_of_leaf, void* stream);
+
+/*
+ * Searches nq queries q (nq x d) for their k nearest neighbours (k <= 1024).
+ *
+ * recall_target > 0: Adaptive Partition Scanning (Sec. 5, Eq. 7-9, Algorithm 1)
+ *   at every level.  The top partition (all centroids of the top level) is
+ *   scored and the M = ceil(f_M * N) nearest kept; an upper level runs APS with
+ *   k' = M of the level below and `upper_recall`; the leaf level runs APS with
+ *   k and recall_target.  Per query, partitions are scanned nearest first until
+ *   k results are held, then in decreasing p_i; p is recomputed when the k-th
+ *   distance rho moves by more than tau_rho * rho; the scan stops when the
+ *   estimate r = p_0 + sum of the scanned p_i reaches the target or the
+ *   candidates run out.
+ * recall_target <= 0: fixed nprobe (Faiss-IVF style): the nprobe nearest leaf
+ *   partitions are scanned (found through the upper level when there is one).
+ *
+ * Outputs (nq x k, row-major): out_ids, out_dist.  Optional (NULL to skip):
+ * out_nprobe[nq] leaf partitions scanned, out_recall[nq] the final estimate r
+ * (NaN in fixed-nprobe mode).  Per-partition access counts are accumulated in
+ * the index (see qk_get_hits).  NaN in q -> QK_ERR_ARG.
+ */
+qk_status qk_search(qk_index* index, const float* q, int64_t nq, int32_t k, float recall_target,
+                    int32_t nprobe, int64_t* out_ids, float* out_dist, int32_t* out_nprobe,
+                    float* out_recall, void* stream);
+
+/*
+ * Waits for the index's work on `stream` and reports what its kernels found:
+ * QK_ERR_TIMEOUT if a bounded device wait expired, QK_ERR_INTERNAL if a
+ * kernel's consistency check failed (details in qk_last_error), QK_OK
+ * otherwise.  Clears the device status.  Calls with host buffers do this
+ * themselves; calls with device buffers return before the kernels finish, so
+ * their callers use qk_check to learn the outcome.
+ */
+qk_status qk_check(qk_index* index, void* stream);
+
+/* Index shape.  Any output pointer may be NULL. */
+qk_status qk_info(const qk_index* index, int64_t* n_vectors, int32_t* n_leaf, int32_t* n_parent,
+                  int32_t* d);
+
+/*
+ * Copies the structure of one level to host arrays for inspection:
+ * level 0: sizes[n_leaf], centroids (n_leaf x d), and, if not NULL,
+ *   ids[n_vectors] grouped by partition in partition order;
+ * level 1: sizes[n_parent], centroids (n_parent x d), ids[n_leaf] = leaf
+ *   indices grouped by parent.
+ * All outputs are host pointers; any may be NULL.
+ */
+qk_status qk_export_level(const qk_index* index, int32_t level, int32_t* sizes, float* centroids,
+                          int64_t* ids);
+
+/* Copies the access counts of `level` (one int64 per partition, summed over
+ * searches since the last reset) to a host array; reset != 0 zeroes them. */
+qk_status qk_get_hits(qk_index* index, int32_t level, int64_t* hits, int32_t reset);
+
+/*
+ * Exact cap volume fraction u = 1/2 I_x((d+1)/2, 1/2), x = 1 - (t/rho)^2 for
+ * t < rho and 0 otherwise (Sec. 5, "Intersection Volume Approximation", after
+ * Li 2010), evaluated in FP64 on the GPU with the library's continued fraction
+ * (mode QK_BETA_EXACT) or its 1024-point table (QK_BETA_TABLE), for n pairs
+ * (t[i], rho[i]).  Exposed so the estimator's arithmetic can be checked.
+ */
+qk_status qk_cap_fraction(int32_t d, int32_t mode, const double* t, const double* rho, int64_t n,
+                          double* out_u, void* stream);
+
+/*
+ * One Lloyd step on the GPU (Sec. 3; k-means as in qk_build): assigns each of
+ * the n rows of x to the nearest of the K centroids c (ties to the lower
+ * index) and returns the FP64 member means rounded to FP32 in c_new (empty
+ * clusters keep c), the assignment in assign[n] and the member counts in
+ * counts[K].  c_new, assign and counts may be NULL.
+ */
+qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, int32_t K,
+                         float* c_new, int32_t* assign, int32_t* counts, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QUAKE_B300_H */

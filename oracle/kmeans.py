@@ -62,9 +62,10 @@ def assign(X, C, chunk=4096):
 def update(X, a, C_prev):
     """New centroids: FP64 member means rounded to FP32; empty clusters keep theirs."""
     K, d = C_prev.shape
-    X64 = np.asarray(X, dtype=np.float64)
-    sums = np.zeros((K, d), dtype=np.float64)
-    np.add.at(sums, a, X64)
+    X = np.asarray(X)
+    sums = np.empty((K, d), dtype=np.float64)
+    for j in range(d):   # per-dimension FP64 sums over the members, in row order
+        sums[:, j] = np.bincount(a, weights=X[:, j].astype(np.float64), minlength=K)
     counts = np.bincount(a, minlength=K)
     C = np.array(C_prev, dtype=np.float32, copy=True)
     nz = counts > 0

@@ -1,0 +1,96 @@
+"""ctypes binding of the C ABI in include/quake_b300.h (argument marshalling only).
+
+Every function here forwards to the CUDA library; nothing is computed in
+Python.  Arrays may be numpy arrays (host memory) or torch tensors (host or
+CUDA); they must be C-contiguous with the documented dtype.  If the library
+is missing the import fails: there is no fallback.
+"""
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libquake_b300.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DUP_ID, ERR_STATE, ERR_UNSUPPORTED, ERR_INTERNAL = range(9)
+METRIC_L2, METRIC_IP = 0, 1
+BETA_TABLE, BETA_EXACT = 0, 1
+
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
+                5: "ERR_DUP_ID", 6: "ERR_STATE", 7: "ERR_UNSUPPORTED", 8: "ERR_INTERNAL"}
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTS = [
+    "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load",
+    "qk_search", "qk_check", "qk_info", "qk_export_level", "qk_get_hits", "qk_cap_fraction",
+    "qk_kmeans_step",
+]
+
+
+class QkConfig(C.Structure):
+    _fields_ = [
+        ("d", C.c_int32), ("metric", C.c_int32), ("n_leaf", C.c_int32), ("n_parent", C.c_int32),
+        ("kmeans_iters", C.c_int32), ("beta_mode", C.c_int32), ("seed", C.c_uint64),
+        ("f_M_leaf", C.c_double), ("f_M_parent", C.c_double), ("tau_rho", C.c_double),
+        ("upper_recall", C.c_double),
+    ]
+
+
+class QkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_2506_03437_b300.build")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, i32, f32, f64 = C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_double
+    sig = {
+        "qk_config_default": (None, [C.POINTER(QkConfig)]),
+        "qk_create": (i32, [C.POINTER(QkConfig), C.POINTER(vp)]),
+        "qk_destroy": (None, [vp]),
+        "qk_last_error": (C.c_char_p, []),
+        "qk_build": (i32, [vp, vp, vp, i64, vp]),
+        "qk_load": (i32, [vp, vp, vp, i64, vp, vp, vp, vp, vp]),
+        "qk_search": (i32, [vp, vp, i64, i32, f32, i32, vp, vp, vp, vp, vp]),
+        "qk_check": (i32, [vp, vp]),
+        "qk_info": (i32, [vp, vp, vp, vp, vp]),
+        "qk_export_level": (i32, [vp, i32, vp, vp, vp]),
+        "qk_get_hits": (i32, [vp, i32, vp, i32]),
+        "qk_cap_fraction": (i32, [i32, i32, vp, vp, i64, vp, vp]),
+        "qk_kmeans_step": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def check(status):
+    if status != OK:
+        raise QkError(status, lib.qk_last_error().decode())
+
+
+def ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)

@@ -1,0 +1,696 @@
+// Host runtime of the index and the C-ABI entry points declared in
+// include/quake_b300.h.  The runtime owns the device arena, the per-level
+// partition tables and the id -> (partition, slot) map; every computation on
+// vectors runs in the kernels of search.cu, kmeans.cu and arena.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "capvol.cuh"
+#include "common.cuh"
+#include "index.cuh"
+
+namespace qk {
+
+qk_status launch_search(const SearchArgs& a, cudaStream_t stream);
+qk_status launch_beta_table(double a, double lnB, double* table, cudaStream_t stream);
+qk_status launch_cap_fraction(int mode, double a, double lnB, const double* table, const double* t,
+                              const double* rho, int64_t n, double* out, cudaStream_t stream);
+qk_status launch_kmeans_assign(const float* X, int64_t n, int d, const float* C, int K, int32_t* assign,
+                               float* best_dist, cudaStream_t s);
+qk_status launch_kmeans_update(const float* X, int64_t n, int d, const int32_t* assign, const float* C_prev, int K,
+                               float* C_new, double* sums, int32_t* counts, cudaStream_t s);
+qk_status launch_gather_rows(const float* X, int d, const int64_t* rows, int K, float* out, cudaStream_t s);
+qk_status launch_histogram(const int32_t* lab, int64_t n, int32_t K, int32_t* counts, int32_t* status,
+                           cudaStream_t s);
+qk_status launch_scatter(const float* X, const int64_t* ids, int64_t n, int d, const int32_t* lab,
+                         const int64_t* off, int32_t* cursor, float* vec, int64_t* ids_out, cudaStream_t s);
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+qk_status cuda_status(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return QK_ERR_OOM;
+  }
+  return QK_ERR_CUDA;
+}
+
+static bool supported_dim(int d) {
+  switch (d) {
+    case 32: case 64: case 96: case 128: case 192: case 256: case 384: case 512: case 768: case 1024:
+      return true;
+    default:
+      return false;
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Temporary device buffer freed on scope exit (set-up paths only).
+struct Tmp {
+  void* p = nullptr;
+  Tmp() = default;
+  Tmp(const Tmp&) = delete;
+  ~Tmp() {
+    if (p) cudaFree(p);
+  }
+  template <class T>
+  qk_status alloc(size_t count, T** out) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    if (count == 0) count = 1;
+    QK_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    *out = static_cast<T*>(p);
+    return QK_OK;
+  }
+};
+
+template <class T>
+static qk_status in_device(const T* src, size_t count, Tmp& tmp, const T** out, cudaStream_t s) {
+  if (!src || is_device_ptr(src)) {
+    *out = src;
+    return QK_OK;
+  }
+  T* d = nullptr;
+  QK_TRY(tmp.alloc<T>(count, &d));
+  QK_CUDA(cudaMemcpyAsync(d, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  *out = d;
+  return QK_OK;
+}
+
+template <class T>
+static void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <class T>
+static qk_status dalloc(T** p, size_t count) {
+  dfree(*p);
+  if (count == 0) count = 1;
+  QK_CUDA(cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)));
+  return QK_OK;
+}
+
+static qk_status ensure(Buffer& b, size_t bytes) {
+  if (b.bytes >= bytes) return QK_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  size_t want = std::max<size_t>(bytes, 1 << 20);
+  QK_CUDA(cudaMalloc(&b.p, want));
+  b.bytes = want;
+  return QK_OK;
+}
+
+static int32_t n_candidates(double f, int32_t n) {
+  double m = std::ceil(f * (double)n);
+  if (m < 1) m = 1;
+  if (m > n) m = n;
+  return (int32_t)m;
+}
+
+// Rows reserved per partition: its size plus room for inserts.
+static int64_t capacity_for(int64_t size) { return size + std::max<int64_t>(16, size / 4); }
+
+static void free_structure(qk_index* ix) {
+  dfree(ix->vec0);
+  dfree(ix->ids0);
+  dfree(ix->off0);
+  dfree(ix->size0);
+  dfree(ix->cent0);
+  dfree(ix->vec1);
+  dfree(ix->ids1);
+  dfree(ix->off1);
+  dfree(ix->size1);
+  dfree(ix->cent1);
+  dfree(ix->hits0);
+  dfree(ix->hits1);
+  ix->ready = false;
+  ix->where.clear();
+}
+
+// Groups `rows` (n x d, device) by label into a fresh arena.  Returns the
+// arena, its partition offsets/sizes on host and device.
+static qk_status group_rows(const float* rows, const int64_t* ids, int64_t n, int d, const int32_t* lab,
+                            int32_t K, bool slack, int32_t* status, float** vec, int64_t** ids_out,
+                            int64_t** off, int32_t** size, std::vector<int64_t>& h_off,
+                            std::vector<int32_t>& h_size, std::vector<int64_t>* h_cap, int64_t* cap_rows,
+                            cudaStream_t s) {
+  Tmp tc;
+  int32_t* counts = nullptr;
+  QK_TRY(tc.alloc<int32_t>(K, &counts));
+  QK_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * K, s));
+  QK_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+  QK_TRY(launch_histogram(lab, n, K, counts, status, s));
+  h_size.assign(K, 0);
+  int32_t st = 0;
+  QK_CUDA(cudaMemcpyAsync(h_size.data(), counts, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s));
+  QK_CUDA(cudaMemcpyAsync(&st, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  if (st != 0) {
+    set_error("partition label out of range");
+    return QK_ERR_ARG;
+  }
+  h_off.assign(K, 0);
+  if (h_cap) h_cap->assign(K, 0);
+  int64_t o = 0;
+  for (int32_t j = 0; j < K; ++j) {
+    h_off[j] = o;
+    int64_t c = slack ? capacity_for(h_size[j]) : h_size[j];
+    if (h_cap) (*h_cap)[j] = c;
+    o += c;
+  }
+  *cap_rows = o;
+  QK_TRY(dalloc(vec, (size_t)o * d));
+  QK_TRY(dalloc(ids_out, (size_t)o));
+  QK_TRY(dalloc(off, (size_t)K));
+  QK_TRY(dalloc(size, (size_t)K));
+  QK_CUDA(cudaMemcpyAsync(*off, h_off.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, s));
+  QK_CUDA(cudaMemcpyAsync(*size, h_size.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
+  QK_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * K, s));
+  QK_TRY(launch_scatter(rows, ids, n, d, lab, *off, counts, *vec, *ids_out, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  return QK_OK;
+}
+
+// Installs a partitioning given by device arrays (the common end of build and load).
+static qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, const float* C0,
+                         const int32_t* leaf_of_row, const float* C1, const int32_t* parent_of_leaf,
+                         cudaStream_t s) {
+  const int d = ix->cfg.d;
+  const int32_t N0 = ix->cfg.n_leaf, N1 = ix->cfg.n_parent;
+  free_structure(ix);
+  QK_TRY(group_rows(X, ids, n, d, leaf_of_row, N0, true, ix->status, &ix->vec0, &ix->ids0, &ix->off0,
+                    &ix->size0, ix->h_off0, ix->h_size0, &ix->h_cap_part0, &ix->cap0, s));
+  QK_TRY(dalloc(&ix->cent0, (size_t)N0 * d));
+  QK_CUDA(cudaMemcpyAsync(ix->cent0, C0, sizeof(float) * (size_t)N0 * d, cudaMemcpyDeviceToDevice, s));
+  QK_TRY(dalloc(&ix->hits0, (size_t)N0));
+  QK_CUDA(cudaMemsetAsync(ix->hits0, 0, sizeof(unsigned long long) * N0, s));
+  if (N1 > 0) {
+    Tmp tl;
+    int64_t* leaf_ids = nullptr;
+    QK_TRY(tl.alloc<int64_t>(N0, &leaf_ids));
+    std::vector<int64_t> seq(N0);
+    for (int32_t j = 0; j < N0; ++j) seq[j] = j;
+    QK_CUDA(cudaMemcpyAsync(leaf_ids, seq.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
+    int64_t cap1 = 0;
+    QK_TRY(group_rows(C0, leaf_ids, N0, d, parent_of_leaf, N1, false, ix->status, &ix->vec1, &ix->ids1,
+                      &ix->off1, &ix->size1, ix->h_off1, ix->h_size1, nullptr, &cap1, s));
+    QK_TRY(dalloc(&ix->cent1, (size_t)N1 * d));
+    QK_CUDA(cudaMemcpyAsync(ix->cent1, C1, sizeof(float) * (size_t)N1 * d, cudaMemcpyDeviceToDevice, s));
+    QK_TRY(dalloc(&ix->hits1, (size_t)N1));
+    QK_CUDA(cudaMemsetAsync(ix->hits1, 0, sizeof(unsigned long long) * N1, s));
+  }
+  // id map, built from the arena so that it records the real slots
+  std::vector<int64_t> h_ids((size_t)ix->cap0);
+  QK_CUDA(cudaMemcpyAsync(h_ids.data(), ix->ids0, sizeof(int64_t) * ix->cap0, cudaMemcpyDeviceToHost, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  ix->where.clear();
+  ix->where.reserve((size_t)n * 2);
+  for (int32_t j = 0; j < N0; ++j) {
+    for (int32_t t = 0; t < ix->h_size0[j]; ++t) {
+      int64_t id = h_ids[ix->h_off0[j] + t];
+      if (!ix->where.emplace(id, ((int64_t)j << 32) | (uint32_t)t).second) {
+        free_structure(ix);
+        set_error("duplicate id " + std::to_string(id));
+        return QK_ERR_DUP_ID;
+      }
+    }
+  }
+  ix->n = n;
+  ix->n_leaf = N0;
+  ix->n_parent = N1;
+  ix->ready = true;
+  return QK_OK;
+}
+
+// Seeded initial rows: partial Fisher-Yates driven by SplitMix64
+// (Steele, Lea, Flood 2014).
+static void splitmix_init_rows(int64_t n, int32_t K, uint64_t seed, std::vector<int64_t>& out) {
+  std::vector<int64_t> perm((size_t)n);
+  for (int64_t i = 0; i < n; ++i) perm[i] = i;
+  uint64_t state = seed;
+  for (int32_t i = 0; i < K; ++i) {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    int64_t j = i + (int64_t)(z % (uint64_t)(n - i));
+    std::swap(perm[i], perm[j]);
+  }
+  out.assign(perm.begin(), perm.begin() + K);
+}
+
+// Lloyd k-means of n device rows into K centroids (device, K x d) and the
+// final assignment (device, n).
+static qk_status kmeans(const float* X, int64_t n, int d, int32_t K, int iters, uint64_t seed, float* C,
+                        int32_t* assign, cudaStream_t s) {
+  std::vector<int64_t> init;
+  splitmix_init_rows(n, K, seed, init);
+  Tmp t_rows, t_c2, t_sums, t_counts;
+  int64_t* rows = nullptr;
+  float* C2 = nullptr;
+  double* sums = nullptr;
+  int32_t* counts = nullptr;
+  QK_TRY(t_rows.alloc<int64_t>(K, &rows));
+  QK_TRY(t_c2.alloc<float>((size_t)K * d, &C2));
+  QK_TRY(t_sums.alloc<double>((size_t)K * d, &sums));
+  QK_TRY(t_counts.alloc<int32_t>(K, &counts));
+  QK_CUDA(cudaMemcpyAsync(rows, init.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, s));
+  QK_TRY(launch_gather_rows(X, d, rows, K, C, s));
+  for (int it = 0; it < iters; ++it) {
+    QK_TRY(launch_kmeans_assign(X, n, d, C, K, assign, nullptr, s));
+    QK_TRY(launch_kmeans_update(X, n, d, assign, C, K, C2, sums, counts, s));
+    QK_CUDA(cudaMemcpyAsync(C, C2, sizeof(float) * (size_t)K * d, cudaMemcpyDeviceToDevice, s));
+  }
+  QK_TRY(launch_kmeans_assign(X, n, d, C, K, assign, nullptr, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  return QK_OK;
+}
+
+static qk_status check_ready(const qk_index* ix) {
+  if (!ix) {
+    set_error("null index");
+    return QK_ERR_ARG;
+  }
+  if (!ix->ready) {
+    set_error("index is empty: build or load it first");
+    return QK_ERR_STATE;
+  }
+  return QK_OK;
+}
+
+// Synchronises `s`, then reads and clears the device status word and the
+// diagnostic record of the index's kernels.
+static qk_status read_device_status(qk_index* ix, cudaStream_t s) {
+  int32_t st = 0;
+  int64_t dg[kDiagWords] = {0};
+  QK_CUDA(cudaStreamSynchronize(s));
+  QK_CUDA(cudaMemcpy(&st, ix->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (std::getenv("QK_DEBUG_WAITS")) {
+    int64_t w = 0;
+    QK_CUDA(cudaMemcpy(&w, ix->diag + 8, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    std::fprintf(stderr, "qk: longest bulk-copy wait %lld cycles\n", (long long)w);
+    QK_CUDA(cudaMemset(ix->diag + 8, 0, sizeof(int64_t)));
+  }
+  if (st == DEV_OK) return QK_OK;
+  QK_CUDA(cudaMemcpy(dg, ix->diag, sizeof(dg), cudaMemcpyDeviceToHost));
+  QK_CUDA(cudaMemset(ix->status, 0, sizeof(int32_t)));
+  QK_CUDA(cudaMemset(ix->diag, 0, sizeof(dg)));
+  std::string what = "device status " + std::to_string(st) + " (query " + std::to_string(dg[1]) + ", details " +
+                     std::to_string(dg[2]) + " " + std::to_string(dg[3]) + " " + std::to_string(dg[4]) + " " +
+                     std::to_string(dg[5]) + " " + std::to_string(dg[6]) + " " + std::to_string(dg[7]) + ")";
+  if (st == DEV_TIMEOUT) {
+    set_error("a bounded device wait expired: " + what);
+    return QK_ERR_TIMEOUT;
+  }
+  set_error("internal consistency check failed: " + what);
+  return QK_ERR_INTERNAL;
+}
+
+}  // namespace qk
+
+using namespace qk;
+
+extern "C" {
+
+void qk_config_default(qk_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->d = 128;
+  c->metric = QK_METRIC_L2;
+  c->n_leaf = 1000;
+  c->n_parent = 0;
+  c->kmeans_iters = 10;
+  c->beta_mode = QK_BETA_TABLE;
+  c->seed = 1234;
+  c->f_M_leaf = 0.1;
+  c->f_M_parent = 0.25;
+  c->tau_rho = 0.01;
+  c->upper_recall = 0.99;
+}
+
+const char* qk_last_error(void) { return g_err.c_str(); }
+
+qk_status qk_create(const qk_config* cfg, qk_index** out) {
+  if (!cfg || !out) {
+    set_error("null argument");
+    return QK_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!supported_dim(cfg->d)) {
+    set_error("unsupported dimension " + std::to_string(cfg->d));
+    return QK_ERR_ARG;
+  }
+  if (cfg->metric != QK_METRIC_L2 && cfg->metric != QK_METRIC_IP) {
+    set_error("unknown metric");
+    return QK_ERR_ARG;
+  }
+  if (cfg->n_leaf < 1 || cfg->n_parent < 0 || cfg->n_parent > cfg->n_leaf || cfg->kmeans_iters < 0 ||
+      !(cfg->f_M_leaf > 0) || !(cfg->f_M_parent > 0) || !(cfg->tau_rho >= 0) ||
+      (cfg->beta_mode != QK_BETA_TABLE && cfg->beta_mode != QK_BETA_EXACT)) {
+    set_error("invalid configuration");
+    return QK_ERR_ARG;
+  }
+  qk_index* ix = new qk_index();
+  ix->cfg = *cfg;
+  cudaGetDevice(&ix->device);
+  ix->beta_a = 0.5 * (cfg->d + 1);
+  ix->beta_lnB = std::lgamma(ix->beta_a) + std::lgamma(0.5) - std::lgamma(ix->beta_a + 0.5);
+  qk_status st = QK_OK;
+  if ((st = dalloc(&ix->beta_table, kBetaTablePoints)) != QK_OK || (st = dalloc(&ix->work, 1)) != QK_OK ||
+      (st = dalloc(&ix->status, 1)) != QK_OK || (st = dalloc(&ix->diag, kDiagWords)) != QK_OK) {
+    qk_destroy(ix);
+    return st;
+  }
+  cudaMemset(ix->status, 0, sizeof(int32_t));
+  cudaMemset(ix->diag, 0, sizeof(int64_t) * kDiagWords);
+  st = launch_beta_table(ix->beta_a, ix->beta_lnB, ix->beta_table, 0);
+  if (st == QK_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_status(e, "beta table");
+  }
+  if (st != QK_OK) {
+    qk_destroy(ix);
+    return st;
+  }
+  *out = ix;
+  return QK_OK;
+}
+
+void qk_destroy(qk_index* ix) {
+  if (!ix) return;
+  free_structure(ix);
+  dfree(ix->beta_table);
+  dfree(ix->work);
+  dfree(ix->status);
+  dfree(ix->diag);
+  if (ix->stage_in.p) cudaFree(ix->stage_in.p);
+  if (ix->stage_out.p) cudaFree(ix->stage_out.p);
+  delete ix;
+}
+
+qk_status qk_build(qk_index* ix, const float* x, const int64_t* ids, int64_t n, void* stream) {
+  if (!ix || !x || !ids || n < 1) {
+    set_error("null argument or empty input");
+    return QK_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = ix->cfg.d;
+  const int32_t N0 = ix->cfg.n_leaf, N1 = ix->cfg.n_parent;
+  if (n < N0) {
+    set_error("fewer vectors than leaf partitions");
+    return QK_ERR_ARG;
+  }
+  Tmp tx, ti, tc0, ta0, tc1, ta1;
+  const float* X = nullptr;
+  const int64_t* I = nullptr;
+  QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
+  QK_TRY(in_device(ids, (size_t)n, ti, &I, s));
+  float* C0 = nullptr;
+  int32_t* a0 = nullptr;
+  QK_TRY(tc0.alloc<float>((size_t)N0 * d, &C0));
+  QK_TRY(ta0.alloc<int32_t>((size_t)n, &a0));
+  QK_TRY(kmeans(X, n, d, N0, ix->cfg.kmeans_iters, ix->cfg.seed, C0, a0, s));
+  float* C1 = nullptr;
+  int32_t* a1 = nullptr;
+  if (N1 > 0) {
+    QK_TRY(tc1.alloc<float>((size_t)N1 * d, &C1));
+    QK_TRY(ta1.alloc<int32_t>((size_t)N0, &a1));
+    QK_TRY(kmeans(C0, N0, d, N1, ix->cfg.kmeans_iters, ix->cfg.seed + 1, C1, a1, s));
+  }
+  return install(ix, X, I, n, C0, a0, C1, a1, s);
+}
+
+qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, const float* leaf_centroids,
+                  const int32_t* leaf_of_row, const float* parent_centroids, const int32_t* parent_of_leaf,
+                  void* stream) {
+  if (!ix || !x || !ids || n < 0 || !leaf_centroids || !leaf_of_row) {
+    set_error("null argument");
+    return QK_ERR_ARG;
+  }
+  const int d = ix->cfg.d;
+  const int32_t N0 = ix->cfg.n_leaf, N1 = ix->cfg.n_parent;
+  if (N1 > 0 && (!parent_centroids || !parent_of_leaf)) {
+    set_error("two-level index needs parent centroids and parent_of_leaf");
+    return QK_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Tmp tx, ti, tc0, ta0, tc1, ta1;
+  const float *X = nullptr, *C0 = nullptr, *C1 = nullptr;
+  const int64_t* I = nullptr;
+  const int32_t *a0 = nullptr, *a1 = nullptr;
+  QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
+  QK_TRY(in_device(ids, (size_t)n, ti, &I, s));
+  QK_TRY(in_device(leaf_centroids, (size_t)N0 * d, tc0, &C0, s));
+  QK_TRY(in_device(leaf_of_row, (size_t)n, ta0, &a0, s));
+  if (N1 > 0) {
+    QK_TRY(in_device(parent_centroids, (size_t)N1 * d, tc1, &C1, s));
+    QK_TRY(in_device(parent_of_leaf, (size_t)N0, ta1, &a1, s));
+  }
+  return install(ix, X, I, n, C0, a0, C1, a1, s);
+}
+
+qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
+                    int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall, void* stream) {
+  QK_TRY(check_ready(ix));
+  if (nq < 0 || k < 1 || k > 1024 || (nq > 0 && (!q || !out_ids || !out_dist))) {
+    set_error("invalid search arguments");
+    return QK_ERR_ARG;
+  }
+  if (!(recall_target > 0.f) && nprobe < 1) {
+    set_error("fixed-nprobe search needs nprobe >= 1");
+    return QK_ERR_ARG;
+  }
+  if (ix->cfg.metric == QK_METRIC_IP && recall_target > 0.f) {
+    set_error("APS with inner product is not supported by this build");
+    return QK_ERR_UNSUPPORTED;
+  }
+  if (nq == 0) return QK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = ix->cfg.d;
+  const bool q_dev = is_device_ptr(q);
+  const bool ids_dev = is_device_ptr(out_ids), dist_dev = is_device_ptr(out_dist);
+  const bool np_dev = !out_nprobe || is_device_ptr(out_nprobe);
+  const bool rc_dev = !out_recall || is_device_ptr(out_recall);
+  const bool all_dev = q_dev && ids_dev && dist_dev && np_dev && rc_dev;
+  if (!q_dev) {
+    for (int64_t i = 0; i < nq * d; ++i)
+      if (std::isnan(q[i])) {
+        set_error("NaN in queries");
+        return QK_ERR_ARG;
+      }
+  }
+  // staging for host buffers
+  const size_t bq = sizeof(float) * (size_t)nq * d;
+  const size_t bi = sizeof(int64_t) * (size_t)nq * k, bd = sizeof(float) * (size_t)nq * k;
+  const size_t bn = sizeof(int32_t) * (size_t)nq, br = sizeof(float) * (size_t)nq;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  if (!all_dev) {
+    QK_TRY(ensure(ix->stage_in, al(bq)));
+    QK_TRY(ensure(ix->stage_out, al(bi) + al(bd) + al(bn) + al(br)));
+  }
+  unsigned char* so = static_cast<unsigned char*>(ix->stage_out.p);
+  const float* dq = q;
+  if (!q_dev) {
+    QK_CUDA(cudaMemcpyAsync(ix->stage_in.p, q, bq, cudaMemcpyHostToDevice, s));
+    dq = static_cast<const float*>(ix->stage_in.p);
+  }
+  int64_t* dids = ids_dev ? out_ids : reinterpret_cast<int64_t*>(so);
+  float* ddist = dist_dev ? out_dist : reinterpret_cast<float*>(so + al(bi));
+  int32_t* dnp = np_dev ? out_nprobe : reinterpret_cast<int32_t*>(so + al(bi) + al(bd));
+  float* drc = rc_dev ? out_recall : reinterpret_cast<float*>(so + al(bi) + al(bd) + al(bn));
+
+  SearchArgs a;
+  a.Q = dq;
+  a.nq = nq;
+  a.d = d;
+  a.metric = ix->cfg.metric;
+  a.L = ix->n_parent > 0 ? 2 : 1;
+  a.lv[0] = DevLevel{ix->vec0, ix->ids0, ix->off0, ix->size0, ix->cent0, ix->n_leaf};
+  a.lv[1] = DevLevel{ix->vec1, ix->ids1, ix->off1, ix->size1, ix->cent1, ix->n_parent};
+  const bool fixed = !(recall_target > 0.f);
+  a.fixed_nprobe = fixed ? nprobe : 0;
+  if (a.L == 1) {
+    a.root = ix->cent0;
+    a.n_root = ix->n_leaf;
+    a.M_root = fixed ? std::min(nprobe, ix->n_leaf) : n_candidates(ix->cfg.f_M_leaf, ix->n_leaf);
+    a.k1 = 0;
+  } else {
+    a.root = ix->cent1;
+    a.n_root = ix->n_parent;
+    a.M_root = n_candidates(ix->cfg.f_M_parent, ix->n_parent);
+    a.k1 = n_candidates(ix->cfg.f_M_leaf, ix->n_leaf);
+  }
+  a.k0 = k;
+  a.tau0 = recall_target;
+  a.tau1 = ix->cfg.upper_recall;
+  a.tau_rho = ix->cfg.tau_rho;
+  a.beta_mode = ix->cfg.beta_mode;
+  a.beta_table = ix->beta_table;
+  a.beta_a = ix->beta_a;
+  a.beta_lnB = ix->beta_lnB;
+  a.out_ids = dids;
+  a.out_dist = ddist;
+  a.out_nprobe = out_nprobe ? dnp : nullptr;
+  a.out_recall = out_recall ? drc : nullptr;
+  a.hits0 = ix->hits0;
+  a.hits1 = ix->hits1;
+  a.work = ix->work;
+  a.status = ix->status;
+  a.diag = ix->diag;
+  a.wait_stats = ix->diag + 8;
+  a.kcap = std::max({k, a.k1, a.M_root});
+  a.mcap = std::max({a.M_root, a.k1, 1});
+  QK_TRY(launch_search(a, s));
+  if (!all_dev) {
+    if (!ids_dev) QK_CUDA(cudaMemcpyAsync(out_ids, dids, bi, cudaMemcpyDeviceToHost, s));
+    if (!dist_dev) QK_CUDA(cudaMemcpyAsync(out_dist, ddist, bd, cudaMemcpyDeviceToHost, s));
+    if (!np_dev) QK_CUDA(cudaMemcpyAsync(out_nprobe, dnp, bn, cudaMemcpyDeviceToHost, s));
+    if (!rc_dev) QK_CUDA(cudaMemcpyAsync(out_recall, drc, br, cudaMemcpyDeviceToHost, s));
+    return read_device_status(ix, s);
+  }
+  return QK_OK;
+}
+
+qk_status qk_check(qk_index* ix, void* stream) {
+  if (!ix) {
+    set_error("null index");
+    return QK_ERR_ARG;
+  }
+  return read_device_status(ix, (cudaStream_t)stream);
+}
+
+qk_status qk_info(const qk_index* ix, int64_t* n_vectors, int32_t* n_leaf, int32_t* n_parent, int32_t* d) {
+  if (!ix) {
+    set_error("null index");
+    return QK_ERR_ARG;
+  }
+  if (n_vectors) *n_vectors = ix->n;
+  if (n_leaf) *n_leaf = ix->ready ? ix->n_leaf : ix->cfg.n_leaf;
+  if (n_parent) *n_parent = ix->ready ? ix->n_parent : ix->cfg.n_parent;
+  if (d) *d = ix->cfg.d;
+  return QK_OK;
+}
+
+qk_status qk_export_level(const qk_index* ix, int32_t level, int32_t* sizes, float* centroids, int64_t* ids) {
+  QK_TRY(check_ready(ix));
+  const int d = ix->cfg.d;
+  if (level == 0) {
+    if (sizes) std::copy(ix->h_size0.begin(), ix->h_size0.end(), sizes);
+    if (centroids)
+      QK_CUDA(cudaMemcpy(centroids, ix->cent0, sizeof(float) * (size_t)ix->n_leaf * d, cudaMemcpyDeviceToHost));
+    if (ids) {
+      std::vector<int64_t> h((size_t)ix->cap0);
+      QK_CUDA(cudaMemcpy(h.data(), ix->ids0, sizeof(int64_t) * ix->cap0, cudaMemcpyDeviceToHost));
+      int64_t o = 0;
+      for (int32_t j = 0; j < ix->n_leaf; ++j)
+        for (int32_t t = 0; t < ix->h_size0[j]; ++t) ids[o++] = h[ix->h_off0[j] + t];
+    }
+    return QK_OK;
+  }
+  if (level == 1 && ix->n_parent > 0) {
+    if (sizes) std::copy(ix->h_size1.begin(), ix->h_size1.end(), sizes);
+    if (centroids)
+      QK_CUDA(cudaMemcpy(centroids, ix->cent1, sizeof(float) * (size_t)ix->n_parent * d, cudaMemcpyDeviceToHost));
+    if (ids) {
+      std::vector<int64_t> h((size_t)ix->n_leaf);
+      QK_CUDA(cudaMemcpy(h.data(), ix->ids1, sizeof(int64_t) * ix->n_leaf, cudaMemcpyDeviceToHost));
+      int64_t o = 0;
+      for (int32_t j = 0; j < ix->n_parent; ++j)
+        for (int32_t t = 0; t < ix->h_size1[j]; ++t) ids[o++] = h[ix->h_off1[j] + t];
+    }
+    return QK_OK;
+  }
+  set_error("no such level");
+  return QK_ERR_ARG;
+}
+
+qk_status qk_get_hits(qk_index* ix, int32_t level, int64_t* hits, int32_t reset) {
+  QK_TRY(check_ready(ix));
+  unsigned long long* src = level == 0 ? ix->hits0 : (level == 1 ? ix->hits1 : nullptr);
+  int32_t n = level == 0 ? ix->n_leaf : ix->n_parent;
+  if (!src || n <= 0) {
+    set_error("no such level");
+    return QK_ERR_ARG;
+  }
+  if (hits) QK_CUDA(cudaMemcpy(hits, src, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+  if (reset) QK_CUDA(cudaMemset(src, 0, sizeof(unsigned long long) * n));
+  return QK_OK;
+}
+
+qk_status qk_cap_fraction(int32_t d, int32_t mode, const double* t, const double* rho, int64_t n, double* out_u,
+                          void* stream) {
+  if (d < 1 || n < 0 || (n > 0 && (!t || !rho || !out_u)) || (mode != QK_BETA_EXACT && mode != QK_BETA_TABLE)) {
+    set_error("invalid arguments");
+    return QK_ERR_ARG;
+  }
+  if (n == 0) return QK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  double a = 0.5 * (d + 1);
+  double lnB = std::lgamma(a) + std::lgamma(0.5) - std::lgamma(a + 0.5);
+  Tmp tt, tr, tb, to;
+  const double *dt = nullptr, *dr = nullptr;
+  QK_TRY(in_device(t, (size_t)n, tt, &dt, s));
+  QK_TRY(in_device(rho, (size_t)n, tr, &dr, s));
+  double* table = nullptr;
+  QK_TRY(tb.alloc<double>(kBetaTablePoints, &table));
+  QK_TRY(launch_beta_table(a, lnB, table, s));
+  bool out_dev = is_device_ptr(out_u);
+  double* dout = out_u;
+  if (!out_dev) QK_TRY(to.alloc<double>((size_t)n, &dout));
+  QK_TRY(launch_cap_fraction(mode, a, lnB, table, dt, dr, n, dout, s));
+  if (!out_dev) QK_CUDA(cudaMemcpyAsync(out_u, dout, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  return QK_OK;
+}
+
+qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, int32_t K, float* c_new,
+                         int32_t* assign, int32_t* counts, void* stream) {
+  if (!x || !c || n < 1 || d < 1 || K < 1) {
+    set_error("invalid arguments");
+    return QK_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Tmp tx, tc, ta, tn, tsum, tcnt;
+  const float *X = nullptr, *C = nullptr;
+  QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
+  QK_TRY(in_device(c, (size_t)K * d, tc, &C, s));
+  int32_t* a = nullptr;
+  float* Cn = nullptr;
+  double* sums = nullptr;
+  int32_t* cnt = nullptr;
+  QK_TRY(ta.alloc<int32_t>((size_t)n, &a));
+  QK_TRY(tn.alloc<float>((size_t)K * d, &Cn));
+  QK_TRY(tsum.alloc<double>((size_t)K * d, &sums));
+  QK_TRY(tcnt.alloc<int32_t>((size_t)K, &cnt));
+  QK_TRY(launch_kmeans_assign(X, n, d, C, K, a, nullptr, s));
+  QK_TRY(launch_kmeans_update(X, n, d, a, C, K, Cn, sums, cnt, s));
+  if (c_new) QK_CUDA(cudaMemcpyAsync(c_new, Cn, sizeof(float) * (size_t)K * d, cudaMemcpyDefault, s));
+  if (assign) QK_CUDA(cudaMemcpyAsync(assign, a, sizeof(int32_t) * (size_t)n, cudaMemcpyDefault, s));
+  if (counts) QK_CUDA(cudaMemcpyAsync(counts, cnt, sizeof(int32_t) * (size_t)K, cudaMemcpyDefault, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  return QK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Device layout of the multi-level partitioned index and the host object
+// that owns it.
+//
+// HBM layout (all arrays cudaMalloc'd, 256-byte aligned):
+//   level 0  arena vec0[cap0 x d] FP32 rows, ids0[cap0] int64; partition j
+//            owns rows [off0[j], off0[j] + size0[j]) of the arena, contiguous,
+//            so a partition streams with one-dimensional bulk copies;
+//            cent0[n_leaf x d] its centroids.
+//   level 1  vec1[n_leaf x d] the leaf centroids regrouped by parent,
+//            ids1[n_leaf] the leaf index of each row, off1/size1 per parent,
+//            cent1[n_parent x d] the parent centroids.
+//   root     the centroids of the top level (cent1, or cent0 for one level),
+//            scanned as one partition whose row index is the id.
+//   beta     the FP64 1024-point table of I_x((d+1)/2, 1/2).
+//   hits     int64 access counters per partition and level.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/quake_b300.h"
+
+namespace qk {
+
+struct DevLevel {
+  const float* vec = nullptr;
+  const int64_t* ids = nullptr;
+  const int64_t* off = nullptr;
+  const int32_t* size = nullptr;
+  const float* cent = nullptr;
+  int32_t n_part = 0;
+};
+
+struct SearchArgs {
+  const float* Q = nullptr;
+  int64_t nq = 0;
+  int32_t d = 0;
+  int32_t metric = 0;
+  int32_t L = 1;
+  DevLevel lv[2];
+  const float* root = nullptr;   // top-level centroids, scanned as one partition
+  int32_t n_root = 0;
+  int32_t M_root = 0;            // candidates kept from the root
+  int32_t k0 = 10;               // k at level 0
+  int32_t k1 = 0;                // k' at level 1 (= M of level 0)
+  double tau0 = 0.9;             // recall target of level 0
+  double tau1 = 0.99;            // recall target of level 1
+  double tau_rho = 0.01;
+  int32_t fixed_nprobe = 0;      // > 0: fixed-nprobe mode at level 0
+  int32_t beta_mode = 0;
+  const double* beta_table = nullptr;
+  double beta_a = 0.0, beta_lnB = 0.0;
+  int64_t* out_ids = nullptr;
+  float* out_dist = nullptr;
+  int32_t* out_nprobe = nullptr;
+  float* out_recall = nullptr;
+  unsigned long long* hits0 = nullptr;
+  unsigned long long* hits1 = nullptr;
+  int32_t* work = nullptr;       // work-stealing counter (zeroed before launch)
+  int32_t* status = nullptr;     // device status word
+  int64_t* diag = nullptr;       // first failure: code, query, details
+  int64_t* wait_stats = nullptr; // longest bulk-copy wait of the launch (cycles), optional
+  int32_t kcap = 16;             // capacity of the result set (>= every k used)
+  int32_t mcap = 16;             // capacity of the candidate list
+};
+
+struct Buffer {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct qk_index_impl;
+
+}  // namespace qk
+
+struct qk_index {
+  qk_config cfg;
+  int device = 0;
+  bool ready = false;
+  int64_t n = 0;                 // live vectors
+  int32_t n_leaf = 0, n_parent = 0;
+  // level 0
+  float* vec0 = nullptr;
+  int64_t* ids0 = nullptr;
+  int64_t cap0 = 0;              // arena rows
+  int64_t* off0 = nullptr;
+  int32_t* size0 = nullptr;
+  float* cent0 = nullptr;
+  std::vector<int64_t> h_off0, h_cap_part0;
+  std::vector<int32_t> h_size0;
+  // level 1
+  float* vec1 = nullptr;
+  int64_t* ids1 = nullptr;
+  int64_t* off1 = nullptr;
+  int32_t* size1 = nullptr;
+  float* cent1 = nullptr;
+  std::vector<int32_t> h_size1;
+  std::vector<int64_t> h_off1;
+  // shared
+  double* beta_table = nullptr;
+  unsigned long long* hits0 = nullptr;
+  unsigned long long* hits1 = nullptr;
+  int32_t* work = nullptr;
+  int32_t* status = nullptr;
+  int64_t* diag = nullptr;
+  double beta_a = 0.0, beta_lnB = 0.0;
+  // scratch for host <-> device staging
+  qk::Buffer stage_in, stage_out;
+  // id -> (partition, slot) for deletes
+  std::unordered_map<int64_t, int64_t> where;
+};

@@ -1,0 +1,143 @@
+"""Python face of the C ABI: an `Index` object over qk_* calls.
+
+Marshalling only: arrays are checked for dtype and contiguity and their
+addresses handed to the CUDA library.  Outputs go to the device of the query
+tensor (CUDA tensors in -> CUDA tensors out, stream-ordered) or to numpy
+arrays for host inputs.
+"""
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _as(a, dtype):
+    """numpy array or torch tensor, C-contiguous with the given numpy dtype."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        tdt = {np.float32: torch.float32, np.int64: torch.int64, np.int32: torch.int32,
+               np.float64: torch.float64}[dtype]
+        if a.dtype != tdt:
+            raise TypeError(f"expected {tdt}, got {a.dtype}")
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def config(d, metric=L.METRIC_L2, n_leaf=1000, n_parent=0, kmeans_iters=10, beta_mode=L.BETA_TABLE,
+           seed=1234, f_M_leaf=0.1, f_M_parent=0.25, tau_rho=0.01, upper_recall=0.99):
+    c = L.QkConfig()
+    L.lib.qk_config_default(C.byref(c))
+    c.d, c.metric, c.n_leaf, c.n_parent = d, metric, n_leaf, n_parent
+    c.kmeans_iters, c.beta_mode, c.seed = kmeans_iters, beta_mode, seed
+    c.f_M_leaf, c.f_M_parent, c.tau_rho, c.upper_recall = f_M_leaf, f_M_parent, tau_rho, upper_recall
+    return c
+
+
+class Index:
+    """A Quake index on the current CUDA device (see include/quake_b300.h)."""
+
+    def __init__(self, d, **kw):
+        self.cfg = config(d, **kw)
+        h = C.c_void_p()
+        L.check(L.lib.qk_create(C.byref(self.cfg), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib.qk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def d(self):
+        return self.cfg.d
+
+    def build(self, x, ids, stream=None):
+        x, ids = _as(x, np.float32), _as(ids, np.int64)
+        L.check(L.lib.qk_build(self._h, L.ptr(x), L.ptr(ids), int(ids.shape[0]), L.stream_ptr(stream)))
+
+    def load(self, x, ids, leaf_centroids, leaf_of_row, parent_centroids=None, parent_of_leaf=None,
+             stream=None):
+        x, ids = _as(x, np.float32), _as(ids, np.int64)
+        c0, a0 = _as(leaf_centroids, np.float32), _as(leaf_of_row, np.int32)
+        c1 = None if parent_centroids is None else _as(parent_centroids, np.float32)
+        a1 = None if parent_of_leaf is None else _as(parent_of_leaf, np.int32)
+        L.check(L.lib.qk_load(self._h, L.ptr(x), L.ptr(ids), int(ids.shape[0]), L.ptr(c0), L.ptr(a0),
+                              L.ptr(c1), L.ptr(a1), L.stream_ptr(stream)))
+
+    def search(self, q, k, recall_target=0.9, nprobe=0, out=None, stream=None):
+        """Returns (ids, dist, nprobe, recall_estimate) on the device of `q`."""
+        q = _as(q, np.float32)
+        nq = int(q.shape[0])
+        if out is None:
+            if hasattr(q, "data_ptr"):
+                import torch
+                dev = q.device
+                out = (torch.empty((nq, k), dtype=torch.int64, device=dev),
+                       torch.empty((nq, k), dtype=torch.float32, device=dev),
+                       torch.empty(nq, dtype=torch.int32, device=dev),
+                       torch.empty(nq, dtype=torch.float32, device=dev))
+            else:
+                out = (np.empty((nq, k), np.int64), np.empty((nq, k), np.float32),
+                       np.empty(nq, np.int32), np.empty(nq, np.float32))
+        oi, od, on, orr = out
+        L.check(L.lib.qk_search(self._h, L.ptr(q), nq, int(k), float(recall_target), int(nprobe),
+                                L.ptr(oi), L.ptr(od), L.ptr(on), L.ptr(orr), L.stream_ptr(stream)))
+        return out
+
+    def check(self, stream=None):
+        """Waits for this index's kernels on `stream`; raises if a device check failed."""
+        L.check(L.lib.qk_check(self._h, L.stream_ptr(stream)))
+
+    def info(self):
+        n = C.c_int64()
+        n0, n1, d = C.c_int32(), C.c_int32(), C.c_int32()
+        L.check(L.lib.qk_info(self._h, C.byref(n), C.byref(n0), C.byref(n1), C.byref(d)))
+        return dict(n=n.value, n_leaf=n0.value, n_parent=n1.value, d=d.value)
+
+    def export_level(self, level):
+        """(sizes, centroids, ids grouped by partition) of one level, as numpy."""
+        inf = self.info()
+        nparts = inf["n_leaf"] if level == 0 else inf["n_parent"]
+        nrows = inf["n"] if level == 0 else inf["n_leaf"]
+        sizes = np.empty(nparts, np.int32)
+        cents = np.empty((nparts, self.d), np.float32)
+        ids = np.empty(nrows, np.int64)
+        L.check(L.lib.qk_export_level(self._h, level, L.ptr(sizes), L.ptr(cents), L.ptr(ids)))
+        return sizes, cents, ids
+
+    def hits(self, level=0, reset=False):
+        inf = self.info()
+        n = inf["n_leaf"] if level == 0 else inf["n_parent"]
+        h = np.empty(n, np.int64)
+        L.check(L.lib.qk_get_hits(self._h, level, L.ptr(h), 1 if reset else 0))
+        return h
+
+
+def cap_fraction(d, t, rho, mode=L.BETA_EXACT):
+    """GPU FP64 cap volume fraction for arrays t, rho (host numpy in, numpy out)."""
+    t = np.ascontiguousarray(t, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    out = np.empty_like(t)
+    L.check(L.lib.qk_cap_fraction(int(d), int(mode), L.ptr(t), L.ptr(rho), int(t.shape[0]), L.ptr(out), None))
+    return out
+
+
+def kmeans_step(x, c):
+    """One GPU Lloyd step: (new centroids, assignment, counts) as numpy."""
+    x = np.ascontiguousarray(x, np.float32)
+    c = np.ascontiguousarray(c, np.float32)
+    n, d = x.shape
+    K = c.shape[0]
+    cn = np.empty_like(c)
+    a = np.empty(n, np.int32)
+    cnt = np.empty(K, np.int32)
+    L.check(L.lib.qk_kmeans_step(L.ptr(x), n, d, L.ptr(c), K, L.ptr(cn), L.ptr(a), L.ptr(cnt), None))
+    return cn, a, cnt

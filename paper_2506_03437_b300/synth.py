@@ -92,9 +92,16 @@ def aps_search(seed=1236, n=1_000_000, d=128, n_comp=1000, sigma=1.0, nq=10_000,
     """Two-level APS workload (1M x 128, 1,000 components, Zipf(1.1) queries)."""
     C = mixture_centers(n_comp, d, seed)
     X, _ = mixture_samples(C, n, sigma, seed + 1)
-    lab = zipf_labels(n_comp, nq, zipf, seed + 2)
-    Q, _ = mixture_samples(C, nq, sigma, seed + 3, labels=lab)
+    Q = aps_queries(seed, d, n_comp, sigma, nq, zipf)
     return X, np.arange(n, dtype=np.int64), Q
+
+
+def aps_queries(seed, d, n_comp, sigma, nq, zipf=1.1, stream=0):
+    """Queries of the APS workload; stream > 0 gives further independent batches."""
+    C = mixture_centers(n_comp, d, seed)
+    lab = zipf_labels(n_comp, nq, zipf, seed + 2 + 1000 * stream)
+    Q, _ = mixture_samples(C, nq, sigma, seed + 3 + 1000 * stream, labels=lab)
+    return Q
 
 
 def zipf_partitions(seed=1238, n=5_000_000, d=256, n_part=20_000, a=1.0, lo=10, hi=100_000,
