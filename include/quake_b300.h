@@ -188,6 +188,32 @@ qk_status qk_cap_fraction(int32_t d, int32_t mode, const double* t, const double
 qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, int32_t K,
                          float* c_new, int32_t* assign, int32_t* counts, void* stream);
 
+/*
+ * Allocation-free Lloyd step.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory while they run
+ * (a serving loop that cannot afford the device-wide synchronisation of
+ * cudaMalloc/cudaFree, a process whose custom allocator owns all free
+ * memory, an embedder with a fixed device footprint).  It computes exactly
+ * what qk_kmeans_step computes, but allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ *
+ *  - Every buffer must be device memory (host pointers -> QK_ERR_ARG):
+ *    x (n x d), c (K x d) in; c_new (K x d), assign[n], counts[K] out, all
+ *    required.  c_new may be the same buffer as c.
+ *  - Its only scratch, the FP64 per-cluster sums, lives in a fixed 8 MiB
+ *    array inside the library that every GPU loading the library keeps until
+ *    the process exits.  K * d may not exceed 1,048,576 (QK_ERR_ARG otherwise).
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the one array and each call clears the sums it uses
+ *    before accumulating.  Calls that overlap on the GPU (different streams,
+ *    or different host threads, at the same time) race on it: serialise them.
+ *  - Stream-ordered on `stream`; returns before the GPU has finished.
+ */
+qk_status qk_kmeans_step_noalloc(const float* x, int64_t n, int32_t d, const float* c, int32_t K,
+                                 float* c_new, int32_t* assign, int32_t* counts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
