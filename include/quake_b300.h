@@ -154,15 +154,36 @@ qk_status qk_info(const qk_index* index, int64_t* n_vectors, int32_t* n_leaf, in
                   int32_t* d);
 
 /*
+ * Inserts n vectors x (n x d) with new ids (Sec. 3, "Adaptive Incremental
+ * Maintenance"): each descends the tree greedily (the nearest parent
+ * centroid, then the nearest leaf centroid under it; ties to the lower
+ * index; centroids are not moved) and is appended to that leaf partition,
+ * in batch order.  An id already in the index or repeated in the batch gives
+ * QK_ERR_DUP_ID and NaN gives QK_ERR_ARG; in both cases nothing is inserted.
+ * A partition whose reserved rows run out is moved, with all others, into a
+ * freshly laid-out arena.  Synchronous.
+ */
+qk_status qk_insert(qk_index* index, const float* x, const int64_t* ids, int64_t n, void* stream);
+
+/*
+ * Deletes the vectors with the given ids (Sec. 3: the map locates the
+ * partition, the vector is removed with immediate compaction).  Deletes apply
+ * in order; each moves the partition's last row into the freed slot.  Unknown
+ * ids are skipped; *n_removed (if not NULL) receives the number removed.
+ * Synchronous.
+ */
+qk_status qk_delete(qk_index* index, const int64_t* ids, int64_t n, int64_t* n_removed, void* stream);
+
+/*
  * Copies the structure of one level to host arrays for inspection:
- * level 0: sizes[n_leaf], centroids (n_leaf x d), and, if not NULL,
- *   ids[n_vectors] grouped by partition in partition order;
+ * level 0: sizes[n_leaf], centroids (n_leaf x d), ids[n_vectors] and
+ *   vectors (n_vectors x d) grouped by partition in partition order;
  * level 1: sizes[n_parent], centroids (n_parent x d), ids[n_leaf] = leaf
- *   indices grouped by parent.
+ *   indices grouped by parent (vectors must be NULL).
  * All outputs are host pointers; any may be NULL.
  */
 qk_status qk_export_level(const qk_index* index, int32_t level, int32_t* sizes, float* centroids,
-                          int64_t* ids);
+                          int64_t* ids, float* vectors);
 
 /* Copies the access counts of `level` (one int64 per partition, summed over
  * searches since the last reset) to a host array; reset != 0 zeroes them. */

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIME
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = [
     "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load",
-    "qk_search", "qk_check", "qk_info", "qk_export_level", "qk_get_hits", "qk_cap_fraction",
+    "qk_search", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_get_hits", "qk_cap_fraction",
     "qk_kmeans_step", "qk_kmeans_step_noalloc",
 ]
 
@@ -57,7 +57,9 @@ def _load():
         "qk_search": (i32, [vp, vp, i64, i32, f32, i32, vp, vp, vp, vp, vp]),
         "qk_check": (i32, [vp, vp]),
         "qk_info": (i32, [vp, vp, vp, vp, vp]),
-        "qk_export_level": (i32, [vp, i32, vp, vp, vp]),
+        "qk_insert": (i32, [vp, vp, vp, i64, vp]),
+        "qk_delete": (i32, [vp, vp, i64, vp, vp]),
+        "qk_export_level": (i32, [vp, i32, vp, vp, vp, vp]),
         "qk_get_hits": (i32, [vp, i32, vp, i32]),
         "qk_cap_fraction": (i32, [i32, i32, vp, vp, i64, vp, vp]),
         "qk_kmeans_step": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp]),

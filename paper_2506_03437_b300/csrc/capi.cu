@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "capvol.cuh"
@@ -31,6 +32,18 @@ qk_status launch_histogram(const int32_t* lab, int64_t n, int32_t K, int32_t* co
                            cudaStream_t s);
 qk_status launch_scatter(const float* X, const int64_t* ids, int64_t n, int d, const int32_t* lab,
                          const int64_t* off, int32_t* cursor, float* vec, int64_t* ids_out, cudaStream_t s);
+
+qk_status launch_descend_children(const float* X, int64_t n, int d, const int32_t* parent, const float* vec1,
+                                  const int64_t* ids1, const int64_t* off1, const int32_t* size1, int32_t* leaf,
+                                  cudaStream_t s);
+qk_status launch_nan_check(const float* X, int64_t total, int32_t* flag, cudaStream_t s);
+qk_status launch_relayout(const float* old_vec, const int64_t* old_ids, const int64_t* old_off, const int64_t* new_off,
+                          const int32_t* size, int32_t n_part, int d, float* new_vec, int64_t* new_ids,
+                          cudaStream_t s);
+qk_status launch_place_rows(const float* X, const int64_t* ids, int64_t n, int d, const int64_t* dst, float* vec,
+                            int64_t* ids_out, cudaStream_t s);
+qk_status launch_gather_moves(const float* vec, const int64_t* ids, const int64_t* src, int64_t m, int d, float* tvec,
+                              int64_t* tids, cudaStream_t s);
 
 static thread_local std::string g_err;
 
@@ -221,7 +234,8 @@ static qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64
     QK_CUDA(cudaMemsetAsync(ix->hits1, 0, sizeof(unsigned long long) * N1, s));
   }
   // id map, built from the arena so that it records the real slots
-  std::vector<int64_t> h_ids((size_t)ix->cap0);
+  std::vector<int64_t>& h_ids = ix->h_ids0;
+  h_ids.assign((size_t)ix->cap0, -1);
   QK_CUDA(cudaMemcpyAsync(h_ids.data(), ix->ids0, sizeof(int64_t) * ix->cap0, cudaMemcpyDeviceToHost, s));
   QK_CUDA(cudaStreamSynchronize(s));
   ix->where.clear();
@@ -296,6 +310,63 @@ static qk_status check_ready(const qk_index* ix) {
   if (!ix->ready) {
     set_error("index is empty: build or load it first");
     return QK_ERR_STATE;
+  }
+  return QK_OK;
+}
+
+// Gives every level-0 partition room for need[j] rows: partitions whose
+// capacity is exceeded get capacity_for(need[j]); the arena is re-laid out
+// into fresh memory (all partitions keep their slots).
+static qk_status grow_arena(qk_index* ix, const std::vector<int32_t>& need, cudaStream_t s) {
+  const int d = ix->cfg.d;
+  const int32_t N0 = ix->n_leaf;
+  std::vector<int64_t> cap(ix->h_cap_part0), off(N0);
+  for (int32_t j = 0; j < N0; ++j)
+    if (need[j] > cap[j]) cap[j] = capacity_for(need[j]);
+  int64_t total = 0;
+  for (int32_t j = 0; j < N0; ++j) {
+    off[j] = total;
+    total += cap[j];
+  }
+  float* nvec = nullptr;
+  int64_t* nids = nullptr;
+  Tmp toff;
+  int64_t* doff = nullptr;
+  QK_TRY(dalloc(&nvec, (size_t)total * d));
+  qk_status st = dalloc(&nids, (size_t)total);
+  if (st == QK_OK) st = toff.alloc<int64_t>(N0, &doff);
+  if (st != QK_OK) {
+    dfree(nvec);
+    dfree(nids);
+    return st;
+  }
+  QK_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
+  QK_TRY(launch_relayout(ix->vec0, ix->ids0, ix->off0, doff, ix->size0, N0, d, nvec, nids, s));
+  QK_CUDA(cudaMemcpyAsync(ix->off0, doff, sizeof(int64_t) * N0, cudaMemcpyDeviceToDevice, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  dfree(ix->vec0);
+  dfree(ix->ids0);
+  ix->vec0 = nvec;
+  ix->ids0 = nids;
+  std::vector<int64_t> mirror((size_t)total, -1);
+  for (int32_t j = 0; j < N0; ++j)
+    for (int32_t t = 0; t < ix->h_size0[j]; ++t) mirror[off[j] + t] = ix->h_ids0[ix->h_off0[j] + t];
+  ix->h_ids0.swap(mirror);
+  ix->h_off0 = off;
+  ix->h_cap_part0 = cap;
+  ix->cap0 = total;
+  return QK_OK;
+}
+
+template <class T>
+static qk_status to_host(const T* src, size_t count, std::vector<T>& out, cudaStream_t s) {
+  out.resize(count);
+  if (count == 0) return QK_OK;
+  if (is_device_ptr(src)) {
+    QK_CUDA(cudaMemcpyAsync(out.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost, s));
+    QK_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(out.data(), src, sizeof(T) * count);
   }
   return QK_OK;
 }
@@ -573,6 +644,157 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
   return QK_OK;
 }
 
+qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n, void* stream) {
+  QK_TRY(check_ready(ix));
+  if (n < 0 || (n > 0 && (!x || !ids))) {
+    set_error("invalid insert arguments");
+    return QK_ERR_ARG;
+  }
+  if (n == 0) return QK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = ix->cfg.d;
+  std::vector<int64_t> hid;
+  QK_TRY(to_host(ids, (size_t)n, hid, s));
+  {
+    std::unordered_map<int64_t, int> seen;
+    seen.reserve((size_t)n * 2);
+    for (int64_t r = 0; r < n; ++r) {
+      if (ix->where.count(hid[r]) || !seen.emplace(hid[r], 1).second) {
+        set_error("insert: id " + std::to_string(hid[r]) + " is already present; nothing was inserted");
+        return QK_ERR_DUP_ID;
+      }
+    }
+  }
+  Tmp tx, ti, tflag, tleaf, tpar, tdst;
+  const float* X = nullptr;
+  const int64_t* I = nullptr;
+  QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
+  QK_TRY(in_device(ids, (size_t)n, ti, &I, s));
+  int32_t* flag = nullptr;
+  QK_TRY(tflag.alloc<int32_t>(1, &flag));
+  QK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
+  QK_TRY(launch_nan_check(X, n * d, flag, s));
+  int32_t hflag = 0;
+  QK_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  if (hflag) {
+    set_error("insert: NaN in vectors; nothing was inserted");
+    return QK_ERR_ARG;
+  }
+  // greedy descent (Sec. 3): nearest centroid at each level, ties to the lower index
+  int32_t* leaf = nullptr;
+  QK_TRY(tleaf.alloc<int32_t>((size_t)n, &leaf));
+  if (ix->n_parent == 0) {
+    QK_TRY(launch_kmeans_assign(X, n, d, ix->cent0, ix->n_leaf, leaf, nullptr, s));
+  } else {
+    int32_t* par = nullptr;
+    QK_TRY(tpar.alloc<int32_t>((size_t)n, &par));
+    QK_TRY(launch_kmeans_assign(X, n, d, ix->cent1, ix->n_parent, par, nullptr, s));
+    QK_TRY(launch_descend_children(X, n, d, par, ix->vec1, ix->ids1, ix->off1, ix->size1, leaf, s));
+  }
+  std::vector<int32_t> hleaf((size_t)n);
+  QK_CUDA(cudaMemcpyAsync(hleaf.data(), leaf, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> need(ix->h_size0);
+  bool grow = false;
+  for (int64_t r = 0; r < n; ++r) {
+    int32_t j = hleaf[r];
+    if (j < 0 || j >= ix->n_leaf) {
+      set_error("insert: descent reached an empty parent partition");
+      return QK_ERR_STATE;
+    }
+    if (++need[j] > ix->h_cap_part0[j]) grow = true;
+  }
+  if (grow) QK_TRY(grow_arena(ix, need, s));
+  std::vector<int64_t> dst((size_t)n);
+  std::vector<int32_t> cur(ix->h_size0);
+  for (int64_t r = 0; r < n; ++r) {
+    int32_t j = hleaf[r];
+    int32_t slot = cur[j]++;
+    dst[r] = ix->h_off0[j] + slot;
+  }
+  int64_t* ddst = nullptr;
+  QK_TRY(tdst.alloc<int64_t>((size_t)n, &ddst));
+  QK_CUDA(cudaMemcpyAsync(ddst, dst.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+  QK_TRY(launch_place_rows(X, I, n, d, ddst, ix->vec0, ix->ids0, s));
+  QK_CUDA(cudaMemcpyAsync(ix->size0, cur.data(), sizeof(int32_t) * ix->n_leaf, cudaMemcpyHostToDevice, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  for (int64_t r = 0; r < n; ++r) {
+    int32_t j = hleaf[r];
+    int64_t slot = dst[r] - ix->h_off0[j];
+    ix->where[hid[r]] = ((int64_t)j << 32) | (uint32_t)slot;
+    ix->h_ids0[dst[r]] = hid[r];
+  }
+  ix->h_size0 = cur;
+  ix->n += n;
+  return QK_OK;
+}
+
+qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_removed, void* stream) {
+  QK_TRY(check_ready(ix));
+  if (n < 0 || (n > 0 && !ids)) {
+    set_error("invalid delete arguments");
+    return QK_ERR_ARG;
+  }
+  if (n_removed) *n_removed = 0;
+  if (n == 0) return QK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = ix->cfg.d;
+  std::vector<int64_t> hid;
+  QK_TRY(to_host(ids, (size_t)n, hid, s));
+  // Replay the deletes in order on the host mirror (swap-with-last), keeping,
+  // for every slot that changed, the arena slot its final content came from.
+  std::unordered_map<int32_t, std::unordered_map<int32_t, int32_t>> src_of;
+  std::vector<int32_t> size(ix->h_size0);
+  int64_t removed = 0;
+  for (int64_t r = 0; r < n; ++r) {
+    auto it = ix->where.find(hid[r]);
+    if (it == ix->where.end()) continue;
+    int32_t j = (int32_t)(it->second >> 32), slot = (int32_t)(it->second & 0xffffffff);
+    int32_t last = size[j] - 1;
+    auto& m = src_of[j];
+    if (slot != last) {
+      auto lt = m.find(last);
+      m[slot] = lt == m.end() ? last : lt->second;
+      int64_t moved = ix->h_ids0[ix->h_off0[j] + last];
+      ix->h_ids0[ix->h_off0[j] + slot] = moved;
+      ix->where[moved] = ((int64_t)j << 32) | (uint32_t)slot;
+    }
+    m.erase(last);
+    ix->h_ids0[ix->h_off0[j] + last] = -1;
+    ix->where.erase(it);
+    size[j] = last;
+    ++removed;
+  }
+  std::vector<int64_t> src, dst;
+  for (auto& kv : src_of)
+    for (auto& mv : kv.second)
+      if (mv.first < size[kv.first] && mv.first != mv.second) {
+        src.push_back(ix->h_off0[kv.first] + mv.second);
+        dst.push_back(ix->h_off0[kv.first] + mv.first);
+      }
+  const int64_t m = (int64_t)src.size();
+  if (m > 0) {
+    Tmp tsrc, tdst, tvec, tids;
+    int64_t *dsrc = nullptr, *ddst = nullptr, *dtid = nullptr;
+    float* dtv = nullptr;
+    QK_TRY(tsrc.alloc<int64_t>((size_t)m, &dsrc));
+    QK_TRY(tdst.alloc<int64_t>((size_t)m, &ddst));
+    QK_TRY(tvec.alloc<float>((size_t)m * d, &dtv));
+    QK_TRY(tids.alloc<int64_t>((size_t)m, &dtid));
+    QK_CUDA(cudaMemcpyAsync(dsrc, src.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
+    QK_CUDA(cudaMemcpyAsync(ddst, dst.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
+    QK_TRY(launch_gather_moves(ix->vec0, ix->ids0, dsrc, m, d, dtv, dtid, s));
+    QK_TRY(launch_place_rows(dtv, dtid, m, d, ddst, ix->vec0, ix->ids0, s));
+  }
+  QK_CUDA(cudaMemcpyAsync(ix->size0, size.data(), sizeof(int32_t) * ix->n_leaf, cudaMemcpyHostToDevice, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  ix->h_size0 = size;
+  ix->n -= removed;
+  if (n_removed) *n_removed = removed;
+  return QK_OK;
+}
+
 qk_status qk_check(qk_index* ix, void* stream) {
   if (!ix) {
     set_error("null index");
@@ -593,7 +815,8 @@ qk_status qk_info(const qk_index* ix, int64_t* n_vectors, int32_t* n_leaf, int32
   return QK_OK;
 }
 
-qk_status qk_export_level(const qk_index* ix, int32_t level, int32_t* sizes, float* centroids, int64_t* ids) {
+qk_status qk_export_level(const qk_index* ix, int32_t level, int32_t* sizes, float* centroids, int64_t* ids,
+                          float* vectors) {
   QK_TRY(check_ready(ix));
   const int d = ix->cfg.d;
   if (level == 0) {
@@ -606,6 +829,16 @@ qk_status qk_export_level(const qk_index* ix, int32_t level, int32_t* sizes, flo
       int64_t o = 0;
       for (int32_t j = 0; j < ix->n_leaf; ++j)
         for (int32_t t = 0; t < ix->h_size0[j]; ++t) ids[o++] = h[ix->h_off0[j] + t];
+    }
+    if (vectors) {
+      int64_t o = 0;
+      for (int32_t j = 0; j < ix->n_leaf; ++j) {
+        size_t rows = (size_t)ix->h_size0[j];
+        if (rows)
+          QK_CUDA(cudaMemcpy(vectors + o * d, ix->vec0 + ix->h_off0[j] * d, sizeof(float) * rows * d,
+                             cudaMemcpyDeviceToHost));
+        o += rows;
+      }
     }
     return QK_OK;
   }

@@ -91,6 +91,7 @@ struct qk_index {
   float* cent0 = nullptr;
   std::vector<int64_t> h_off0, h_cap_part0;
   std::vector<int32_t> h_size0;
+  std::vector<int64_t> h_ids0;   // host mirror of ids0 (arena slot -> id)
   // level 1
   float* vec1 = nullptr;
   int64_t* ids1 = nullptr;

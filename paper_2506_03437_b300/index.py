@@ -102,16 +102,28 @@ class Index:
         L.check(L.lib.qk_info(self._h, C.byref(n), C.byref(n0), C.byref(n1), C.byref(d)))
         return dict(n=n.value, n_leaf=n0.value, n_parent=n1.value, d=d.value)
 
-    def export_level(self, level):
-        """(sizes, centroids, ids grouped by partition) of one level, as numpy."""
+    def export_level(self, level, vectors=False):
+        """(sizes, centroids, ids grouped by partition[, vectors]) of one level, as numpy."""
         inf = self.info()
         nparts = inf["n_leaf"] if level == 0 else inf["n_parent"]
         nrows = inf["n"] if level == 0 else inf["n_leaf"]
         sizes = np.empty(nparts, np.int32)
         cents = np.empty((nparts, self.d), np.float32)
         ids = np.empty(nrows, np.int64)
-        L.check(L.lib.qk_export_level(self._h, level, L.ptr(sizes), L.ptr(cents), L.ptr(ids)))
-        return sizes, cents, ids
+        vec = np.empty((nrows, self.d), np.float32) if vectors else None
+        L.check(L.lib.qk_export_level(self._h, level, L.ptr(sizes), L.ptr(cents), L.ptr(ids), L.ptr(vec)))
+        return (sizes, cents, ids, vec) if vectors else (sizes, cents, ids)
+
+    def insert(self, x, ids, stream=None):
+        x, ids = _as(x, np.float32), _as(ids, np.int64)
+        L.check(L.lib.qk_insert(self._h, L.ptr(x), L.ptr(ids), int(ids.shape[0]), L.stream_ptr(stream)))
+
+    def delete(self, ids, stream=None):
+        """Removes the given ids; returns how many were present."""
+        ids = _as(ids, np.int64)
+        n = C.c_int64()
+        L.check(L.lib.qk_delete(self._h, L.ptr(ids), int(ids.shape[0]), C.byref(n), L.stream_ptr(stream)))
+        return n.value
 
     def hits(self, level=0, reset=False):
         inf = self.info()
