@@ -210,6 +210,73 @@ qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, i
                          float* c_new, int32_t* assign, int32_t* counts, void* stream);
 
 /*
+ * Maintenance parameters (Sec. 4 and Sec. 8.1).
+ *   lambda_sizes/us   the latency function lambda(s): lambda_points profiled
+ *                     (size, microseconds) pairs with strictly increasing
+ *                     sizes, interpolated linearly, extended linearly past
+ *                     both ends and floored at 0.  It is applied to partition
+ *                     sizes and to centroid counts (Delta O+ = lambda(N + 1) -
+ *                     lambda(N), Delta O- = lambda(N - 1) - lambda(N)).
+ *   tau_us            decision threshold tau (paper: 250 ns = 0.25).
+ *   alpha             split access scaling (paper: 0.9).
+ *   refine_radius     r_f (paper: 50); also the merge estimate's receiver count.
+ *   refine_iters      Lloyd iterations of the refinement (paper: 1); refine = 0 skips it.
+ *   split_iters       Lloyd iterations of the 2-means that splits a partition.
+ *   s_min             partitions smaller than this are merge candidates.
+ *   window            |W| in queries; 0 = the queries searched since the last
+ *                     build, load or maintain.
+ */
+typedef struct {
+  const double* lambda_sizes;
+  const double* lambda_us;
+  int32_t lambda_points;
+  int32_t refine_radius;
+  int32_t refine_iters;
+  int32_t split_iters;
+  int32_t s_min;
+  int32_t refine;
+  double tau_us;
+  double alpha;
+  int64_t window;
+} qk_maint_params;
+
+/* One considered action: kind 0 = split, 1 = merge; partition is the index
+ * at the start of the level's pass; estimate is Eq. 6 (split) or the uniform
+ * redistribution estimate (merge); delta is Eq. 4 or Eq. 5 after the
+ * tentative action (NaN if a split left a child empty). */
+typedef struct {
+  int32_t level;
+  int32_t kind;
+  int32_t partition;
+  int32_t committed;
+  double estimate;
+  double delta;
+} qk_maint_action;
+
+/*
+ * The maintenance pass of Sec. 4 ("Decision Workflow"), bottom-up over the
+ * levels.  Stage 0: A = access count / |W| from the counters the searches
+ * accumulated, sizes from the index.  Stage 1: split estimate (Eq. 6) for
+ * every partition and merge estimate for partitions smaller than s_min; the
+ * candidates below -tau are taken in ascending order of the estimate.
+ * Stage 2: a tentative split runs 2-means on the partition (rows seeded by
+ * SplitMix64 from the index seed, the level and the partition), a tentative
+ * merge sends every row to its nearest remaining centroid; Eq. 4 / Eq. 5 are
+ * evaluated with the real sizes and the current partition count.  Stage 3:
+ * commit when Delta < -tau, otherwise the partition is left as it was.  A
+ * committed split is followed by refinement (Lloyd iterations over the r_f
+ * partitions nearest each child); partitions touched by a committed action
+ * are not considered again in the same pass.  Stage 4: in a two-level index
+ * the parent level is then maintained the same way over the updated leaf
+ * centroids.  The arena is re-laid out once, partition indices are
+ * renumbered (survivors keep their order; split children are appended) and
+ * the access counters restart.  Up to log_cap actions are written to log;
+ * *n_log receives the number considered.  Synchronous.
+ */
+qk_status qk_maintain(qk_index* index, const qk_maint_params* params, qk_maint_action* log, int32_t log_cap,
+                      int32_t* n_log, void* stream);
+
+/*
  * Allocation-free Lloyd step.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory while they run
  * (a serving loop that cannot afford the device-wide synchronisation of

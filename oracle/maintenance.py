@@ -19,9 +19,11 @@ technical report:
       receiver m gains Delta s_m = its count and Delta A_m = A_j Delta s_m / s_j.
   M6  Verified split: the children's real sizes, each child with alpha A_j
       (the Stage-1 frequency assumption is kept, Stage 2).
-  M7  Split = 2-means inside the partition (seeded rows, fixed iterations),
-      then one refinement pass: a Lloyd iteration seeded by the current
-      centroids over the r_f partitions nearest the two new centroids.
+  M7  Split = 2-means inside the partition (fixed iterations) over its vectors
+      taken in ascending id order, so that the seeded rows do not depend on
+      how a partition happens to be stored; then one refinement pass: a Lloyd
+      iteration seeded by the current centroids over the r_f partitions
+      nearest the two new centroids.
   M8  Partitions are processed in ascending order of their estimated delta;
       N_l is updated after every commit.  Insert descends greedily (the
       nearest centroid at each level, ties to the lower index).  Delete swaps
@@ -186,3 +188,189 @@ def refine(level, parts, iters=1):
         level.centroids[j] = C[n]
         level.vectors[j] = rows[a == n]
         level.ids[j] = rid[a == n]
+
+
+# ------------------------------------------------------ the maintenance pass
+
+MASK64 = (1 << 64) - 1
+
+
+class MaintParams:
+    """Maintenance parameters (Sec. 4 and Sec. 8.1 defaults where the paper gives them)."""
+
+    def __init__(self, lam, tau=0.25, alpha=0.9, refine_radius=50, refine_iters=1, split_iters=10,
+                 s_min=0, seed=1234, refine=True):
+        self.lam = lam
+        self.tau = tau
+        self.alpha = alpha
+        self.refine_radius = refine_radius
+        self.refine_iters = refine_iters
+        self.split_iters = split_iters
+        self.s_min = s_min
+        self.seed = seed
+        self.refine = refine
+
+
+def split_seed(seed, level, j):
+    """Seed of the 2-means that splits partition j of `level` (both sides use this rule)."""
+    return (seed + 0x9E3779B97F4A7C15 * (level * 1_000_003 + j + 1)) & MASK64
+
+
+def nearest(C, live, x, count, exclude=None):
+    """The `count` live centroid indices nearest to x (ties to the lower index)."""
+    cand = [j for j in live if j != exclude]
+    if not cand:
+        return []
+    cand = np.array(cand, dtype=np.int64)
+    d = distances(x, C[cand], L2)
+    order = np.lexsort((cand, d))
+    return [int(cand[i]) for i in order[:count]]
+
+
+def maintain_level(level, A, prm, level_no, parent_of=None):
+    """One estimate / verify / commit pass over one level (Sec. 4 "Decision Workflow").
+
+    level      kmeans.Level (centroids, vectors, ids), modified in place
+    A          access frequency per partition (hits / |W|)
+    parent_of  for level 0 of a two-level index: the parent of every leaf,
+               extended and compacted together with the leaves
+    Returns (log, keep): the actions taken and the old index of every
+    surviving partition, in the new order.
+
+    Readings: candidates are the partitions whose estimate (Eq. 6 for split,
+    M3 for merge) is below -tau, processed in ascending order of the estimate
+    (ties: lower index, split before merge).  A partition touched by an
+    earlier committed action of the pass (a split child, a merge receiver, a
+    refined neighbour) is skipped.  A split keeps the left child in place and
+    appends the right child; a merge marks the partition dead and the dead
+    are removed at the end of the pass, keeping the order of the rest.
+    Every verify uses the current number of live partitions for Delta O.
+    """
+    lam, tau, alpha = prm.lam, prm.tau, prm.alpha
+    C = [np.array(c, dtype=np.float32) for c in level.centroids]
+    V = list(level.vectors)
+    I = list(level.ids)
+    A = [float(a) for a in A]
+    N0 = len(C)
+    live = list(range(N0))
+    sizes = [v.shape[0] for v in V]
+    cands = []
+    for j in range(N0):
+        s, a = sizes[j], A[j]
+        if s >= 2:
+            e = delta_split_estimate(lam(N0 + 1) - lam(N0), a, lam(s), lam(s / 2.0), alpha)
+            if e < -tau:
+                cands.append((e, j, 0))
+        if s < prm.s_min and N0 > 1:
+            nR = min(prm.refine_radius, N0 - 1)
+            R = nearest(np.array(C), live, C[j].astype(np.float64), nR, exclude=j)
+            rec = [(A[m], a / nR, lam(sizes[m] + s / nR), lam(sizes[m])) for m in R]
+            e = delta_merge_exact(lam(N0 - 1) - lam(N0), a, lam(s), rec)
+            if e < -tau:
+                cands.append((e, j, 1))
+    cands.sort()
+    touched, dead, log = set(), set(), []
+    for e, j, kind in cands:
+        if j in touched or j in dead:
+            continue
+        n_live = len(live)
+        rows, rid, s, a = V[j], I[j], sizes[j], A[j]
+        if kind == 0:
+            by_id = np.argsort(rid, kind="stable")
+            C2 = km.lloyd(rows[by_id], 2, prm.split_iters, split_seed(prm.seed, level_no, j))
+            a2 = km.assign(rows, C2)
+            sL, sR = int((a2 == 0).sum()), int((a2 == 1).sum())
+            if sL == 0 or sR == 0:
+                log.append(("split", j, e, None, False))
+                continue
+            d = delta_split_exact(lam(n_live + 1) - lam(n_live), a, lam(s), alpha * a, lam(sL), alpha * a, lam(sR))
+            ok = decide(d, tau)
+            log.append(("split", j, e, d, ok))
+            if not ok:
+                continue
+            jn = len(C)
+            C[j], V[j], I[j] = C2[0], rows[a2 == 0], rid[a2 == 0]
+            C.append(C2[1])
+            V.append(rows[a2 == 1])
+            I.append(rid[a2 == 1])
+            A[j] = alpha * a
+            A.append(alpha * a)
+            sizes[j] = sL
+            sizes.append(sR)
+            live.append(jn)
+            if parent_of is not None:
+                parent_of.append(parent_of[j])
+            touched |= {j, jn}
+            if prm.refine and prm.refine_iters > 0:
+                Cn = np.array(C)
+                P = set(nearest(Cn, live, C[j].astype(np.float64), prm.refine_radius))
+                P |= set(nearest(Cn, live, C[jn].astype(np.float64), prm.refine_radius))
+                P = sorted(P)
+                tmp = km.Level(np.array([C[p] for p in P]), [V[p] for p in P], [I[p] for p in P])
+                refine(tmp, list(range(len(P))), prm.refine_iters)
+                for n, p in enumerate(P):
+                    C[p], V[p], I[p] = tmp.centroids[n], tmp.vectors[n], tmp.ids[n]
+                    sizes[p] = V[p].shape[0]
+                touched |= set(P)
+        else:
+            others = [m for m in live if m != j]
+            Co = np.array([C[m] for m in others])
+            am = km.assign(rows, Co) if s > 0 else np.zeros(0, np.int64)
+            recv = {}
+            for r, k in enumerate(am):
+                recv.setdefault(others[int(k)], []).append(r)
+            rec = [(A[m], a * len(rs) / s, lam(sizes[m] + len(rs)), lam(sizes[m])) for m, rs in sorted(recv.items())]
+            d = delta_merge_exact(lam(n_live - 1) - lam(n_live), a, lam(s), rec)
+            ok = decide(d, tau)
+            log.append(("merge", j, e, d, ok))
+            if not ok:
+                continue
+            for m, rs in sorted(recv.items()):
+                rs = np.array(rs, dtype=np.int64)
+                V[m] = np.concatenate([V[m], rows[rs]])
+                I[m] = np.concatenate([I[m], rid[rs]])
+                A[m] += a * len(rs) / s
+                sizes[m] += len(rs)
+                touched.add(m)
+            dead.add(j)
+            live.remove(j)
+            touched.add(j)
+    keep = [j for j in range(len(C)) if j not in dead]
+    level.centroids = np.array([C[j] for j in keep], dtype=np.float32).reshape(len(keep), -1)
+    level.vectors = [V[j] for j in keep]
+    level.ids = [I[j] for j in keep]
+    if parent_of is not None:
+        parent_of[:] = [parent_of[j] for j in keep]
+    return log, keep
+
+
+def maintain(levels, hits, window, prm):
+    """The bottom-up maintenance pass of Sec. 4 over every level; returns the action logs.
+
+    hits[l] are the access counts of level l's partitions over the last
+    `window` queries (A = hits / |W|, Stage 0).  After the leaves change, the
+    parent level is rebuilt from the parent of every surviving leaf (split
+    children stay with their parent, merged leaves leave it), then the parent
+    level runs its own pass (Stage 4).
+    """
+    logs = []
+    if len(levels) == 1:
+        log, _ = maintain_level(levels[0], np.asarray(hits[0]) / window, prm, 0)
+        return [log]
+    n_leaf = levels[0].n_part
+    parent_of = [0] * n_leaf
+    for p, leaves in enumerate(levels[1].ids):
+        for lf in leaves:
+            parent_of[int(lf)] = p
+    log0, keep = maintain_level(levels[0], np.asarray(hits[0]) / window, prm, 0, parent_of=parent_of)
+    logs.append(log0)
+    P1 = levels[1].n_part
+    members = [[] for _ in range(P1)]
+    for lf, p in enumerate(parent_of):
+        members[p].append(lf)
+    C0 = levels[0].centroids
+    levels[1] = km.Level(levels[1].centroids, [C0[np.array(m, dtype=np.int64)] if m else np.zeros((0, C0.shape[1]), np.float32) for m in members],
+                         [np.array(m, dtype=np.int64) for m in members])
+    log1, _ = maintain_level(levels[1], np.asarray(hits[1]) / window, prm, 1)
+    logs.append(log1)
+    return logs

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIME
 EXPORTS = [
     "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load",
     "qk_search", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_get_hits", "qk_cap_fraction",
-    "qk_kmeans_step", "qk_kmeans_step_noalloc",
+    "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain",
 ]
 
 
@@ -34,6 +34,20 @@ class QkConfig(C.Structure):
         ("f_M_leaf", C.c_double), ("f_M_parent", C.c_double), ("tau_rho", C.c_double),
         ("upper_recall", C.c_double),
     ]
+
+
+class QkMaintParams(C.Structure):
+    _fields_ = [
+        ("lambda_sizes", C.POINTER(C.c_double)), ("lambda_us", C.POINTER(C.c_double)),
+        ("lambda_points", C.c_int32), ("refine_radius", C.c_int32), ("refine_iters", C.c_int32),
+        ("split_iters", C.c_int32), ("s_min", C.c_int32), ("refine", C.c_int32),
+        ("tau_us", C.c_double), ("alpha", C.c_double), ("window", C.c_int64),
+    ]
+
+
+class QkMaintAction(C.Structure):
+    _fields_ = [("level", C.c_int32), ("kind", C.c_int32), ("partition", C.c_int32),
+                ("committed", C.c_int32), ("estimate", C.c_double), ("delta", C.c_double)]
 
 
 class QkError(RuntimeError):
@@ -64,6 +78,8 @@ def _load():
         "qk_cap_fraction": (i32, [i32, i32, vp, vp, i64, vp, vp]),
         "qk_kmeans_step": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp]),
         "qk_kmeans_step_noalloc": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp]),
+        "qk_maintain": (i32, [vp, C.POINTER(QkMaintParams), C.POINTER(QkMaintAction), i32,
+                              C.POINTER(C.c_int32), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

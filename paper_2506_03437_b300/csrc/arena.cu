@@ -8,10 +8,11 @@
 namespace qk {
 
 __global__ void histogram_kernel(const int32_t* __restrict__ lab, int64_t n, int32_t K, int32_t* __restrict__ counts,
-                                 int32_t* __restrict__ status) {
+                                 int32_t* __restrict__ status, bool skip_unlabelled) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t c = lab[i];
+    if (c == -1 && skip_unlabelled) continue;
     if (c < 0 || c >= K) {
       atomicExch(status, DEV_BAD_ARG);
       continue;
@@ -30,6 +31,7 @@ __global__ void scatter_kernel(const float* __restrict__ X, const int64_t* __res
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = w; r < n; r += nw) {
     int32_t c = lab[r];
+    if (c < 0) continue;   // unlabelled rows (reserved arena rows) are left out
     int64_t pos = 0;
     if (lane == 0) pos = off[c] + atomicAdd(&cursor[c], 1);
     pos = __shfl_sync(0xffffffffu, pos, 0);
@@ -41,11 +43,11 @@ __global__ void scatter_kernel(const float* __restrict__ X, const int64_t* __res
 }
 
 qk_status launch_histogram(const int32_t* lab, int64_t n, int32_t K, int32_t* counts, int32_t* status,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool skip_unlabelled) {
   if (n <= 0) return QK_OK;
   int64_t grid = (n + 255) / 256;
   if (grid > 148 * 32) grid = 148 * 32;
-  histogram_kernel<<<(unsigned)grid, 256, 0, s>>>(lab, n, K, counts, status);
+  histogram_kernel<<<(unsigned)grid, 256, 0, s>>>(lab, n, K, counts, status, skip_unlabelled);
   QK_CUDA(cudaGetLastError());
   return QK_OK;
 }

@@ -29,7 +29,7 @@ qk_status launch_kmeans_update(const float* X, int64_t n, int d, const int32_t* 
                                float* C_new, double* sums, int32_t* counts, cudaStream_t s);
 qk_status launch_gather_rows(const float* X, int d, const int64_t* rows, int K, float* out, cudaStream_t s);
 qk_status launch_histogram(const int32_t* lab, int64_t n, int32_t K, int32_t* counts, int32_t* status,
-                           cudaStream_t s);
+                           cudaStream_t s, bool skip_unlabelled);
 qk_status launch_scatter(const float* X, const int64_t* ids, int64_t n, int d, const int32_t* lab,
                          const int64_t* off, int32_t* cursor, float* vec, int64_t* ids_out, cudaStream_t s);
 
@@ -167,13 +167,13 @@ static qk_status group_rows(const float* rows, const int64_t* ids, int64_t n, in
                             int32_t K, bool slack, int32_t* status, float** vec, int64_t** ids_out,
                             int64_t** off, int32_t** size, std::vector<int64_t>& h_off,
                             std::vector<int32_t>& h_size, std::vector<int64_t>* h_cap, int64_t* cap_rows,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool skip_unlabelled) {
   Tmp tc;
   int32_t* counts = nullptr;
   QK_TRY(tc.alloc<int32_t>(K, &counts));
   QK_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * K, s));
   QK_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
-  QK_TRY(launch_histogram(lab, n, K, counts, status, s));
+  QK_TRY(launch_histogram(lab, n, K, counts, status, s, skip_unlabelled));
   h_size.assign(K, 0);
   int32_t st = 0;
   QK_CUDA(cudaMemcpyAsync(h_size.data(), counts, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s));
@@ -205,15 +205,17 @@ static qk_status group_rows(const float* rows, const int64_t* ids, int64_t n, in
   return QK_OK;
 }
 
-// Installs a partitioning given by device arrays (the common end of build and load).
-static qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, const float* C0,
-                         const int32_t* leaf_of_row, const float* C1, const int32_t* parent_of_leaf,
-                         cudaStream_t s) {
+// Installs a partitioning given by device arrays (the common end of build,
+// load and maintain).  With skip_unlabelled, rows labelled -1 are left out
+// (maintain passes the whole arena, reserved rows included).
+qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, const float* C0,
+                  const int32_t* leaf_of_row, const float* C1, const int32_t* parent_of_leaf, cudaStream_t s,
+                  bool skip_unlabelled) {
   const int d = ix->cfg.d;
   const int32_t N0 = ix->cfg.n_leaf, N1 = ix->cfg.n_parent;
   free_structure(ix);
   QK_TRY(group_rows(X, ids, n, d, leaf_of_row, N0, true, ix->status, &ix->vec0, &ix->ids0, &ix->off0,
-                    &ix->size0, ix->h_off0, ix->h_size0, &ix->h_cap_part0, &ix->cap0, s));
+                    &ix->size0, ix->h_off0, ix->h_size0, &ix->h_cap_part0, &ix->cap0, s, skip_unlabelled));
   QK_TRY(dalloc(&ix->cent0, (size_t)N0 * d));
   QK_CUDA(cudaMemcpyAsync(ix->cent0, C0, sizeof(float) * (size_t)N0 * d, cudaMemcpyDeviceToDevice, s));
   QK_TRY(dalloc(&ix->hits0, (size_t)N0));
@@ -227,7 +229,7 @@ static qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64
     QK_CUDA(cudaMemcpyAsync(leaf_ids, seq.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
     int64_t cap1 = 0;
     QK_TRY(group_rows(C0, leaf_ids, N0, d, parent_of_leaf, N1, false, ix->status, &ix->vec1, &ix->ids1,
-                      &ix->off1, &ix->size1, ix->h_off1, ix->h_size1, nullptr, &cap1, s));
+                      &ix->off1, &ix->size1, ix->h_off1, ix->h_size1, nullptr, &cap1, s, false));
     QK_TRY(dalloc(&ix->cent1, (size_t)N1 * d));
     QK_CUDA(cudaMemcpyAsync(ix->cent1, C1, sizeof(float) * (size_t)N1 * d, cudaMemcpyDeviceToDevice, s));
     QK_TRY(dalloc(&ix->hits1, (size_t)N1));
@@ -253,6 +255,7 @@ static qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64
   ix->n = n;
   ix->n_leaf = N0;
   ix->n_parent = N1;
+  ix->queries_seen = 0;
   ix->ready = true;
   return QK_OK;
 }
@@ -276,22 +279,27 @@ static void splitmix_init_rows(int64_t n, int32_t K, uint64_t seed, std::vector<
 }
 
 // Lloyd k-means of n device rows into K centroids (device, K x d) and the
-// final assignment (device, n).
-static qk_status kmeans(const float* X, int64_t n, int d, int32_t K, int iters, uint64_t seed, float* C,
-                        int32_t* assign, cudaStream_t s) {
-  std::vector<int64_t> init;
-  splitmix_init_rows(n, K, seed, init);
+// final assignment (device, n).  Starts from the seeded rows, or from C_init
+// (device, K x d) when it is given.
+qk_status kmeans(const float* X, int64_t n, int d, int32_t K, int iters, uint64_t seed, float* C, int32_t* assign,
+                 cudaStream_t s, const float* C_init) {
   Tmp t_rows, t_c2, t_sums, t_counts;
   int64_t* rows = nullptr;
   float* C2 = nullptr;
   double* sums = nullptr;
   int32_t* counts = nullptr;
-  QK_TRY(t_rows.alloc<int64_t>(K, &rows));
   QK_TRY(t_c2.alloc<float>((size_t)K * d, &C2));
   QK_TRY(t_sums.alloc<double>((size_t)K * d, &sums));
   QK_TRY(t_counts.alloc<int32_t>(K, &counts));
-  QK_CUDA(cudaMemcpyAsync(rows, init.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, s));
-  QK_TRY(launch_gather_rows(X, d, rows, K, C, s));
+  if (C_init) {
+    QK_CUDA(cudaMemcpyAsync(C, C_init, sizeof(float) * (size_t)K * d, cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::vector<int64_t> init;
+    splitmix_init_rows(n, K, seed, init);
+    QK_TRY(t_rows.alloc<int64_t>(K, &rows));
+    QK_CUDA(cudaMemcpyAsync(rows, init.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, s));
+    QK_TRY(launch_gather_rows(X, d, rows, K, C, s));
+  }
   for (int it = 0; it < iters; ++it) {
     QK_TRY(launch_kmeans_assign(X, n, d, C, K, assign, nullptr, s));
     QK_TRY(launch_kmeans_update(X, n, d, assign, C, K, C2, sums, counts, s));
@@ -502,15 +510,15 @@ qk_status qk_build(qk_index* ix, const float* x, const int64_t* ids, int64_t n, 
   int32_t* a0 = nullptr;
   QK_TRY(tc0.alloc<float>((size_t)N0 * d, &C0));
   QK_TRY(ta0.alloc<int32_t>((size_t)n, &a0));
-  QK_TRY(kmeans(X, n, d, N0, ix->cfg.kmeans_iters, ix->cfg.seed, C0, a0, s));
+  QK_TRY(kmeans(X, n, d, N0, ix->cfg.kmeans_iters, ix->cfg.seed, C0, a0, s, nullptr));
   float* C1 = nullptr;
   int32_t* a1 = nullptr;
   if (N1 > 0) {
     QK_TRY(tc1.alloc<float>((size_t)N1 * d, &C1));
     QK_TRY(ta1.alloc<int32_t>((size_t)N0, &a1));
-    QK_TRY(kmeans(C0, N0, d, N1, ix->cfg.kmeans_iters, ix->cfg.seed + 1, C1, a1, s));
+    QK_TRY(kmeans(C0, N0, d, N1, ix->cfg.kmeans_iters, ix->cfg.seed + 1, C1, a1, s, nullptr));
   }
-  return install(ix, X, I, n, C0, a0, C1, a1, s);
+  return install(ix, X, I, n, C0, a0, C1, a1, s, false);
 }
 
 qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, const float* leaf_centroids,
@@ -539,7 +547,7 @@ qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, c
     QK_TRY(in_device(parent_centroids, (size_t)N1 * d, tc1, &C1, s));
     QK_TRY(in_device(parent_of_leaf, (size_t)N0, ta1, &a1, s));
   }
-  return install(ix, X, I, n, C0, a0, C1, a1, s);
+  return install(ix, X, I, n, C0, a0, C1, a1, s, false);
 }
 
 qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
@@ -634,6 +642,7 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
   a.kcap = std::max({k, a.k1, a.M_root});
   a.mcap = std::max({a.M_root, a.k1, 1});
   QK_TRY(launch_search(a, s));
+  ix->queries_seen += nq;
   if (!all_dev) {
     if (!ids_dev) QK_CUDA(cudaMemcpyAsync(out_ids, dids, bi, cudaMemcpyDeviceToHost, s));
     if (!dist_dev) QK_CUDA(cudaMemcpyAsync(out_dist, ddist, bd, cudaMemcpyDeviceToHost, s));

@@ -112,4 +112,15 @@ struct qk_index {
   qk::Buffer stage_in, stage_out;
   // id -> (partition, slot) for deletes
   std::unordered_map<int64_t, int64_t> where;
+  int64_t queries_seen = 0;      // searched queries since the last install/maintain (the window |W|)
 };
+
+namespace qk {
+// Shared by capi.cu and maintain.cu.
+qk_status kmeans(const float* X, int64_t n, int d, int32_t K, int iters, uint64_t seed, float* C, int32_t* assign,
+                 cudaStream_t s, const float* C_init);
+qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, const float* C0,
+                  const int32_t* leaf_of_row, const float* C1, const int32_t* parent_of_leaf, cudaStream_t s,
+                  bool skip_unlabelled);
+bool is_device_ptr(const void* p);
+}  // namespace qk

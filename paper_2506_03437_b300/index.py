@@ -92,6 +92,25 @@ class Index:
                                 L.ptr(oi), L.ptr(od), L.ptr(on), L.ptr(orr), L.stream_ptr(stream)))
         return out
 
+    def maintain(self, lam_sizes, lam_us, tau_us=0.25, alpha=0.9, refine_radius=50, refine_iters=1,
+                 split_iters=10, s_min=0, refine=True, window=0, stream=None):
+        """Runs the maintenance pass; returns the list of considered actions as dicts."""
+        ls = np.ascontiguousarray(lam_sizes, np.float64)
+        lu = np.ascontiguousarray(lam_us, np.float64)
+        p = L.QkMaintParams()
+        p.lambda_sizes = ls.ctypes.data_as(C.POINTER(C.c_double))
+        p.lambda_us = lu.ctypes.data_as(C.POINTER(C.c_double))
+        p.lambda_points = int(ls.shape[0])
+        p.refine_radius, p.refine_iters, p.split_iters = refine_radius, refine_iters, split_iters
+        p.s_min, p.refine, p.tau_us, p.alpha, p.window = s_min, int(bool(refine)), tau_us, alpha, window
+        cap = 1 << 16
+        log = (L.QkMaintAction * cap)()
+        n = C.c_int32()
+        L.check(L.lib.qk_maintain(self._h, C.byref(p), log, cap, C.byref(n), L.stream_ptr(stream)))
+        return [dict(level=a.level, kind=("split", "merge")[a.kind], partition=a.partition,
+                     committed=bool(a.committed), estimate=a.estimate, delta=a.delta)
+                for a in log[:min(n.value, cap)]]
+
     def check(self, stream=None):
         """Waits for this index's kernels on `stream`; raises if a device check failed."""
         L.check(L.lib.qk_check(self._h, L.stream_ptr(stream)))

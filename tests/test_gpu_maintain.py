@@ -1,0 +1,110 @@
+"""GPU parity of the maintenance pass (Sec. 4) against the oracle."""
+
+import numpy as np
+import pytest
+
+from oracle import aps, kmeans, knn, maintenance
+
+from .parity import same_topk
+from .test_gpu_search import make_index
+from .test_oracle_maintain import example_lambda, example_level
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def I():
+    from paper_2506_03437_b300 import index
+    return index
+
+
+def test_worked_example_on_gpu(I):
+    """Sec. 4's example: P2 splits 450/50 (Delta = +5 us, rejected), P1 250/250 (Delta = -5 us, committed)."""
+    g, pts = example_lambda()
+    X, ids, C, lab = example_level()
+    ix = I.Index(32, n_leaf=2, seed=1234)
+    ix.load(X, ids, C, lab.astype(np.int32))
+    # 10 queries land in each partition; with |W| = 100 that is A = 0.10 for both
+    Q = np.concatenate([np.repeat(C[:1], 10, 0), np.repeat(C[1:], 10, 0)])
+    ix.search(Q, 5, recall_target=0.0, nprobe=1)
+    assert ix.hits(0).tolist() == [10, 10]
+    log = ix.maintain(pts[:, 0], pts[:, 1], tau_us=g["tau"], alpha=g["alpha"], refine=False, window=100)
+    assert [(a["kind"], a["partition"], a["committed"]) for a in log] == [("split", 0, False), ("split", 1, True)]
+    assert abs(log[0]["estimate"] - g["delta_estimate"]) < 1e-9
+    assert abs(log[0]["delta"] - g["P2_delta"]) < 1e-9 and abs(log[1]["delta"] - g["P1_delta"]) < 1e-9
+    sizes, _, _ = ix.export_level(0)
+    assert sizes.tolist() == [500, 250, 250]
+
+
+def scenario(seed=3, d=32):
+    g = np.random.default_rng(seed)
+    cen = (3 * g.standard_normal((40, d))).astype(np.float32)
+    sizes = (3000 / np.arange(1, 41) ** 0.8).astype(int) + 20
+    X = np.concatenate([c + 0.05 * g.standard_normal((s, d)) for c, s in zip(cen, sizes)]).astype(np.float32)
+    ids = np.arange(X.shape[0], dtype=np.int64)
+    qlab = np.minimum(g.zipf(1.3, 600) - 1, 39)
+    Q = (cen[qlab] + 0.05 * g.standard_normal((600, d))).astype(np.float32)
+    return X, ids, Q
+
+
+def test_maintenance_pass_matches_oracle(I):
+    X, ids, Q = scenario()
+    levels = kmeans.build_index(X, ids, 24, 5, iters=5, seed=11)
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.25, f_M_parent=1.0, seed=1234)
+    # Stage 0 statistics: the same queries on both sides
+    ix.search(Q, 10, recall_target=0.0, nprobe=2)
+    res = aps.search(levels, Q, aps.Params(k=10, recall_target=0.0, nprobe=2, f_M=(0.25, 1.0)))
+    h0 = np.bincount(np.concatenate([np.array(s) for s in res["scanned"][0]]), minlength=24)
+    h1 = np.bincount(np.concatenate([np.array(s) for s in res["scanned"][1]]), minlength=5)
+    assert np.array_equal(ix.hits(0), h0) and np.array_equal(ix.hits(1), h1)
+    lam = maintenance.Latency([0, 1000], [5.0, 55.0])
+    prm = maintenance.MaintParams(lam, tau=0.01, alpha=0.9, refine_radius=4, s_min=120, split_iters=8, seed=1234)
+    logs = maintenance.maintain(levels, [h0, h1], 600, prm)
+    got = ix.maintain([0, 1000], [5.0, 55.0], tau_us=0.01, alpha=0.9, refine_radius=4, s_min=120, split_iters=8,
+                      window=600)
+    want = [(lv, k, j, ok, e, dl) for lv, lg in enumerate(logs) for k, j, e, dl, ok in lg]
+    if len(got) != len(want) or any((a["level"], a["kind"], a["partition"], a["committed"]) != w[:4]
+                                    for a, w in zip(got, want)):
+        print("gpu   :", [(a["level"], a["kind"], a["partition"], a["committed"], a["estimate"], a["delta"]) for a in got])
+        print("oracle:", want)
+        print("gpu sizes", ix.export_level(0)[0].tolist(), ix.export_level(1)[0].tolist())
+        print("orc sizes", levels[0].sizes().tolist(), levels[1].sizes().tolist())
+    assert len(got) == len(want)
+    assert any(w[3] for w in want) and any(w[1] == "merge" for w in want)
+    for a, (lv, k, j, ok, e, dl) in zip(got, want):
+        assert (a["level"], a["kind"], a["partition"], a["committed"]) == (lv, k, j, ok)
+        assert abs(a["estimate"] - e) <= 1e-6 * max(1.0, abs(e))
+        if dl is not None:
+            assert abs(a["delta"] - dl) <= 1e-6 * max(1.0, abs(dl))
+    # the new structure: same partitions (as id sets), centroids to FP32 rounding
+    sizes, cents, gids = ix.export_level(0)
+    assert sizes.tolist() == levels[0].sizes().tolist()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for j in range(len(sizes)):
+        assert set(gids[off[j]:off[j + 1]].tolist()) == set(levels[0].ids[j].tolist())
+    np.testing.assert_allclose(cents, levels[0].centroids, rtol=1e-5, atol=1e-5)
+    s1, c1, g1 = ix.export_level(1)
+    assert s1.tolist() == levels[1].sizes().tolist()
+    off = np.concatenate([[0], np.cumsum(s1)])
+    for p in range(len(s1)):
+        assert set(g1[off[p]:off[p + 1]].tolist()) == set(levels[1].ids[p].tolist())
+    # every vector is still there: a full scan is exact kNN
+    info = ix.info()
+    assert info["n"] == X.shape[0] and info["n_leaf"] == levels[0].n_part
+    gi, gd, gn, gr = ix.search(Q[:20], 10, recall_target=0.0, nprobe=info["n_leaf"])
+    D, Ix = knn.knn(X, ids, Q[:20], 10)
+    for j in range(20):
+        assert same_topk(gi[j], gd[j], Ix[j], D[j])
+
+
+def test_maintain_needs_statistics(I):
+    from paper_2506_03437_b300 import _lib as L
+    X, ids, Q = scenario()
+    levels = kmeans.build_index(X[:3000], ids[:3000], 6, 0, iters=2, seed=1)
+    ix = make_index(I, X[:3000], ids[:3000], levels)
+    with pytest.raises(L.QkError) as e:
+        ix.maintain([0, 1000], [5.0, 55.0])
+    assert e.value.status == L.ERR_STATE
+    with pytest.raises(L.QkError) as e:
+        ix.maintain([10, 5], [1.0, 2.0], window=10)
+    assert e.value.status == L.ERR_ARG
