@@ -45,10 +45,10 @@ __host__ __device__ inline int next_pow2(int x) {
 
 // Shared-memory layout, computed identically on host and device.
 struct SmemLayout {
-  size_t stages, bars, q, sd, sid, cpart, cD, ct, cp, csc, red, total;
+  size_t stages, bars, q, sd, sid, cpart, cD, ct, cp, csc, total;
   int sortn;
   __host__ __device__ SmemLayout(int tile_floats, int d, int kcap, int mcap) {
-    sortn = next_pow2(kcap + kBufCap);
+    sortn = 2 * kcap + kBufCap;   // R, the survivor buffer, the merge output
     size_t o = 0;
     auto take = [&](size_t bytes, size_t align) {
       o = (o + align - 1) / align * align;
@@ -66,13 +66,16 @@ struct SmemLayout {
     ct = take(sizeof(double) * mcap, 16);
     cp = take(sizeof(double) * mcap, 16);
     csc = take(sizeof(uint8_t) * mcap, 16);
-    red = take(sizeof(double) * 2 * kWarps + 64, 16);
     total = o;
   }
 };
 
 struct Scalars {
   int64_t qi;
+  double rho;        // current k-th radius (APS)
+  double r;          // current recall estimate (APS)
+  int32_t next;      // next candidate position (APS)
+  int32_t go;        // APS continues
   int32_t buf_count;
   int32_t r_count;
   float thr;
@@ -95,7 +98,6 @@ struct Block {
   double* ct;
   double* cp;
   uint8_t* csc;
-  double* red;
   Scalars* s;
   uint32_t consumed;  // tiles consumed (uniform across the CTA)
   int tid, lane, warp;
@@ -120,49 +122,6 @@ struct Block {
     }
   }
 
-  // ---------------------------------------------------------- reductions
-  __device__ double block_sum(double v) {
-    v = warp_sum_d(v);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) t += red[w];
-    __syncthreads();
-    return t;
-  }
-  __device__ double block_prod(double v) {
-    v = warp_prod_d(v);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 1.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) t *= red[w];
-    __syncthreads();
-    return t;
-  }
-  // arg-max of v over the CTA, ties to the lower index; returns the index
-  __device__ int block_argmax(double v, int i) {
-    warp_argmax(v, i);
-    int* ri = reinterpret_cast<int*>(red + kWarps);
-    if (lane == 0) {
-      red[warp] = v;
-      ri[warp] = i;
-    }
-    __syncthreads();
-    double bv = red[0];
-    int bi = ri[0];
-#pragma unroll
-    for (int w = 1; w < kWarps; ++w) {
-      if (red[w] > bv || (red[w] == bv && ri[w] < bi)) {
-        bv = red[w];
-        bi = ri[w];
-      }
-    }
-    __syncthreads();
-    return bi;
-  }
-
   // -------------------------------------------------------------- top-k
   __device__ static bool key_less(float d1, int64_t i1, float d2, int64_t i2) {
     return d1 < d2 || (d1 == d2 && i1 < i2);
@@ -181,13 +140,41 @@ struct Block {
     __syncthreads();
   }
 
-  // Merges the survivor buffer [K, K + cnt) into R = [0, K).  Called by the
-  // whole CTA with the same cnt.
-  __device__ void merge(int K, int cnt) {
-    int n = next_pow2(K + cnt);
-    for (int i = K + cnt + tid; i < n; i += kThreads) {
-      sd[i] = INFINITY;
-      sid[i] = INT64_MAX;
+  // Sorts the survivor buffer [K, K + cnt) in place.  Up to 32 survivors are
+  // sorted by one warp with shuffles; more by a CTA bitonic network.
+  __device__ void sort_buffer(int K, int cnt) {
+    float* bd = sd + K;
+    int64_t* bi = sid + K;
+    if (cnt <= 32) {
+      if (warp == 0) {
+        float d = lane < cnt ? bd[lane] : INFINITY;
+        int64_t id = lane < cnt ? bi[lane] : INT64_MAX;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+          for (int j = k >> 1; j > 0; j >>= 1) {
+            float od = __shfl_xor_sync(0xffffffffu, d, j);
+            int64_t oi = __shfl_xor_sync(0xffffffffu, id, j);
+            bool take_min = ((lane & j) == 0) == ((lane & k) == 0);
+            bool other_less = key_less(od, oi, d, id);
+            if (take_min ? other_less : (!other_less && (od != d || oi != id))) {
+              d = od;
+              id = oi;
+            }
+          }
+        }
+        if (lane < cnt) {
+          bd[lane] = d;
+          bi[lane] = id;
+        }
+      }
+      __syncthreads();
+      return;
+    }
+    int n = next_pow2(cnt);
+    for (int i = cnt + tid; i < n; i += kThreads) {
+      bd[i] = INFINITY;
+      bi[i] = INT64_MAX;
     }
     __syncthreads();
     for (int k = 2; k <= n; k <<= 1) {
@@ -195,26 +182,73 @@ struct Block {
         for (int i = tid; i < n; i += kThreads) {
           int p = i ^ j;
           if (p > i) {
-            float di = sd[i], dp = sd[p];
-            int64_t ii = sid[i], ip = sid[p];
+            float di = bd[i], dp = bd[p];
+            int64_t ii = bi[i], ip = bi[p];
             bool up = (i & k) == 0;
             bool sw = up ? key_less(dp, ip, di, ii) : key_less(di, ii, dp, ip);
             if (sw) {
-              sd[i] = dp;
-              sd[p] = di;
-              sid[i] = ip;
-              sid[p] = ii;
+              bd[i] = dp;
+              bd[p] = di;
+              bi[i] = ip;
+              bi[p] = ii;
             }
           }
         }
         __syncthreads();
       }
     }
+  }
+
+  // Merges the survivor buffer [K, K + cnt) into the sorted R = [0, K): the
+  // buffer is sorted, then every element of R and of the buffer finds its rank
+  // in the union by binary search in the other list (keys (dist, id) are
+  // unique) and the first K land in R.  Called by the whole CTA with the same cnt.
+  __device__ void merge(int K, int cnt) {
+    sort_buffer(K, cnt);
+    const int rc = s->r_count;
+    const float* bd = sd + K;
+    const int64_t* bi = sid + K;
+    float* od = sd + K + kBufCap;
+    int64_t* oi = sid + K + kBufCap;
+    for (int e = tid; e < rc + cnt; e += kThreads) {
+      float d;
+      int64_t id;
+      int rank;
+      if (e < rc) {
+        d = sd[e];
+        id = sid[e];
+        int lo = 0, hi = cnt;   // buffer elements below (d, id)
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (key_less(bd[mid], bi[mid], d, id)) lo = mid + 1; else hi = mid;
+        }
+        rank = e + lo;
+      } else {
+        int m = e - rc;
+        d = bd[m];
+        id = bi[m];
+        int lo = 0, hi = rc;    // R elements below (d, id)
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (key_less(sd[mid], sid[mid], d, id)) lo = mid + 1; else hi = mid;
+        }
+        rank = m + lo;
+      }
+      if (rank < K) {
+        od[rank] = d;
+        oi[rank] = id;
+      }
+    }
+    __syncthreads();
+    const int nc = rc + cnt < K ? rc + cnt : K;
+    for (int i = tid; i < nc; i += kThreads) {
+      sd[i] = od[i];
+      sid[i] = oi[i];
+    }
     if (tid == 0) {
-      int rc = s->r_count + cnt;
-      s->r_count = rc < K ? rc : K;
+      s->r_count = nc;
       s->buf_count = 0;
-      s->thr = (s->r_count == K) ? sd[K - 1] : INFINITY;
+      s->thr = nc == K ? od[K - 1] : INFINITY;
     }
     __syncthreads();
   }
@@ -273,22 +307,28 @@ struct Block {
       float acc = 0.f;
       if (r < nr) {
         const float4* row = reinterpret_cast<const float4*>(stages + (size_t)st * TILE + (size_t)r * D);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;   // four independent FMA chains
+        if (metric == QK_METRIC_L2) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          float4 x = row[sub + TPR * v];
-          if (metric == QK_METRIC_L2) {
+          for (int v = 0; v < NV; ++v) {
+            float4 x = row[sub + TPR * v];
             float dx = x.x - qv[v].x, dy = x.y - qv[v].y, dz = x.z - qv[v].z, dw = x.w - qv[v].w;
-            acc = fmaf(dx, dx, acc);
-            acc = fmaf(dy, dy, acc);
-            acc = fmaf(dz, dz, acc);
-            acc = fmaf(dw, dw, acc);
-          } else {
-            acc = fmaf(x.x, qv[v].x, acc);
-            acc = fmaf(x.y, qv[v].y, acc);
-            acc = fmaf(x.z, qv[v].z, acc);
-            acc = fmaf(x.w, qv[v].w, acc);
+            a0 = fmaf(dx, dx, a0);
+            a1 = fmaf(dy, dy, a1);
+            a2 = fmaf(dz, dz, a2);
+            a3 = fmaf(dw, dw, a3);
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            float4 x = row[sub + TPR * v];
+            a0 = fmaf(x.x, qv[v].x, a0);
+            a1 = fmaf(x.y, qv[v].y, a1);
+            a2 = fmaf(x.z, qv[v].z, a2);
+            a3 = fmaf(x.w, qv[v].w, a3);
           }
         }
+        acc = (a0 + a1) + (a2 + a3);
       }
 #pragma unroll
       for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -306,7 +346,9 @@ struct Block {
         issue(rows, nrows, t + kStages, g + kStages);
         s->issued = g + kStages + 1;
       }
-      if (buffered > kBufCap - ROWS) {
+      // merge when the buffer could overflow, or as soon as R can first be
+      // filled (the threshold then turns finite and filters the rest)
+      if (buffered > kBufCap - ROWS || (s->r_count < K && s->r_count + buffered >= K)) {
         merge(K, buffered);
         buffered = 0;
       }
@@ -341,7 +383,8 @@ struct Block {
     __syncthreads();
   }
 
-  // t_i = (D_i - D_0) / (2 ||c_i - c_0||) for L2, / ||c_i - c_0|| for IP.
+  // t_i = (D_i - D_0) / (2 ||c_i - c_0||) for L2, / ||c_i - c_0|| for IP, in
+  // FP32 like the distances it comes from (one warp per candidate).
   __device__ void bisector(const DevLevel& lv, int M) {
     const float* c0 = lv.cent + (size_t)cpart[0] * D;
     for (int i = 1 + warp; i < M; i += kWarps) {
@@ -353,56 +396,87 @@ struct Block {
       }
       acc = warp_sum_f(acc);
       if (lane == 0) {
-        double cd = sqrt((double)acc);
-        double num = (double)cD[i] - (double)cD[0];
-        double den = metric == QK_METRIC_L2 ? 2.0 * cd : cd;
-        double t = den > 0.0 ? num / den : 0.0;
-        ct[i] = t > 0.0 ? t : 0.0;
+        float cd = sqrtf(acc);
+        float den = metric == QK_METRIC_L2 ? 2.f * cd : cd;
+        float t = den > 0.f ? (cD[i] - cD[0]) / den : 0.f;
+        ct[i] = t > 0.f ? (double)t : 0.0;
       }
     }
     if (tid == 0) ct[0] = 0.0;
     __syncthreads();
   }
 
-  // p_0 = prod (1 - u_j), p_i = (1 - p_0) u_i / sum u (Eq. 8-9, raw caps for p_0).
-  __device__ void probabilities(int M, double rho) {
+  // ---- the estimator, run by warp 0 only (the FP64 pipe is narrow on this
+  // part, so FP64 work is confined to the cap-volume terms of one warp) ----
+
+  // p_0 = prod (1 - u_j), p_i = (1 - p_0) u_i / sum u (Eq. 8-9, raw caps for
+  // p_0) for every candidate; then r = p_0 + sum of the scanned p_i (R5).
+  __device__ double w0_probabilities(int M, double rho) {
     double su = 0.0, pr = 1.0;
-    for (int i = 1 + tid; i < M; i += kThreads) {
-      double u = beta_mode == QK_BETA_EXACT ? cap_fraction_exact(ct[i], rho, beta_a, beta_lnB)
-                                              : cap_fraction_table(ct[i], rho, beta_table);
+    const double inv = rho > 0.0 ? 1.0 / rho : 0.0;
+    for (int i = 1 + lane; i < M; i += 32) {
+      double u = 0.0;
+      double t = ct[i];
+      if (rho > 0.0 && t < rho) {
+        if (beta_mode == QK_BETA_EXACT) {
+          u = cap_fraction_exact(t, rho, beta_a, beta_lnB);
+        } else {
+          double sc = t * inv;
+          double x = 1.0 - sc * sc;
+          double f = x * (kBetaTablePoints - 1);
+          int j = (int)f;
+          if (j > kBetaTablePoints - 2) j = kBetaTablePoints - 2;
+          double lo = beta_table[j], hi = beta_table[j + 1];
+          u = 0.5 * (lo + (f - j) * (hi - lo));
+        }
+      }
       cp[i] = u;
       su += u;
       pr *= 1.0 - u;
     }
-    double U = block_sum(su);
-    double P0 = block_prod(pr);
-    for (int i = 1 + tid; i < M; i += kThreads) cp[i] = U > 0.0 ? (1.0 - P0) * cp[i] / U : 0.0;
-    if (tid == 0) cp[0] = P0;
-    __syncthreads();
+    const double U = warp_sum_d(su);
+    const double P0 = warp_prod_d(pr);
+    const double c = U > 0.0 ? (1.0 - P0) / U : 0.0;
+    double rs = 0.0;
+    for (int i = 1 + lane; i < M; i += 32) {
+      double p = cp[i] * c;
+      cp[i] = p;
+      if (csc[i]) rs += p;
+    }
+    if (lane == 0) cp[0] = P0;
+    return P0 + warp_sum_d(rs);
   }
 
-  __device__ double recall_estimate(int M) {
-    double v = 0.0;
-    for (int i = 1 + tid; i < M; i += kThreads)
-      if (csc[i]) v += cp[i];
-    return cp[0] + block_sum(v);
-  }
-
-  __device__ int next_candidate(int M) {
-    double bv = -1.0;
-    int bi = 0x7fffffff;
-    for (int i = 1 + tid; i < M; i += kThreads) {
-      if (!csc[i] && (cp[i] > bv || (cp[i] == bv && i < bi))) {
-        bv = cp[i];
+  // The unscanned candidate with the largest p (R6: ties to the lower
+  // position).  p >= 0, so its IEEE bits order like its value and the
+  // comparison runs on the integer pipe.  Returns M if none is left.
+  __device__ int w0_next(int M) {
+    long long bk = -1;
+    int bi = M;
+    for (int i = 1 + lane; i < M; i += 32) {
+      if (csc[i]) continue;
+      long long k = __double_as_longlong(cp[i]);
+      if (k > bk) {
+        bk = k;
         bi = i;
       }
     }
-    return block_argmax(bv, bi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      long long k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+      int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (k2 > bk || (k2 == bk && i2 < bi)) {
+        bk = k2;
+        bi = i2;
+      }
+    }
+    return bi;
   }
 
+  // rho from the current k-th result (R1), in FP32 like the distances.
   __device__ double kth_radius(int K) {
     float dk = sd[K - 1];
-    return sqrt(dk > 0.f ? (double)dk : 0.0);
+    return (double)sqrtf(dk > 0.f ? dk : 0.f);
   }
 
   // Algorithm 1 over the M candidates in (cpart, cD); result set in R.
@@ -432,21 +506,43 @@ struct Block {
       r_out = 1.0;
       return;
     }
-    double rho = kth_radius(K);
-    probabilities(M, rho);
-    double r = recall_estimate(M);
-    while (r < tau && ns < M && !aborted) {
-      int best = next_candidate(M);
+    // warp 0 owns rho, p and r; the CTA follows its decisions through shared memory
+    if (warp == 0) {
+      double rho = kth_radius(K);
+      double r = w0_probabilities(M, rho);
+      int nx = w0_next(M);
+      if (lane == 0) {
+        s->rho = rho;
+        s->r = r;
+        s->next = nx;
+        s->go = (r < tau && ns < M) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    while (s->go && !aborted) {
+      const int best = s->next;
       scan_pos(lv, best, M, K, hits);
       ++ns;
-      double rho2 = kth_radius(K);
-      if (fabs(rho2 - rho) > tau_rho * rho) {
-        rho = rho2;
-        probabilities(M, rho);
+      if (warp == 0) {
+        double rho = s->rho, r = s->r;
+        double rho2 = kth_radius(K);
+        if (fabs(rho2 - rho) > tau_rho * rho) {           // R7: recompute every p
+          rho = rho2;
+          r = w0_probabilities(M, rho);
+        } else {                                          // p unchanged: add the scanned p
+          r += cp[best];
+        }
+        int nx = w0_next(M);
+        if (lane == 0) {
+          s->rho = rho;
+          s->r = r;
+          s->next = nx;
+          s->go = (r < tau && ns < M) ? 1 : 0;
+        }
       }
-      r = recall_estimate(M);
+      __syncthreads();
     }
-    r_out = r;
+    r_out = s->r;
     nprobe_out = ns;
   }
 
@@ -490,7 +586,6 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
   b.ct = reinterpret_cast<double*>(smem + L.ct);
   b.cp = reinterpret_cast<double*>(smem + L.cp);
   b.csc = reinterpret_cast<uint8_t*>(smem + L.csc);
-  b.red = reinterpret_cast<double*>(smem + L.red);
   b.s = &sc;
   b.tid = threadIdx.x;
   b.lane = threadIdx.x & 31;
