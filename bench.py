@@ -41,6 +41,7 @@ F_M_LEAF, F_M_PARENT = 0.1, 0.25
 METRIC = "QPS at recall@10>=0.9 vs FP64 brute force (APS, two-level index)"
 WORKLOAD = "aps_search_1Mx128_1000leaf_32parent_10kq_zipf1.1_k10"
 ORACLE_BUILD_ITERS = 3   # Lloyd iterations of the index the CPU-baseline leg searches
+STORAGE = "f32"
 
 
 # DRAM traffic of one aps_search_kernel launch on the full workload, from the
@@ -155,8 +156,9 @@ def run_ours(args):
     Xd = torch.from_numpy(X).to(dev)
     idd = torch.from_numpy(ids).to(dev)
     Qd = torch.from_numpy(Q).to(dev)
+    storage = {"f32": 0, "bf16": 1, "fp8": 2}[args.storage]
     ix = I.Index(D, n_leaf=N_LEAF, n_parent=N_PARENT, kmeans_iters=ITERS, seed=SEED,
-                 f_M_leaf=F_M_LEAF, f_M_parent=F_M_PARENT)
+                 f_M_leaf=F_M_LEAF, f_M_parent=F_M_PARENT, storage=storage, rerank=args.rerank)
     t0 = time.time()
     ix.build(Xd, idd)
     torch.cuda.synchronize()
@@ -210,7 +212,11 @@ def run_ours(args):
     h1 = ix.hits(1)
     # algorithmic bytes: every (query, partition) item reads the partition's rows once,
     # plus the top partition (32 parent centroids) per query
-    bytes_total = (float((h0 * sizes0).sum()) + float((h1 * sizes1).sum())) * D * 4 + args.steps * NQ * N_PARENT * D * 4
+    eb = {"f32": 4, "bf16": 2, "fp8": 1}[args.storage]
+    bytes_total = (float((h0 * sizes0).sum()) * D * eb + float((h1 * sizes1).sum()) * D * 4
+                   + args.steps * NQ * N_PARENT * D * 4)
+    if args.storage != "f32":   # the re-rank reads rerank * k FP32 rows per query
+        bytes_total += args.steps * NQ * min(1024, args.rerank * K) * D * 4
     bytes_per_launch = bytes_total / args.steps
     avg_launch_s = dev_s / args.steps
     achieved = bytes_per_launch / avg_launch_s / 1e9
@@ -236,12 +242,15 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": round(qps, 1), "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dev_s / args.steps, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f32": "f32", "bf16": "bf16 storage, f32 accumulate + f32 re-rank",
+                      "fp8": "fp8-e4m3 storage, f32 accumulate + f32 re-rank"}[args.storage],
             "data": "synthetic (seeded Gaussian mixture; stands in for Sift1M-shaped data)",
             "config": {"workload": WORKLOAD, "n": N, "d": D, "n_leaf": N_LEAF, "n_parent": N_PARENT,
                        "queries_per_step": NQ, "k": K, "recall_target": tau, "recall_at_10": round(rec, 4),
                        "mean_nprobe": round(mean_nprobe, 2), "f_M": [F_M_LEAF, F_M_PARENT],
                        "tau_rho": 0.01, "upper_recall": 0.99, "beta": "table", "build_s": round(build_s, 2),
+                       "storage": args.storage, "rerank": args.rerank if args.storage != "f32" else None,
                        "l2": "no flush: 640 MB arena > 126 MB L2",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": round(e2e_qps, 1), "unit": "queries/s",
@@ -261,7 +270,7 @@ def run_ours(args):
 def roofline(achieved, peak, peak_kind, launch_s):
     """Roofline of aps_search_kernel: algorithmic bytes = every scanned (query,
     partition) item's rows (s_p * d * 4 bytes) plus the top partition per query."""
-    full = (N, NQ, N_LEAF, N_PARENT) == (1_000_000, 10_000, 1000, 32)
+    full = (N, NQ, N_LEAF, N_PARENT) == (1_000_000, 10_000, 1000, 32) and STORAGE == "f32"
     traffic = TRAFFIC_BYTES if (full and kernel_hash() == TRAFFIC_KERNEL_HASH) else None
     out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
@@ -337,9 +346,13 @@ def main():
     ap.add_argument("--nq", type=int, default=10_000, help="queries per step")
     ap.add_argument("--leaves", type=int, default=1000)
     ap.add_argument("--parents", type=int, default=32)
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"],
+                    help="leaf storage: FP32, or BF16 / FP8 E4M3 with an FP32 re-rank of 4k candidates")
+    ap.add_argument("--rerank", type=int, default=4)
     args = ap.parse_args()
-    global N, N_COMP, NQ, N_LEAF, N_PARENT, WORKLOAD
+    global N, N_COMP, NQ, N_LEAF, N_PARENT, WORKLOAD, STORAGE
     N, NQ, N_LEAF, N_PARENT = args.n, args.nq, args.leaves, args.parents
+    STORAGE = args.storage
     N_COMP = max(1, N // 1000)
     if (N, NQ, N_LEAF, N_PARENT) != (1_000_000, 10_000, 1000, 32):
         WORKLOAD = f"aps_search_{N}x128_{N_LEAF}leaf_{N_PARENT}parent_{NQ}q_zipf1.1_k10"

@@ -49,6 +49,7 @@ typedef enum {
 
 enum { QK_METRIC_L2 = 0, QK_METRIC_IP = 1 };
 enum { QK_BETA_TABLE = 0, QK_BETA_EXACT = 1 };
+enum { QK_STORE_F32 = 0, QK_STORE_BF16 = 1, QK_STORE_FP8 = 2 };
 
 /*
  * Index configuration.  Paper parameters (Sec. 3, Sec. 5, Sec. 8.1):
@@ -63,6 +64,13 @@ enum { QK_BETA_TABLE = 0, QK_BETA_EXACT = 1 };
  *                      interpolation (Sec. 5, "Performance Optimizations");
  *                      QK_BETA_EXACT: evaluated per candidate.
  *   kmeans_iters, seed Lloyd iterations and the SplitMix64 seed of the build.
+ *   storage            QK_STORE_F32: the leaf scan reads the FP32 rows.
+ *                      QK_STORE_BF16 / QK_STORE_FP8: it reads a BF16 copy, or
+ *                      an FP8 E4M3 copy with one scale per partition
+ *                      (s = max|x| / 448), accumulating in FP32, keeps
+ *                      rerank * k candidates and re-ranks them exactly from
+ *                      the FP32 rows.  Upper levels always use FP32.
+ *   rerank             candidate multiple of the low-precision scan (>= 1).
  */
 typedef struct {
   int32_t d;
@@ -76,10 +84,13 @@ typedef struct {
   double f_M_parent;
   double tau_rho;
   double upper_recall;
+  int32_t storage;
+  int32_t rerank;
 } qk_config;
 
 /* Fills `cfg` with the paper's defaults: L2, one level, f_M = 0.1 / 0.25,
- * tau_rho = 0.01, upper_recall = 0.99, table mode, 10 Lloyd iterations. */
+ * tau_rho = 0.01, upper_recall = 0.99, table mode, 10 Lloyd iterations,
+ * FP32 storage, rerank 4. */
 void qk_config_default(qk_config* cfg);
 
 /* Creates an empty index on the current CUDA device.  Errors: QK_ERR_ARG for
@@ -133,7 +144,10 @@ qk_status qk_load(qk_index* index, const float* x, const int64_t* ids, int64_t n
  * Outputs (nq x k, row-major): out_ids, out_dist.  Optional (NULL to skip):
  * out_nprobe[nq] leaf partitions scanned, out_recall[nq] the final estimate r
  * (NaN in fixed-nprobe mode).  Per-partition access counts are accumulated in
- * the index (see qk_get_hits).  NaN in q -> QK_ERR_ARG.
+ * the index (see qk_get_hits).  NaN in q -> QK_ERR_ARG.  With low-precision
+ * storage the leaf scan keeps rerank * k candidates by their approximate
+ * distance (rho is the k-th of them) and the k returned are re-ranked with
+ * exact FP32 distances.  Inner product: rho is ||q - x_k|| of the k-th result.
  */
 qk_status qk_search(qk_index* index, const float* q, int64_t nq, int32_t k, float recall_target,
                     int32_t nprobe, int64_t* out_ids, float* out_dist, int32_t* out_nprobe,
@@ -184,6 +198,14 @@ qk_status qk_delete(qk_index* index, const int64_t* ids, int64_t n, int64_t* n_r
  */
 qk_status qk_export_level(const qk_index* index, int32_t level, int32_t* sizes, float* centroids,
                           int64_t* ids, float* vectors);
+
+/*
+ * Copies the low-precision copy of level 0 to host memory: codes holds every
+ * vector's d elements (2 bytes each for BF16, 1 for FP8) grouped by partition
+ * in partition order, as qk_export_level orders ids; scales[n_leaf] the FP8
+ * scale of every partition (1 for BF16).  QK_ERR_STATE for FP32 storage.
+ */
+qk_status qk_export_quantized(const qk_index* index, uint8_t* codes, float* scales);
 
 /* Copies the access counts of `level` (one int64 per partition, summed over
  * searches since the last reset) to a host array; reset != 0 zeroes them. */

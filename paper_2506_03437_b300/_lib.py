@@ -10,11 +10,12 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libquake_b300.so")
+LIB_PATH = os.environ.get("QK_LIBRARY") or os.path.join(HERE, "libquake_b300.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DUP_ID, ERR_STATE, ERR_UNSUPPORTED, ERR_INTERNAL = range(9)
 METRIC_L2, METRIC_IP = 0, 1
 BETA_TABLE, BETA_EXACT = 0, 1
+STORE_F32, STORE_BF16, STORE_FP8 = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
                 5: "ERR_DUP_ID", 6: "ERR_STATE", 7: "ERR_UNSUPPORTED", 8: "ERR_INTERNAL"}
@@ -22,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIME
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = [
     "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load",
-    "qk_search", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_get_hits", "qk_cap_fraction",
+    "qk_search", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_export_quantized", "qk_get_hits", "qk_cap_fraction",
     "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain",
 ]
 
@@ -32,7 +33,7 @@ class QkConfig(C.Structure):
         ("d", C.c_int32), ("metric", C.c_int32), ("n_leaf", C.c_int32), ("n_parent", C.c_int32),
         ("kmeans_iters", C.c_int32), ("beta_mode", C.c_int32), ("seed", C.c_uint64),
         ("f_M_leaf", C.c_double), ("f_M_parent", C.c_double), ("tau_rho", C.c_double),
-        ("upper_recall", C.c_double),
+        ("upper_recall", C.c_double), ("storage", C.c_int32), ("rerank", C.c_int32),
     ]
 
 
@@ -74,6 +75,7 @@ def _load():
         "qk_insert": (i32, [vp, vp, vp, i64, vp]),
         "qk_delete": (i32, [vp, vp, i64, vp, vp]),
         "qk_export_level": (i32, [vp, i32, vp, vp, vp, vp]),
+        "qk_export_quantized": (i32, [vp, vp, vp]),
         "qk_get_hits": (i32, [vp, i32, vp, i32]),
         "qk_cap_fraction": (i32, [i32, i32, vp, vp, i64, vp, vp]),
         "qk_kmeans_step": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp]),

@@ -45,6 +45,17 @@ qk_status launch_place_rows(const float* X, const int64_t* ids, int64_t n, int d
 qk_status launch_gather_moves(const float* vec, const int64_t* ids, const int64_t* src, int64_t m, int d, float* tvec,
                               int64_t* tids, cudaStream_t s);
 
+qk_status launch_quantize_arena(const float* vec, const int64_t* off, const int32_t* size, int32_t n_part, int d,
+                                int storage, float* scale, unsigned char* lp, cudaStream_t s);
+qk_status launch_quantize_rows(const float* X, int64_t n, int d, const int64_t* dst, const int32_t* part, int storage,
+                               const float* scale, unsigned char* lp, cudaStream_t s);
+qk_status launch_move_bytes(unsigned char* a, const int64_t* src, const int64_t* dst, int64_t m, int rb,
+                            unsigned char* tmp, cudaStream_t s);
+qk_status launch_relayout_bytes(const unsigned char* old_a, const int64_t* old_off, const int64_t* new_off,
+                                const int32_t* size, int32_t n_part, int rb, unsigned char* new_a, cudaStream_t s);
+
+static int elem_bytes(int storage) { return storage == QK_STORE_BF16 ? 2 : (storage == QK_STORE_FP8 ? 1 : 4); }
+
 static thread_local std::string g_err;
 
 void set_error(const std::string& msg) { g_err = msg; }
@@ -157,6 +168,8 @@ static void free_structure(qk_index* ix) {
   dfree(ix->cent1);
   dfree(ix->hits0);
   dfree(ix->hits1);
+  dfree(ix->lp0);
+  dfree(ix->lp_scale0);
   ix->ready = false;
   ix->where.clear();
 }
@@ -218,6 +231,11 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
                     &ix->size0, ix->h_off0, ix->h_size0, &ix->h_cap_part0, &ix->cap0, s, skip_unlabelled));
   QK_TRY(dalloc(&ix->cent0, (size_t)N0 * d));
   QK_CUDA(cudaMemcpyAsync(ix->cent0, C0, sizeof(float) * (size_t)N0 * d, cudaMemcpyDeviceToDevice, s));
+  if (ix->cfg.storage != QK_STORE_F32) {
+    QK_TRY(dalloc(&ix->lp0, (size_t)ix->cap0 * d * elem_bytes(ix->cfg.storage)));
+    QK_TRY(dalloc(&ix->lp_scale0, (size_t)N0));
+    QK_TRY(launch_quantize_arena(ix->vec0, ix->off0, ix->size0, N0, d, ix->cfg.storage, ix->lp_scale0, ix->lp0, s));
+  }
   QK_TRY(dalloc(&ix->hits0, (size_t)N0));
   QK_CUDA(cudaMemsetAsync(ix->hits0, 0, sizeof(unsigned long long) * N0, s));
   if (N1 > 0) {
@@ -350,12 +368,27 @@ static qk_status grow_arena(qk_index* ix, const std::vector<int32_t>& need, cuda
   }
   QK_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
   QK_TRY(launch_relayout(ix->vec0, ix->ids0, ix->off0, doff, ix->size0, N0, d, nvec, nids, s));
+  unsigned char* nlp = nullptr;
+  if (ix->lp0) {
+    const int rb = d * elem_bytes(ix->cfg.storage);
+    st = dalloc(&nlp, (size_t)total * rb);
+    if (st != QK_OK) {
+      dfree(nvec);
+      dfree(nids);
+      return st;
+    }
+    QK_TRY(launch_relayout_bytes(ix->lp0, ix->off0, doff, ix->size0, N0, rb, nlp, s));
+  }
   QK_CUDA(cudaMemcpyAsync(ix->off0, doff, sizeof(int64_t) * N0, cudaMemcpyDeviceToDevice, s));
   QK_CUDA(cudaStreamSynchronize(s));
   dfree(ix->vec0);
   dfree(ix->ids0);
   ix->vec0 = nvec;
   ix->ids0 = nids;
+  if (ix->lp0) {
+    dfree(ix->lp0);
+    ix->lp0 = nlp;
+  }
   std::vector<int64_t> mirror((size_t)total, -1);
   for (int32_t j = 0; j < N0; ++j)
     for (int32_t t = 0; t < ix->h_size0[j]; ++t) mirror[off[j] + t] = ix->h_ids0[ix->h_off0[j] + t];
@@ -427,6 +460,8 @@ void qk_config_default(qk_config* c) {
   c->f_M_parent = 0.25;
   c->tau_rho = 0.01;
   c->upper_recall = 0.99;
+  c->storage = QK_STORE_F32;
+  c->rerank = 4;
 }
 
 const char* qk_last_error(void) { return g_err.c_str(); }
@@ -447,7 +482,8 @@ qk_status qk_create(const qk_config* cfg, qk_index** out) {
   }
   if (cfg->n_leaf < 1 || cfg->n_parent < 0 || cfg->n_parent > cfg->n_leaf || cfg->kmeans_iters < 0 ||
       !(cfg->f_M_leaf > 0) || !(cfg->f_M_parent > 0) || !(cfg->tau_rho >= 0) ||
-      (cfg->beta_mode != QK_BETA_TABLE && cfg->beta_mode != QK_BETA_EXACT)) {
+      (cfg->beta_mode != QK_BETA_TABLE && cfg->beta_mode != QK_BETA_EXACT) || cfg->storage < QK_STORE_F32 ||
+      cfg->storage > QK_STORE_FP8 || cfg->rerank < 1) {
     set_error("invalid configuration");
     return QK_ERR_ARG;
   }
@@ -561,10 +597,6 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
     set_error("fixed-nprobe search needs nprobe >= 1");
     return QK_ERR_ARG;
   }
-  if (ix->cfg.metric == QK_METRIC_IP && recall_target > 0.f) {
-    set_error("APS with inner product is not supported by this build");
-    return QK_ERR_UNSUPPORTED;
-  }
   if (nq == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int d = ix->cfg.d;
@@ -621,7 +653,12 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
     a.M_root = n_candidates(ix->cfg.f_M_parent, ix->n_parent);
     a.k1 = n_candidates(ix->cfg.f_M_leaf, ix->n_leaf);
   }
-  a.k0 = k;
+  const int storage = ix->cfg.storage;
+  a.kq = k;
+  a.k0 = storage == QK_STORE_F32 ? k : std::min(1024, k * std::max(1, ix->cfg.rerank));
+  a.mode0 = storage == QK_STORE_BF16 ? 2 : storage == QK_STORE_FP8 ? 3 : (ix->cfg.metric == QK_METRIC_IP ? 1 : 0);
+  a.lp_vec = ix->lp0;
+  a.lp_scale = ix->lp_scale0;
   a.tau0 = recall_target;
   a.tau1 = ix->cfg.upper_recall;
   a.tau_rho = ix->cfg.tau_rho;
@@ -639,7 +676,7 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
   a.status = ix->status;
   a.diag = ix->diag;
   a.wait_stats = ix->diag + 8;
-  a.kcap = std::max({k, a.k1, a.M_root});
+  a.kcap = std::max({a.k0, a.k1, a.M_root});
   a.mcap = std::max({a.M_root, a.k1, 1});
   QK_TRY(launch_search(a, s));
   ix->queries_seen += nq;
@@ -726,6 +763,8 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   QK_TRY(tdst.alloc<int64_t>((size_t)n, &ddst));
   QK_CUDA(cudaMemcpyAsync(ddst, dst.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
   QK_TRY(launch_place_rows(X, I, n, d, ddst, ix->vec0, ix->ids0, s));
+  if (ix->lp0)   // FP8 rows use their partition's current scale (values beyond it saturate)
+    QK_TRY(launch_quantize_rows(X, n, d, ddst, leaf, ix->cfg.storage, ix->lp_scale0, ix->lp0, s));
   QK_CUDA(cudaMemcpyAsync(ix->size0, cur.data(), sizeof(int32_t) * ix->n_leaf, cudaMemcpyHostToDevice, s));
   QK_CUDA(cudaStreamSynchronize(s));
   for (int64_t r = 0; r < n; ++r) {
@@ -795,6 +834,10 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
     QK_CUDA(cudaMemcpyAsync(ddst, dst.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
     QK_TRY(launch_gather_moves(ix->vec0, ix->ids0, dsrc, m, d, dtv, dtid, s));
     QK_TRY(launch_place_rows(dtv, dtid, m, d, ddst, ix->vec0, ix->ids0, s));
+    if (ix->lp0) {   // the temporary FP32 rows are free again once place_rows ran (same stream)
+      QK_TRY(launch_move_bytes(ix->lp0, dsrc, ddst, m, d * elem_bytes(ix->cfg.storage),
+                               reinterpret_cast<unsigned char*>(dtv), s));
+    }
   }
   QK_CUDA(cudaMemcpyAsync(ix->size0, size.data(), sizeof(int32_t) * ix->n_leaf, cudaMemcpyHostToDevice, s));
   QK_CUDA(cudaStreamSynchronize(s));
@@ -866,6 +909,27 @@ qk_status qk_export_level(const qk_index* ix, int32_t level, int32_t* sizes, flo
   }
   set_error("no such level");
   return QK_ERR_ARG;
+}
+
+qk_status qk_export_quantized(const qk_index* ix, uint8_t* codes, float* scales) {
+  QK_TRY(check_ready(ix));
+  if (!ix->lp0) {
+    set_error("the index stores FP32 only");
+    return QK_ERR_STATE;
+  }
+  const size_t rb = (size_t)ix->cfg.d * elem_bytes(ix->cfg.storage);
+  if (scales) QK_CUDA(cudaMemcpy(scales, ix->lp_scale0, sizeof(float) * ix->n_leaf, cudaMemcpyDeviceToHost));
+  if (codes) {
+    int64_t o = 0;
+    for (int32_t j = 0; j < ix->n_leaf; ++j) {
+      size_t rows = (size_t)ix->h_size0[j];
+      if (rows) QK_CUDA(cudaMemcpy(codes + o * rb, ix->lp0 + ix->h_off0[j] * rb, rows * rb, cudaMemcpyDeviceToHost));
+      o += (int64_t)rows;
+    }
+  }
+  if (scales && ix->cfg.storage == QK_STORE_BF16)
+    for (int32_t j = 0; j < ix->n_leaf; ++j) scales[j] = 1.0f;
+  return QK_OK;
 }
 
 qk_status qk_get_hits(qk_index* ix, int32_t level, int64_t* hits, int32_t reset) {

@@ -44,7 +44,11 @@ struct SearchArgs {
   const float* root = nullptr;   // top-level centroids, scanned as one partition
   int32_t n_root = 0;
   int32_t M_root = 0;            // candidates kept from the root
-  int32_t k0 = 10;               // k at level 0
+  int32_t k0 = 10;               // results kept at level 0 (k, or rerank * k for low-precision scans)
+  int32_t kq = 10;               // k returned
+  int32_t mode0 = 0;             // level-0 rows: 0 FP32 + ids, 1 FP32 + slots, 2 BF16, 3 FP8 (slots)
+  const void* lp_vec = nullptr;  // level-0 low-precision arena
+  const float* lp_scale = nullptr;
   int32_t k1 = 0;                // k' at level 1 (= M of level 0)
   double tau0 = 0.9;             // recall target of level 0
   double tau1 = 0.99;            // recall target of level 1
@@ -89,6 +93,8 @@ struct qk_index {
   int64_t* off0 = nullptr;
   int32_t* size0 = nullptr;
   float* cent0 = nullptr;
+  unsigned char* lp0 = nullptr;  // low-precision copy of the arena (BF16 / FP8)
+  float* lp_scale0 = nullptr;    // FP8 scale per partition
   std::vector<int64_t> h_off0, h_cap_part0;
   std::vector<int32_t> h_size0;
   std::vector<int64_t> h_ids0;   // host mirror of ids0 (arena slot -> id)

@@ -26,6 +26,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "capvol.cuh"
 #include "common.cuh"
 #include "index.cuh"
@@ -82,6 +85,34 @@ struct Scalars {
   uint32_t issued;   // tiles issued so far (thread 0 writes)
 };
 
+// Element types of a scanned row.  load4 returns the 4 consecutive elements
+// starting at element 4 * i as FP32 (FP8 multiplied by the partition scale).
+struct ElemF32 {
+  static constexpr int kBytes = 4;
+  __device__ static float4 load4(const unsigned char* row, int i, float) {
+    return reinterpret_cast<const float4*>(row)[i];
+  }
+};
+struct ElemBF16 {
+  static constexpr int kBytes = 2;
+  __device__ static float4 load4(const unsigned char* row, int i, float) {
+    uint2 u = reinterpret_cast<const uint2*>(row)[i];
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                       __uint_as_float(u.y & 0xffff0000u));
+  }
+};
+struct ElemFP8 {
+  static constexpr int kBytes = 1;
+  __device__ static float4 load4(const unsigned char* row, int i, float scale) {
+    uint32_t u = reinterpret_cast<const uint32_t*>(row)[i];
+    __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3);
+    __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3);
+    float2 a = __half22float2(*reinterpret_cast<__half2*>(&lo));
+    float2 b = __half22float2(*reinterpret_cast<__half2*>(&hi));
+    return make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
+  }
+};
+
 template <int TPR, int NV>
 struct Block {
   static constexpr int D = NV * 4 * TPR;
@@ -108,6 +139,9 @@ struct Block {
   int32_t* status;
   int64_t* diag;
   int64_t qi;
+  const unsigned char* lp_vec;   // level-0 low-precision rows (BF16 or FP8), or NULL
+  const float* lp_scale;         // FP8 scale per level-0 partition
+  float qn;                      // ||q||^2 (inner product radius)
   long long max_wait;   // longest tile wait of this thread, in SM cycles
   bool aborted;         // a tile wait expired (uniform across the CTA)
 
@@ -145,6 +179,61 @@ struct Block {
   __device__ void sort_buffer(int K, int cnt) {
     float* bd = sd + K;
     int64_t* bi = sid + K;
+    if (cnt > 32 && cnt <= 64) {
+      // one warp, two elements per lane (positions 2 lane and 2 lane + 1)
+      if (warp == 0) {
+        float d0 = 2 * lane < cnt ? bd[2 * lane] : INFINITY;
+        int64_t i0 = 2 * lane < cnt ? bi[2 * lane] : INT64_MAX;
+        float d1 = 2 * lane + 1 < cnt ? bd[2 * lane + 1] : INFINITY;
+        int64_t i1 = 2 * lane + 1 < cnt ? bi[2 * lane + 1] : INT64_MAX;
+#pragma unroll
+        for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+          for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 1) {   // the pair (2 lane, 2 lane + 1) sits in this lane
+              bool up = ((2 * lane) & k) == 0;
+              bool sw = up ? key_less(d1, i1, d0, i0) : key_less(d0, i0, d1, i1);
+              if (sw) {
+                float td = d0;
+                int64_t ti = i0;
+                d0 = d1;
+                i0 = i1;
+                d1 = td;
+                i1 = ti;
+              }
+            } else {        // partner positions differ by j: lane ^ (j / 2), same slot
+              int pl = j >> 1;
+              bool lower = (lane & pl) == 0;
+              bool up = ((2 * lane) & k) == 0;
+              bool take_min = lower == up;
+              float od0 = __shfl_xor_sync(0xffffffffu, d0, pl);
+              int64_t oi0 = __shfl_xor_sync(0xffffffffu, i0, pl);
+              float od1 = __shfl_xor_sync(0xffffffffu, d1, pl);
+              int64_t oi1 = __shfl_xor_sync(0xffffffffu, i1, pl);
+              bool l0 = key_less(od0, oi0, d0, i0), l1 = key_less(od1, oi1, d1, i1);
+              if (take_min ? l0 : (!l0 && (od0 != d0 || oi0 != i0))) {
+                d0 = od0;
+                i0 = oi0;
+              }
+              if (take_min ? l1 : (!l1 && (od1 != d1 || oi1 != i1))) {
+                d1 = od1;
+                i1 = oi1;
+              }
+            }
+          }
+        }
+        if (2 * lane < cnt) {
+          bd[2 * lane] = d0;
+          bi[2 * lane] = i0;
+        }
+        if (2 * lane + 1 < cnt) {
+          bd[2 * lane + 1] = d1;
+          bi[2 * lane + 1] = i1;
+        }
+      }
+      __syncthreads();
+      return;
+    }
     if (cnt <= 32) {
       if (warp == 0) {
         float d = lane < cnt ? bd[lane] : INFINITY;
@@ -254,30 +343,41 @@ struct Block {
   }
 
   // ------------------------------------------------------------ the scan
-  __device__ void issue(const float* rows, int32_t nrows, int t, uint32_t g) {
+  // A tile holds ROWS rows of FP32, or as many more narrow rows as fit the same
+  // bytes: RPT = 4 / element bytes rows per thread (1 FP32, 2 BF16, 4 FP8).
+  template <class E>
+  __device__ void issue(const unsigned char* rows, int32_t nrows, int t, uint32_t g) {
+    constexpr int RT = ROWS * (4 / E::kBytes);
     int st = g % kStages;
-    int r0 = t * ROWS;
-    int nr = nrows - r0 < ROWS ? nrows - r0 : ROWS;
-    uint32_t bytes = (uint32_t)nr * D * sizeof(float);
+    int r0 = t * RT;
+    int nr = nrows - r0 < RT ? nrows - r0 : RT;
+    uint32_t bytes = (uint32_t)nr * D * E::kBytes;
     fence_proxy_async();
     mbar_arrive_expect_tx(&bars[st], bytes);
-    bulk_g2s(stages + (size_t)st * TILE, rows + (size_t)r0 * D, bytes, &bars[st]);
+    bulk_g2s(stages + (size_t)st * TILE, rows + (size_t)r0 * D * E::kBytes, bytes, &bars[st]);
   }
 
-  // Scans rows [0, nrows) of `rows` (ids[r] or base_id + r), keeping the K best in R.
+  // Scans rows [0, nrows) of `rows` (element type E; ids[r], or base_id + r
+  // when ids is NULL), keeping the K best in R.  FP8 rows are multiplied by
+  // `scale` as they are read.
   //
   // Every decision that leads to a __syncthreads() is taken on values that are
   // identical in all threads: the survivor count of a tile comes back from the
   // tile's own barrier (__syncthreads_count), so threads that run ahead into
   // the next tile and append its survivors cannot change the merge decision
   // of threads still finishing this one.
-  __device__ void scan(const float* rows, const int64_t* ids, int64_t base_id, int32_t nrows, int K) {
+  template <class E>
+  __device__ void scan(const unsigned char* rows, const int64_t* ids, int64_t base_id, int32_t nrows, int K,
+                       float scale) {
     if (nrows <= 0 || aborted) return;
-    int ntiles = (nrows + ROWS - 1) / ROWS;
+    constexpr int RPT = 4 / E::kBytes;       // rows per thread per tile
+    constexpr int RT = ROWS * RPT;           // rows per tile
+    static_assert(RPT <= TPR, "each row's survivor flag needs its own lane");
+    int ntiles = (nrows + RT - 1) / RT;
     uint32_t g0 = consumed;
     if (tid == 0) {
       int pre = ntiles < kStages ? ntiles : kStages;
-      for (int t = 0; t < pre; ++t) issue(rows, nrows, t, g0 + t);
+      for (int t = 0; t < pre; ++t) issue<E>(rows, nrows, t, g0 + t);
       s->issued = g0 + pre;
     }
     const int r = tid / TPR, sub = tid % TPR;
@@ -303,52 +403,69 @@ struct Block {
         }
         if (waited > max_wait) max_wait = waited;
       }
-      int nr = nrows - t * ROWS < ROWS ? nrows - t * ROWS : ROWS;
-      float acc = 0.f;
-      if (r < nr) {
-        const float4* row = reinterpret_cast<const float4*>(stages + (size_t)st * TILE + (size_t)r * D);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;   // four independent FMA chains
-        if (metric == QK_METRIC_L2) {
+      int nr = nrows - t * RT < RT ? nrows - t * RT : RT;
+      const unsigned char* tile = reinterpret_cast<const unsigned char*>(stages + (size_t)st * TILE);
+      float acc[RPT];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            float4 x = row[sub + TPR * v];
-            float dx = x.x - qv[v].x, dy = x.y - qv[v].y, dz = x.z - qv[v].z, dw = x.w - qv[v].w;
-            a0 = fmaf(dx, dx, a0);
-            a1 = fmaf(dy, dy, a1);
-            a2 = fmaf(dz, dz, a2);
-            a3 = fmaf(dw, dw, a3);
-          }
-        } else {
+      for (int i = 0; i < RPT; ++i) {
+        acc[i] = 0.f;
+        const int rr = r + ROWS * i;
+        if (rr < nr) {
+          const unsigned char* row = tile + (size_t)rr * D * E::kBytes;
+          float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;   // four independent FMA chains
+          if (metric == QK_METRIC_L2) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            float4 x = row[sub + TPR * v];
-            a0 = fmaf(x.x, qv[v].x, a0);
-            a1 = fmaf(x.y, qv[v].y, a1);
-            a2 = fmaf(x.z, qv[v].z, a2);
-            a3 = fmaf(x.w, qv[v].w, a3);
+            for (int v = 0; v < NV; ++v) {
+              float4 x = E::load4(row, sub + TPR * v, scale);
+              float dx = x.x - qv[v].x, dy = x.y - qv[v].y, dz = x.z - qv[v].z, dw = x.w - qv[v].w;
+              a0 = fmaf(dx, dx, a0);
+              a1 = fmaf(dy, dy, a1);
+              a2 = fmaf(dz, dz, a2);
+              a3 = fmaf(dw, dw, a3);
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              float4 x = E::load4(row, sub + TPR * v, scale);
+              a0 = fmaf(x.x, qv[v].x, a0);
+              a1 = fmaf(x.y, qv[v].y, a1);
+              a2 = fmaf(x.z, qv[v].z, a2);
+              a3 = fmaf(x.w, qv[v].w, a3);
+            }
           }
+          acc[i] = (a0 + a1) + (a2 + a3);
         }
-        acc = (a0 + a1) + (a2 + a3);
       }
 #pragma unroll
-      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      float dist = metric == QK_METRIC_L2 ? acc : -acc;
-      bool surv = !tmo && sub == 0 && r < nr && dist <= s->thr;
-      if (surv) {
-        int pos = atomicAdd(&s->buf_count, 1);
-        int64_t rr = (int64_t)t * ROWS + r;
-        sd[K + pos] = dist;
-        sid[K + pos] = ids ? ids[rr] : base_id + rr;
+      for (int o = TPR / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+      // every lane of the group now holds every row's distance; lane sub = i
+      // judges row i, so each thread raises at most one survivor flag
+      bool surv = false;
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        if (sub == i) {
+          const int rr = r + ROWS * i;
+          float dist = metric == QK_METRIC_L2 ? acc[i] : -acc[i];
+          surv = !tmo && rr < nr && dist <= s->thr;
+          if (surv) {
+            int pos = atomicAdd(&s->buf_count, 1);
+            int64_t gr = (int64_t)t * RT + rr;
+            sd[K + pos] = dist;
+            sid[K + pos] = ids ? ids[gr] : base_id + gr;
+          }
+        }
       }
       buffered += __syncthreads_count(surv);
       ++consumed;
       if (tid == 0 && !tmo && t + kStages < ntiles) {
-        issue(rows, nrows, t + kStages, g + kStages);
+        issue<E>(rows, nrows, t + kStages, g + kStages);
         s->issued = g + kStages + 1;
       }
       // merge when the buffer could overflow, or as soon as R can first be
       // filled (the threshold then turns finite and filters the rest)
-      if (buffered > kBufCap - ROWS || (s->r_count < K && s->r_count + buffered >= K)) {
+      if (buffered > kBufCap - RT || (s->r_count < K && s->r_count + buffered >= K)) {
         merge(K, buffered);
         buffered = 0;
       }
@@ -361,7 +478,9 @@ struct Block {
   }
 
   // ---------------------------------------------------- APS on one level
-  __device__ void scan_pos(const DevLevel& lv, int pos, int M, int K, unsigned long long* hits) {
+  // mode: 0 FP32 rows, ids kept; 1 FP32 rows, arena slots kept; 2 BF16 rows,
+  // slots kept; 3 FP8 rows (scaled per partition), slots kept.
+  __device__ void scan_pos(const DevLevel& lv, int pos, int M, int K, unsigned long long* hits, int mode) {
     if (pos < 0 || pos >= M) {            // never expected: record and skip
       if (tid == 0) report(DEV_BAD_INDEX, 1, pos, M);
       __syncthreads();
@@ -375,7 +494,13 @@ struct Block {
     }
     int64_t off = lv.off[part];
     int32_t sz = lv.size[part];
-    scan(lv.vec + off * D, lv.ids + off, 0, sz, K);
+    const unsigned char* f32 = reinterpret_cast<const unsigned char*>(lv.vec + off * D);
+    switch (mode) {
+      case 0: scan<ElemF32>(f32, lv.ids + off, 0, sz, K, 1.f); break;
+      case 1: scan<ElemF32>(f32, nullptr, off, sz, K, 1.f); break;
+      case 2: scan<ElemBF16>(lp_vec + off * D * 2, nullptr, off, sz, K, 1.f); break;
+      default: scan<ElemFP8>(lp_vec + off * D, nullptr, off, sz, K, lp_scale[part]); break;
+    }
     if (tid == 0) {
       csc[pos] = 1;
       if (hits) atomicAdd(&hits[part], 1ull);
@@ -473,42 +598,53 @@ struct Block {
     return bi;
   }
 
-  // rho from the current k-th result (R1), in FP32 like the distances.
-  __device__ double kth_radius(int K) {
-    float dk = sd[K - 1];
-    return (double)sqrtf(dk > 0.f ? dk : 0.f);
+  // rho from the current k-th result (R1), in FP32 like the distances.  For
+  // inner product, rho = ||q - x_k|| = sqrt(||q||^2 + ||x_k||^2 + 2 D_k) with
+  // D_k = -<q, x_k>; x_k is row sid[k-1] of krow (called by warp 0).
+  __device__ double kth_radius(int k, const float* krow) {
+    float dk = sd[k - 1];
+    if (metric == QK_METRIC_L2) return (double)sqrtf(dk > 0.f ? dk : 0.f);
+    const float* x = krow + (size_t)sid[k - 1] * D;
+    float xn = 0.f;
+    for (int j = lane; j < D; j += 32) xn = fmaf(x[j], x[j], xn);
+    xn = warp_sum_f(xn);
+    float r2 = qn + xn + 2.f * dk;
+    return (double)sqrtf(r2 > 0.f ? r2 : 0.f);
   }
 
   // Algorithm 1 over the M candidates in (cpart, cD); result set in R.
   // Returns r (NaN in fixed-nprobe mode) and the number of scanned partitions.
-  __device__ void aps(const DevLevel& lv, int M, int K, double tau, int fixed,
-                      unsigned long long* hits, double& r_out, int& nprobe_out) {
+  // K results are kept (K >= k when low-precision candidates are oversized);
+  // rho and the "R holds k results" rule use the k-th; krow locates result rows
+  // for the inner-product radius; mode selects the scanned rows (see scan_pos).
+  __device__ void aps(const DevLevel& lv, int M, int K, int k, double tau, int fixed, unsigned long long* hits,
+                      int mode, const float* krow, double& r_out, int& nprobe_out) {
     reset_R(K);
     for (int i = tid; i < M; i += kThreads) csc[i] = 0;
     __syncthreads();
     if (fixed > 0) {
       int n = fixed < M ? fixed : M;
-      for (int pos = 0; pos < n && !aborted; ++pos) scan_pos(lv, pos, M, K, hits);
+      for (int pos = 0; pos < n && !aborted; ++pos) scan_pos(lv, pos, M, K, hits, mode);
       r_out = NAN;
       nprobe_out = n;
       return;
     }
     bisector(lv, M);
     int ns = 0;
-    scan_pos(lv, 0, M, K, hits);
+    scan_pos(lv, 0, M, K, hits, mode);
     ns = 1;
-    while (s->r_count < K && ns < M && !aborted) {   // R holds fewer than k: centroid order
-      scan_pos(lv, ns, M, K, hits);
+    while (s->r_count < k && ns < M && !aborted) {   // R holds fewer than k: centroid order
+      scan_pos(lv, ns, M, K, hits, mode);
       ++ns;
     }
     nprobe_out = ns;
-    if (s->r_count < K || aborted) {
+    if (s->r_count < k || aborted) {
       r_out = 1.0;
       return;
     }
     // warp 0 owns rho, p and r; the CTA follows its decisions through shared memory
     if (warp == 0) {
-      double rho = kth_radius(K);
+      double rho = kth_radius(k, krow);
       double r = w0_probabilities(M, rho);
       int nx = w0_next(M);
       if (lane == 0) {
@@ -521,11 +657,11 @@ struct Block {
     __syncthreads();
     while (s->go && !aborted) {
       const int best = s->next;
-      scan_pos(lv, best, M, K, hits);
+      scan_pos(lv, best, M, K, hits, mode);
       ++ns;
       if (warp == 0) {
         double rho = s->rho, r = s->r;
-        double rho2 = kth_radius(K);
+        double rho2 = kth_radius(k, krow);
         if (fabs(rho2 - rho) > tau_rho * rho) {           // R7: recompute every p
           rho = rho2;
           r = w0_probabilities(M, rho);
@@ -544,6 +680,63 @@ struct Block {
     }
     r_out = s->r;
     nprobe_out = ns;
+  }
+
+  // Sorts sd/sid[0, n) by (dist, id) with a CTA bitonic network (pads to a power of two).
+  __device__ void sort_range(int n) {
+    int np = next_pow2(n);
+    for (int i = n + tid; i < np; i += kThreads) {
+      sd[i] = INFINITY;
+      sid[i] = INT64_MAX;
+    }
+    __syncthreads();
+    for (int k = 2; k <= np; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < np; i += kThreads) {
+          int p = i ^ j;
+          if (p > i) {
+            float di = sd[i], dp = sd[p];
+            int64_t ii = sid[i], ip = sid[p];
+            bool up = (i & k) == 0;
+            if (up ? key_less(dp, ip, di, ii) : key_less(di, ii, dp, ip)) {
+              sd[i] = dp;
+              sd[p] = di;
+              sid[i] = ip;
+              sid[p] = ii;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+
+  // Replaces the arena slots in R by ids with exact FP32 distances computed
+  // from the FP32 master rows (the re-rank of low-precision candidates), then
+  // sorts R by (distance, id).
+  __device__ void rerank(const float* vec0, const int64_t* ids0) {
+    const int rc = s->r_count;
+    for (int i = warp; i < rc; i += kWarps) {
+      const float* x = vec0 + (size_t)sid[i] * D;
+      float acc = 0.f;
+      if (metric == QK_METRIC_L2) {
+        for (int j = lane; j < D; j += 32) {
+          float df = x[j] - sq[j];
+          acc = fmaf(df, df, acc);
+        }
+      } else {
+        for (int j = lane; j < D; j += 32) acc = fmaf(x[j], sq[j], acc);
+      }
+      acc = warp_sum_f(acc);
+      __syncwarp();
+      if (lane == 0) {
+        int64_t slot = sid[i];
+        sd[i] = metric == QK_METRIC_L2 ? acc : -acc;
+        sid[i] = ids0[slot];
+      }
+    }
+    __syncthreads();
+    sort_range(rc);
   }
 
   // R -> candidate list of the next level.
@@ -573,6 +766,8 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
   b.beta_table = args.beta_table;
   b.status = args.status;
   b.diag = args.diag;
+  b.lp_vec = static_cast<const unsigned char*>(args.lp_vec);
+  b.lp_scale = args.lp_scale;
   b.qi = -1;
   b.max_wait = 0;
   b.aborted = false;
@@ -612,25 +807,31 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
       int sub = threadIdx.x % TPR;
 #pragma unroll
       for (int v = 0; v < NV; ++v) b.qv[v] = q4[sub + TPR * v];
+      float qn = 0.f;
+      for (int j = b.lane; j < B::D; j += 32) qn = fmaf(b.sq[j], b.sq[j], qn);
+      b.qn = warp_sum_f(qn);
     }
     // top partition: all centroids of the top level
     b.reset_R(args.M_root);
-    b.scan(args.root, nullptr, 0, args.n_root, args.M_root);
+    b.template scan<ElemF32>(reinterpret_cast<const unsigned char*>(args.root), nullptr, 0, args.n_root, args.M_root, 1.f);
     int M = b.take_candidates();
     double r = 0.0;
     int np = 0;
     if (args.L == 2) {
-      b.aps(args.lv[1], M, args.k1, args.tau1, 0, args.hits1, r, np);
+      // level-1 rows are leaf centroids whose id is the leaf index: x_k = cent0[id]
+      b.aps(args.lv[1], M, args.k1, args.k1, args.tau1, 0, args.hits1, 0, args.lv[0].cent, r, np);
       M = b.take_candidates();
     }
-    b.aps(args.lv[0], M, args.k0, args.tau0, args.fixed_nprobe, args.hits0, r, np);
+    b.aps(args.lv[0], M, args.k0, args.kq, args.tau0, args.fixed_nprobe, args.hits0, args.mode0, args.lv[0].vec, r,
+          np);
     if (b.aborted) break;
+    if (args.mode0 != 0) b.rerank(args.lv[0].vec, args.lv[0].ids);
     int rc = sc.r_count;
-    for (int i = threadIdx.x; i < args.k0; i += kThreads) {
+    for (int i = threadIdx.x; i < args.kq; i += kThreads) {
       bool ok = i < rc;
       if (ok && (b.sid[i] < 0 || !(b.sd[i] < INFINITY))) b.report(DEV_BAD_INDEX, 3, i, rc);
-      args.out_dist[qi * args.k0 + i] = ok ? b.sd[i] : INFINITY;
-      args.out_ids[qi * args.k0 + i] = ok ? b.sid[i] : -1;
+      args.out_dist[qi * args.kq + i] = ok ? b.sd[i] : INFINITY;
+      args.out_ids[qi * args.kq + i] = ok ? b.sid[i] : -1;
     }
     if (threadIdx.x == 0) {
       if (args.out_nprobe) args.out_nprobe[qi] = np;

@@ -26,12 +26,14 @@ def _as(a, dtype):
 
 
 def config(d, metric=L.METRIC_L2, n_leaf=1000, n_parent=0, kmeans_iters=10, beta_mode=L.BETA_TABLE,
-           seed=1234, f_M_leaf=0.1, f_M_parent=0.25, tau_rho=0.01, upper_recall=0.99):
+           seed=1234, f_M_leaf=0.1, f_M_parent=0.25, tau_rho=0.01, upper_recall=0.99, storage=L.STORE_F32,
+           rerank=4):
     c = L.QkConfig()
     L.lib.qk_config_default(C.byref(c))
     c.d, c.metric, c.n_leaf, c.n_parent = d, metric, n_leaf, n_parent
     c.kmeans_iters, c.beta_mode, c.seed = kmeans_iters, beta_mode, seed
     c.f_M_leaf, c.f_M_parent, c.tau_rho, c.upper_recall = f_M_leaf, f_M_parent, tau_rho, upper_recall
+    c.storage, c.rerank = storage, rerank
     return c
 
 
@@ -132,6 +134,17 @@ class Index:
         vec = np.empty((nrows, self.d), np.float32) if vectors else None
         L.check(L.lib.qk_export_level(self._h, level, L.ptr(sizes), L.ptr(cents), L.ptr(ids), L.ptr(vec)))
         return (sizes, cents, ids, vec) if vectors else (sizes, cents, ids)
+
+    def export_quantized(self):
+        """(codes grouped like export_level's ids, scale per partition) of the low-precision copy."""
+        inf = self.info()
+        eb = 2 if self.cfg.storage == L.STORE_BF16 else 1
+        codes = np.empty((inf["n"], self.d * eb), np.uint8)
+        scales = np.empty(inf["n_leaf"], np.float32)
+        L.check(L.lib.qk_export_quantized(self._h, L.ptr(codes), L.ptr(scales)))
+        if eb == 2:
+            codes = codes.view(np.uint16)
+        return codes, scales
 
     def insert(self, x, ids, stream=None):
         x, ids = _as(x, np.float32), _as(ids, np.int64)

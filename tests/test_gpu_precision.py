@@ -1,0 +1,103 @@
+"""Low-precision storage (BF16, FP8 E4M3 with per-partition scales), the FP32 re-rank,
+and inner-product APS, against the oracle."""
+
+import numpy as np
+import pytest
+
+from oracle import aps, kmeans, knn, quant
+from paper_2506_03437_b300 import synth
+
+from .parity import compare_search, exact_dist, same_topk
+from .test_gpu_search import load_args
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def I():
+    from paper_2506_03437_b300 import index
+    return index
+
+
+def make(I, X, ids, levels, **cfg):
+    ix = I.Index(X.shape[1], n_leaf=levels[0].n_part, n_parent=levels[1].n_part if len(levels) > 1 else 0, **cfg)
+    ix.load(X, ids, **load_args(levels, X.shape[0]))
+    return ix
+
+
+def codes_by_id(ix):
+    sizes, _, ids = ix.export_level(0)
+    codes, scales = ix.export_quantized()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    part = np.repeat(np.arange(len(sizes)), sizes)
+    return {int(i): (codes[r], part[r]) for r, i in enumerate(ids)}, scales, off
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_quantized_codes_are_bit_exact(I, storage):
+    X, ids, Q = synth.aps_search(seed=31, n=3000, d=64, n_comp=10, sigma=1.0, nq=4)
+    X[5, 3] = 0.0
+    levels = kmeans.build_index(X, ids, 12, 0, iters=2, seed=1)
+    ix = make(I, X, ids, levels, storage=storage)
+    got, scales, _ = codes_by_id(ix)
+    for j in range(12):
+        rows, rid = levels[0].vectors[j], levels[0].ids[j]
+        if storage == 2:
+            s = quant.partition_scale(rows)
+            assert scales[j] == s
+            want = quant.quantize_e4m3(rows, s)
+        else:
+            want = quant.quantize_bf16(rows)
+        for r, i in enumerate(rid[::5]):
+            assert np.array_equal(got[int(i)][0], want[::5][r]), (j, int(i))
+    # inserted rows use their partition's existing scale (saturating beyond it)
+    if storage == 2:
+        nx = (X[:40] * 3).astype(np.float32)
+        ni = np.arange(90_000, 90_040, dtype=np.int64)
+        ix.insert(nx, ni)
+        got, scales2, _ = codes_by_id(ix)
+        assert np.array_equal(scales2, scales)
+        for x, i in zip(nx, ni):
+            c, part = got[int(i)]
+            assert np.array_equal(c, quant.quantize_e4m3(x[None, :], scales[part])[0])
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("metric", [0, 1])
+def test_rerank_of_all_candidates_is_exact(I, storage, metric):
+    X, ids, Q = synth.aps_search(seed=32, n=900, d=128, n_comp=6, sigma=1.0, nq=12)
+    if metric == 1:
+        X, Q = synth.unit_rows(X), synth.unit_rows(Q)
+    levels = kmeans.build_index(X, ids, 9, 0, iters=2, seed=2)
+    ix = make(I, X, ids, levels, storage=storage, rerank=100, metric=metric, f_M_leaf=1.0)
+    gi, gd, gn, gr = ix.search(Q, 10, recall_target=0.0, nprobe=9)
+    D, Ix = knn.knn(X, ids, Q, 10, metric=metric)
+    for j in range(Q.shape[0]):
+        assert same_topk(gi[j], gd[j], Ix[j], D[j])
+
+
+def test_low_precision_recall_against_fp64(I):
+    X, ids, Q = synth.aps_search(seed=33, n=40_000, d=128, n_comp=40, sigma=1.5, nq=200)
+    levels = kmeans.build_index(X, ids, 100, 0, iters=4, seed=3)
+    gtD, _ = knn.knn(X, ids, Q, 10, bulk=True)
+    rec = {}
+    for storage in (0, 1, 2):
+        ix = make(I, X, ids, levels, storage=storage, rerank=4, f_M_leaf=0.3)
+        gi, gd, gn, gr = ix.search(Q, 10, recall_target=0.0, nprobe=20)
+        ex = exact_dist(X, Q, gi)
+        rec[storage] = knn.recall_at_k(gi, ex, gtD, 10).mean()
+        # the distances returned are exact FP32 distances of the returned ids
+        ok = gi >= 0
+        np.testing.assert_allclose(gd[ok], ex[ok], rtol=1e-5, atol=1e-4)
+    assert rec[1] >= rec[0] - 0.01 and rec[2] >= rec[0] - 0.03, rec
+
+
+def test_inner_product_aps_matches_oracle(I):
+    X, ids, Q = synth.aps_search(seed=34, n=20_000, d=128, n_comp=40, sigma=1.0, nq=100)
+    X, Q = synth.unit_rows(X), synth.unit_rows(Q)
+    levels = kmeans.build_index(X, ids, 120, 8, iters=4, seed=4)
+    ix = make(I, X, ids, levels, metric=1, f_M_leaf=0.15, f_M_parent=0.5)
+    out = ix.search(Q, 10, recall_target=0.9)
+    orc = aps.search(levels, Q, aps.Params(k=10, recall_target=0.9, f_M=(0.15, 0.5)), metric=knn.IP)
+    n_ok, n_exc = compare_search(out, orc, 10)
+    assert n_exc <= 0.05 * Q.shape[0]
