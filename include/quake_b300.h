@@ -222,6 +222,23 @@ qk_status qk_cap_fraction(int32_t d, int32_t mode, const double* t, const double
                           double* out_u, void* stream);
 
 /*
+ * For each of the n rows of x (n x d), the k nearest of the K centroids c
+ * (K x d), 1 <= k <= min(8, K), d a multiple of 32: out_idx (n x k) and, if
+ * not NULL, out_dist (n x k, exact FP32 distances: squared L2, or the negated
+ * inner product) in (distance, index) order.  This is the centroid scoring of
+ * the top-down search and of k-means assignment (Sec. 3): tensor cores
+ * (tcgen05, TF32 operands, FP32 accumulation) score every centroid, the 16
+ * best approximate candidates of a row are re-scored exactly in FP32 from the
+ * direct differences, and the k best are kept.  TF32 moves an approximate
+ * distance by at most about 2^-10 ||x|| ||c||; keeping twice the largest k
+ * as approximate candidates leaves a margin for that, and a true neighbour
+ * outside the 16 approximate candidates is the only way the result can
+ * differ from an exact scan.
+ */
+qk_status qk_nearest_centroids(const float* x, int64_t n, int32_t d, const float* c, int32_t K, int32_t metric,
+                               int32_t k, int32_t* out_idx, float* out_dist, void* stream);
+
+/*
  * One Lloyd step on the GPU (Sec. 3; k-means as in qk_build): assigns each of
  * the n rows of x to the nearest of the K centroids c (ties to the lower
  * index) and returns the FP64 member means rounded to FP32 in c_new (empty

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIME
 EXPORTS = [
     "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load",
     "qk_search", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_export_quantized", "qk_get_hits", "qk_cap_fraction",
-    "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain",
+    "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain", "qk_nearest_centroids",
 ]
 
 
@@ -79,6 +79,7 @@ def _load():
         "qk_get_hits": (i32, [vp, i32, vp, i32]),
         "qk_cap_fraction": (i32, [i32, i32, vp, vp, i64, vp, vp]),
         "qk_kmeans_step": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp]),
+        "qk_nearest_centroids": (i32, [vp, i64, i32, vp, i32, i32, i32, vp, vp, vp]),
         "qk_kmeans_step_noalloc": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp]),
         "qk_maintain": (i32, [vp, C.POINTER(QkMaintParams), C.POINTER(QkMaintAction), i32,
                               C.POINTER(C.c_int32), vp]),

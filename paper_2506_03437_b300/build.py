@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libquake_b300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["capi.cu", "search.cu", "kmeans.cu", "arena.cu", "update.cu", "maintain.cu", "quant.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "search.cu", "kmeans.cu", "arena.cu", "update.cu", "maintain.cu", "quant.cu", "tc_score.cu", "noalloc.cu"]
 HEADERS = ["common.cuh", "capvol.cuh", "index.cuh"]
 
 NVCC_FLAGS = [

@@ -54,6 +54,11 @@ qk_status launch_move_bytes(unsigned char* a, const int64_t* src, const int64_t*
 qk_status launch_relayout_bytes(const unsigned char* old_a, const int64_t* old_off, const int64_t* new_off,
                                 const int32_t* size, int32_t n_part, int rb, unsigned char* new_a, cudaStream_t s);
 
+qk_status launch_tc_nearest(const float* X, int64_t n, int d, const float* C, int K, int metric, int k,
+                            int32_t* out_idx, float* out_dist, float* cnorm, int32_t* cand, int32_t* status,
+                            cudaStream_t s);
+int tc_candidates_per_row();
+
 static int elem_bytes(int storage) { return storage == QK_STORE_BF16 ? 2 : (storage == QK_STORE_FP8 ? 1 : 4); }
 
 static thread_local std::string g_err;
@@ -110,6 +115,10 @@ struct Tmp {
 template <class T>
 static qk_status in_device(const T* src, size_t count, Tmp& tmp, const T** out, cudaStream_t s) {
   if (!src || is_device_ptr(src)) {
+    if (reinterpret_cast<uintptr_t>(src) % 16 != 0) {   // rows are read with 16-byte accesses
+      set_error("device buffers must be 16-byte aligned");
+      return QK_ERR_ARG;
+    }
     *out = src;
     return QK_OK;
   }
@@ -296,6 +305,30 @@ static void splitmix_init_rows(int64_t n, int32_t K, uint64_t seed, std::vector<
   out.assign(perm.begin(), perm.begin() + K);
 }
 
+// Nearest centroid of every row (L2, ties to the lower index).  With 32 or
+// more centroids the candidates come from the tensor-core scoring kernel and
+// are re-scored exactly; otherwise the SIMT kernel compares every centroid.
+qk_status assign_nearest(const float* X, int64_t n, int d, const float* C, int K, int32_t* assign, cudaStream_t s) {
+  if (K < 32 || d % 32 != 0 || n <= 0) return launch_kmeans_assign(X, n, d, C, K, assign, nullptr, s);
+  Tmp tn, tc_, ts;
+  float* cnorm = nullptr;
+  int32_t* cand = nullptr;
+  int32_t* st = nullptr;
+  QK_TRY(tn.alloc<float>((size_t)K, &cnorm));
+  QK_TRY(tc_.alloc<int32_t>((size_t)n * tc_candidates_per_row(), &cand));
+  QK_TRY(ts.alloc<int32_t>(1, &st));
+  QK_CUDA(cudaMemsetAsync(st, 0, sizeof(int32_t), s));
+  QK_TRY(launch_tc_nearest(X, n, d, C, K, QK_METRIC_L2, 1, assign, nullptr, cnorm, cand, st, s));
+  int32_t hst = 0;
+  QK_CUDA(cudaMemcpyAsync(&hst, st, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  if (hst != 0) {
+    set_error("tensor-core scoring: a bounded wait expired");
+    return QK_ERR_TIMEOUT;
+  }
+  return QK_OK;
+}
+
 // Lloyd k-means of n device rows into K centroids (device, K x d) and the
 // final assignment (device, n).  Starts from the seeded rows, or from C_init
 // (device, K x d) when it is given.
@@ -319,11 +352,11 @@ qk_status kmeans(const float* X, int64_t n, int d, int32_t K, int iters, uint64_
     QK_TRY(launch_gather_rows(X, d, rows, K, C, s));
   }
   for (int it = 0; it < iters; ++it) {
-    QK_TRY(launch_kmeans_assign(X, n, d, C, K, assign, nullptr, s));
+    QK_TRY(assign_nearest(X, n, d, C, K, assign, s));
     QK_TRY(launch_kmeans_update(X, n, d, assign, C, K, C2, sums, counts, s));
     QK_CUDA(cudaMemcpyAsync(C, C2, sizeof(float) * (size_t)K * d, cudaMemcpyDeviceToDevice, s));
   }
-  QK_TRY(launch_kmeans_assign(X, n, d, C, K, assign, nullptr, s));
+  QK_TRY(assign_nearest(X, n, d, C, K, assign, s));
   QK_CUDA(cudaStreamSynchronize(s));
   return QK_OK;
 }
@@ -731,11 +764,11 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   int32_t* leaf = nullptr;
   QK_TRY(tleaf.alloc<int32_t>((size_t)n, &leaf));
   if (ix->n_parent == 0) {
-    QK_TRY(launch_kmeans_assign(X, n, d, ix->cent0, ix->n_leaf, leaf, nullptr, s));
+    QK_TRY(assign_nearest(X, n, d, ix->cent0, ix->n_leaf, leaf, s));
   } else {
     int32_t* par = nullptr;
     QK_TRY(tpar.alloc<int32_t>((size_t)n, &par));
-    QK_TRY(launch_kmeans_assign(X, n, d, ix->cent1, ix->n_parent, par, nullptr, s));
+    QK_TRY(assign_nearest(X, n, d, ix->cent1, ix->n_parent, par, s));
     QK_TRY(launch_descend_children(X, n, d, par, ix->vec1, ix->ids1, ix->off1, ix->size1, leaf, s));
   }
   std::vector<int32_t> hleaf((size_t)n);
@@ -971,6 +1004,44 @@ qk_status qk_cap_fraction(int32_t d, int32_t mode, const double* t, const double
   return QK_OK;
 }
 
+qk_status qk_nearest_centroids(const float* x, int64_t n, int32_t d, const float* c, int32_t K, int32_t metric,
+                               int32_t k, int32_t* out_idx, float* out_dist, void* stream) {
+  if (!x || !c || !out_idx || n < 0 || K < 1 || d < 32 || d % 32 != 0 || k < 1 || k > 8 || k > K ||
+      (metric != QK_METRIC_L2 && metric != QK_METRIC_IP)) {
+    set_error("qk_nearest_centroids: invalid arguments (d a multiple of 32, 1 <= k <= min(8, K))");
+    return QK_ERR_ARG;
+  }
+  if (n == 0) return QK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  Tmp tx, tcen, ti, td, tn, tcand, ts;
+  const float *X = nullptr, *C = nullptr;
+  QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
+  QK_TRY(in_device(c, (size_t)K * d, tcen, &C, s));
+  const bool idx_dev = is_device_ptr(out_idx), dist_dev = !out_dist || is_device_ptr(out_dist);
+  int32_t* di = out_idx;
+  float* dd = out_dist;
+  if (!idx_dev) QK_TRY(ti.alloc<int32_t>((size_t)n * k, &di));
+  if (!dist_dev) QK_TRY(td.alloc<float>((size_t)n * k, &dd));
+  float* cnorm = nullptr;
+  int32_t* cand = nullptr;
+  int32_t* st = nullptr;
+  QK_TRY(tn.alloc<float>((size_t)K, &cnorm));
+  QK_TRY(tcand.alloc<int32_t>((size_t)n * tc_candidates_per_row(), &cand));
+  QK_TRY(ts.alloc<int32_t>(1, &st));
+  QK_CUDA(cudaMemsetAsync(st, 0, sizeof(int32_t), s));
+  QK_TRY(launch_tc_nearest(X, n, d, C, K, metric, k, di, dd, cnorm, cand, st, s));
+  if (!idx_dev) QK_CUDA(cudaMemcpyAsync(out_idx, di, sizeof(int32_t) * n * k, cudaMemcpyDeviceToHost, s));
+  if (!dist_dev) QK_CUDA(cudaMemcpyAsync(out_dist, dd, sizeof(float) * n * k, cudaMemcpyDeviceToHost, s));
+  int32_t hst = 0;
+  QK_CUDA(cudaMemcpyAsync(&hst, st, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  QK_CUDA(cudaStreamSynchronize(s));
+  if (hst != 0) {
+    set_error("tensor-core scoring: a bounded wait expired");
+    return QK_ERR_TIMEOUT;
+  }
+  return QK_OK;
+}
+
 qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, int32_t K, float* c_new,
                          int32_t* assign, int32_t* counts, void* stream) {
   if (!x || !c || n < 1 || d < 1 || K < 1) {
@@ -990,7 +1061,7 @@ qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, i
   QK_TRY(tn.alloc<float>((size_t)K * d, &Cn));
   QK_TRY(tsum.alloc<double>((size_t)K * d, &sums));
   QK_TRY(tcnt.alloc<int32_t>((size_t)K, &cnt));
-  QK_TRY(launch_kmeans_assign(X, n, d, C, K, a, nullptr, s));
+  QK_TRY(assign_nearest(X, n, d, C, K, a, s));
   QK_TRY(launch_kmeans_update(X, n, d, a, C, K, Cn, sums, cnt, s));
   if (c_new) QK_CUDA(cudaMemcpyAsync(c_new, Cn, sizeof(float) * (size_t)K * d, cudaMemcpyDefault, s));
   if (assign) QK_CUDA(cudaMemcpyAsync(assign, a, sizeof(int32_t) * (size_t)n, cudaMemcpyDefault, s));

@@ -129,4 +129,5 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
                   const int32_t* leaf_of_row, const float* C1, const int32_t* parent_of_leaf, cudaStream_t s,
                   bool skip_unlabelled);
 bool is_device_ptr(const void* p);
+qk_status assign_nearest(const float* X, int64_t n, int d, const float* C, int K, int32_t* assign, cudaStream_t s);
 }  // namespace qk

@@ -326,8 +326,8 @@ qk_status maintain_level(Ctx& cx, Level& L, int level_no, std::vector<int32_t>* 
         QK_TRY(cx.cent.reserve(sizeof(float) * Co.size()));
         QK_TRY(cx.assign.reserve(sizeof(int32_t) * n));
         QK_CUDA(cudaMemcpyAsync(cx.cent.p, Co.data(), sizeof(float) * Co.size(), cudaMemcpyHostToDevice, cx.s));
-        QK_TRY(launch_kmeans_assign(cx.rows.as<float>(), n, d, cx.cent.as<float>(), (int)others.size(),
-                                    cx.assign.as<int32_t>(), nullptr, cx.s));
+        QK_TRY(assign_nearest(cx.rows.as<float>(), n, d, cx.cent.as<float>(), (int)others.size(),
+                              cx.assign.as<int32_t>(), cx.s));
         QK_CUDA(cudaMemcpyAsync(am.data(), cx.assign.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, cx.s));
         QK_CUDA(cudaStreamSynchronize(cx.s));
       }

@@ -185,3 +185,14 @@ def kmeans_step(x, c):
     cnt = np.empty(K, np.int32)
     L.check(L.lib.qk_kmeans_step(L.ptr(x), n, d, L.ptr(c), K, L.ptr(cn), L.ptr(a), L.ptr(cnt), None))
     return cn, a, cnt
+
+
+def nearest_centroids(x, c, k, metric=L.METRIC_L2):
+    """The k nearest centroids of every row (tensor-core scoring + exact FP32 re-score), as numpy."""
+    x = np.ascontiguousarray(x, np.float32)
+    c = np.ascontiguousarray(c, np.float32)
+    n, d = x.shape
+    idx = np.empty((n, k), np.int32)
+    dist = np.empty((n, k), np.float32)
+    L.check(L.lib.qk_nearest_centroids(L.ptr(x), n, d, L.ptr(c), c.shape[0], metric, k, L.ptr(idx), L.ptr(dist), None))
+    return idx, dist
