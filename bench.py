@@ -333,12 +333,65 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_assign(args):
+    """Tensor-core nearest-centroid assignment (k-means step of the build): 1M x 128 rows, 1,000 centroids."""
+    import torch
+    from paper_2506_03437_b300 import _lib as L
+    torch.cuda.set_device(0)
+    n, d, K = args.n, D, args.leaves
+    X, _, _ = synth.aps_search(n=n, d=d, n_comp=max(1, n // 1000), sigma=SIGMA, nq=1)
+    C = X[np.random.default_rng(SEED).choice(n, K, replace=False)].copy()
+    Xd, Cd = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+    idx = torch.empty((n, 1), dtype=torch.int32, device="cuda")
+    dist = torch.empty((n, 1), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        L.check(L.lib.qk_nearest_centroids(Xd.data_ptr(), n, d, Cd.data_ptr(), K, 0, 1, idx.data_ptr(),
+                                           dist.data_ptr(), stream.cuda_stream))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        for a, b in ev:
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+    s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    flops = 2.0 * n * K * d
+    peak_bf16 = 1767.5
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    kind = "fallback"
+    if os.path.exists(p):
+        with open(p) as f:
+            peak_bf16 = float(json.load(f)["bf16_tflops"])
+        kind = "measured"
+    peak_tf32 = peak_bf16 * (1.1 / 2.25)   # nominal TF32 / BF16 dense ratio
+    tf = flops * args.steps / s / 1e12
+    print(json.dumps({
+        "metric": "rows assigned per second (tensor-core nearest centroid, exact FP32 re-score)",
+        "value": round(n * args.steps / s, 1), "unit": "rows/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * s / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "tf32 operands, f32 accumulate",
+        "data": "synthetic", "config": {"workload": f"nearest_centroid_{n}x{d}_K{K}", "n": n, "d": d, "K": K},
+        "roofline": {"bound": "tensor", "achieved": round(tf, 1), "peak": round(peak_tf32, 1), "unit": "TFLOP/s",
+                     "frac": round(tf / peak_tf32, 4), "traffic": None,
+                     "peak_kind": f"{kind} bf16 burst x nominal tf32/bf16 ratio 1.1/2.25",
+                     "note": "achieved counts the 2*n*K*d dot-product flops over the whole call "
+                             "(GEMM, candidate selection and exact re-score)"},
+        "clocks": clk.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="aps", choices=["aps", "assign"],
+                    help="aps: the APS search (default); assign: tensor-core nearest-centroid assignment")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -358,6 +411,8 @@ def main():
         WORKLOAD = f"aps_search_{N}x128_{N_LEAF}leaf_{N_PARENT}parent_{NQ}q_zipf1.1_k10"
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "assign":
+        run_assign(args)
     else:
         run_ours(args)
 

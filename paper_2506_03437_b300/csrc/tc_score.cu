@@ -32,12 +32,13 @@ namespace tc {
 constexpr int kM = 128;        // rows per CTA (TMEM lanes)
 constexpr int kN = 256;        // centroids per tile (TMEM columns)
 constexpr int kKS = 32;        // K elements per staged slice
-constexpr int kThreads = 128;
-constexpr int kT = 16;         // approximate candidates kept per row
+constexpr int kThreads = 256;  // 8 warps: warps w and w + 4 share TMEM lanes, split the columns
+constexpr int kT = 16;         // approximate candidates kept per row (k <= 8)
+constexpr int kT1 = 4;         // ... when only the nearest centroid is wanted
 
 constexpr int kSliceA = kM * kKS * 4;    // 16 KB
 constexpr int kSliceB = kN * kKS * 4;    // 32 KB
-constexpr int kSmem = 2 * (kSliceA + kSliceB) + 64;
+constexpr int kSmem = 2 * (kSliceA + kSliceB) + kN * 4 + 64;
 
 // Instruction descriptor of kind::tf32 (PTX ISA, tcgen05 instruction
 // descriptor): D format F32 (bits 4-5 = 1), A and B format TF32 (bits 7-9
@@ -126,7 +127,8 @@ __global__ void row_norms_kernel(const float* __restrict__ C, int64_t K, int d, 
   if (lane == 0) out[w] = acc;
 }
 
-// Approximate top-kT candidates per row (see the file comment).
+// Approximate top-T candidates per row (see the file comment).
+template <int T>
 __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float* __restrict__ X, int64_t n, int d,
                                                                      const float* __restrict__ C, int K,
                                                                      const float* __restrict__ cnorm, int metric,
@@ -134,11 +136,11 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
                                                                      int32_t* __restrict__ status) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* bufA[2] = {smem, smem + kSliceA};
-  unsigned char* bufB[2] = {smem + 2 * kSliceA, smem + 2 * kSliceA + kSliceB};
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * (kSliceA + kSliceB));
+  float* scn = reinterpret_cast<float*>(smem + 2 * (kSliceA + kSliceB));   // ||c||^2 of the tile
+  uint64_t* bars = reinterpret_cast<uint64_t*>(scn + kN);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int quarter = warp & 3, half = warp >> 2;   // TMEM lanes 32 * quarter.., columns 128 * half..
   const int64_t row0 = (int64_t)blockIdx.x * kM;
 
   if (warp == 0) tmem_alloc(tmem_holder, kN);
@@ -152,12 +154,13 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
   fence_after_sync();
   const uint32_t tmem = *tmem_holder;
 
-  // this thread's row and its running top-kT (ascending)
-  const int64_t my_row = row0 + tid;
-  float bd[kT];
-  int32_t bi[kT];
+  // this thread's row and its running top-T over its half of every tile (ascending)
+  const int my_lane = quarter * 32 + (tid & 31);
+  const int64_t my_row = row0 + my_lane;
+  float bd[T];
+  int32_t bi[T];
 #pragma unroll
-  for (int i = 0; i < kT; ++i) {
+  for (int i = 0; i < T; ++i) {
     bd[i] = INFINITY;
     bi[i] = -1;
   }
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
       // ((r / 8) * 8 + c) * 128 + (r % 8) * 16.  K stride 128 B, row-group
       // stride 1024 B, so every address the descriptors can form stays
       // inside the slice.
-      const uint32_t a_base = smem_u32(bufA[b]), b_base = smem_u32(bufB[b]);
+      const uint32_t a_base = smem_u32(smem + b * kSliceA), b_base = smem_u32(smem + 2 * kSliceA + b * kSliceB);
       for (int e = tid; e < kM * (kKS / 4); e += kThreads) {
         int r = e % kM, c = e / kM;
         int64_t gr = row0 + r;
@@ -198,6 +201,8 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
         const float* src = C + (int64_t)(v ? gc : 0) * d + ks * kKS + c * 4;
         cp_async16(b_base + ((r >> 3) * (kKS / 4) + c) * 128 + (r & 7) * 16, src, v);
       }
+      if (ks == 0)
+        for (int j = tid; j < kN; j += kThreads) scn[j] = n0 + j < K ? cnorm[n0 + j] : INFINITY;
       cp_async_wait_all();
       fence_proxy_async();        // generic-proxy writes -> tensor-core (async proxy) reads
       fence_before_sync();
@@ -231,22 +236,21 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
       issued[bl ^ 1] = 0;
     }
     fence_after_sync();
-    // epilogue: this thread's TMEM lane = its row
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < kN; c0 += 8) {
+    // epilogue: this thread's TMEM lane = its row, its half of the columns
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    for (int c0 = half * (kN / 2); c0 < (half + 1) * (kN / 2); c0 += 8) {
       float v[8];
       tc::tmem_ld8(lane_addr + c0, v);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         int col = n0 + c0 + i;
-        if (col >= K) continue;
-        float dist = metric == QK_METRIC_L2 ? fmaf(-2.f, v[i], cnorm[col]) : -v[i];
-        if (dist < bd[kT - 1] || (dist == bd[kT - 1] && col < bi[kT - 1])) {
+        float dist = metric == QK_METRIC_L2 ? fmaf(-2.f, v[i], scn[c0 + i]) : (col < K ? -v[i] : INFINITY);
+        if (dist < bd[T - 1] || (dist == bd[T - 1] && col < bi[T - 1])) {
           // insert into the sorted registers
           float cd = dist;
           int32_t ci = col;
 #pragma unroll
-          for (int j = 0; j < kT; ++j) {
+          for (int j = 0; j < T; ++j) {
             bool lt = cd < bd[j] || (cd == bd[j] && ci < bi[j]);
             float td = bd[j];
             int32_t ti = bi[j];
@@ -262,11 +266,33 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
     __syncthreads();      // every lane read before the next tile's MMAs overwrite TMEM
     fence_after_sync();
   }
-  if (my_row < n) {
+  // merge the two halves of every row: the second half passes its list through
+  // shared memory (the operand buffers are idle now)
+  // both halves' lists go to shared memory (the operand buffers are idle now)
+  float* xd = reinterpret_cast<float*>(smem) + half * kM * T;
+  int32_t* xi = reinterpret_cast<int32_t*>(smem + 2 * kM * T * 4) + half * kM * T;
 #pragma unroll
-    for (int i = 0; i < kT; ++i) cand[my_row * kT + i] = bi[i];
+  for (int i = 0; i < T; ++i) {
+    xd[my_lane * T + i] = bd[i];
+    xi[my_lane * T + i] = bi[i];
   }
   fence_before_sync();
+  __syncthreads();
+  if (half == 0 && my_row < n) {
+    const float* ad = reinterpret_cast<const float*>(smem) + my_lane * T;
+    const int32_t* ai = reinterpret_cast<const int32_t*>(smem + 2 * kM * T * 4) + my_lane * T;
+    const float* bd2 = ad + kM * T;
+    const int32_t* bi2 = ai + kM * T;
+    int a = 0, b = 0;
+    for (int i = 0; i < T; ++i) {   // merge two ascending lists, keep T
+      bool take_b = a >= T || (b < T && (bd2[b] < ad[a] || (bd2[b] == ad[a] && bi2[b] < ai[a])));
+      float vd = take_b ? bd2[b] : ad[a];
+      int32_t vi = take_b ? bi2[b] : ai[a];
+      cand[my_row * kT + i] = vd < INFINITY ? vi : -1;
+      if (take_b) ++b; else ++a;
+    }
+    for (int i = T; i < kT; ++i) cand[my_row * kT + i] = -1;
+  }
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kN);
 }
@@ -330,9 +356,16 @@ qk_status launch_tc_nearest(const float* X, int64_t n, int d, const float* C, in
   if (d % tc::kKS != 0 || k < 1 || k > tc::kT) return QK_ERR_ARG;
   row_norms_kernel<<<(unsigned)(((int64_t)K * 32 + 255) / 256), 256, 0, s>>>(C, K, d, cnorm);
   QK_CUDA(cudaGetLastError());
-  QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem));
   unsigned grid = (unsigned)((n + tc::kM - 1) / tc::kM);
-  tc_candidates_kernel<<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, cand, status);
+  if (k == 1) {
+    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<tc::kT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::kSmem));
+    tc_candidates_kernel<tc::kT1><<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, cand, status);
+  } else {
+    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<tc::kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::kSmem));
+    tc_candidates_kernel<tc::kT><<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, cand, status);
+  }
   QK_CUDA(cudaGetLastError());
   rescore_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, d, C, cand, metric, k, out_idx, out_dist);
   QK_CUDA(cudaGetLastError());

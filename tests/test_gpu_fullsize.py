@@ -1,0 +1,45 @@
+"""Parity at the full APS workload size (1M x 128, 1,000 leaves under 32 parents, 10,000 queries).
+
+The GPU searches the whole 10,000-query batch in one launch, as bench.py
+times it; the oracle recomputes a sample of those queries one by one.  The
+partitioning is fixed by the oracle: leaf centroids are the generator's
+1,000 component centres with every vector in its nearest centre's partition
+(exact FP64 assignment), parents are the oracle's k-means of those centres.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import aps, kmeans, knn
+from paper_2506_03437_b300 import synth
+
+from .parity import compare_search, exact_dist
+from .test_gpu_search import make_index
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("storage", [0])
+def test_full_size_aps_sampled_parity(storage):
+    import torch
+    from paper_2506_03437_b300 import index as I
+    n, d, n_comp, nq = 1_000_000, 128, 1000, 10_000
+    X, ids, Q = synth.aps_search(n=n, d=d, n_comp=n_comp, sigma=1.5, nq=nq)
+    C0 = synth.mixture_centers(n_comp, d, 1236)
+    a0 = kmeans.assign(X, C0)
+    C1 = kmeans.lloyd(C0, 32, 10, 1235)
+    a1 = kmeans.assign(C0, C1)
+    levels = kmeans.index_from_assignment(X, ids, C0, a0, C1, a1)
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.1, f_M_parent=0.25)
+    gi, gd, gn, gr = ix.search(torch.from_numpy(Q).cuda(), 10, recall_target=0.9)
+    ix.check()
+    gi, gd, gn, gr = gi.cpu().numpy(), gd.cpu().numpy(), gn.cpu().numpy(), gr.cpu().numpy()
+    assert ((gi >= 0) & (gi < n)).all() and (np.diff(gd, axis=1) >= 0).all()
+    sel = np.random.default_rng(0).choice(nq, 40, replace=False)
+    orc = aps.search(levels, Q[sel], aps.Params(k=10, recall_target=0.9, f_M=(0.1, 0.25)))
+    n_ok, n_exc = compare_search((gi[sel], gd[sel], gn[sel], gr[sel]), orc, 10)
+    assert n_exc <= 2
+    # recall of the sample against FP64 brute force
+    gtD, _ = knn.knn(X, ids, Q[sel], 10, bulk=True)
+    rec = knn.recall_at_k(gi[sel], exact_dist(X, Q[sel], gi[sel]), gtD, 10).mean()
+    assert rec > 0.85
