@@ -384,14 +384,62 @@ def run_assign(args):
         "clocks": clk.summary()}), flush=True)
 
 
+def run_serve(args):
+    """Dynamic skewed stream (start 2M x 128 from 2,000 components; 90% queries, 5% inserts,
+    5% deletes; Zipf(1.2) over a hot set of 100 components rotating every 100,000 operations;
+    maintenance every 100,000 operations), open-loop Poisson arrivals at a fraction of the
+    measured saturation rate.  Reports p50/p99 latency and QPS."""
+    import torch
+    from paper_2506_03437_b300 import index as I
+    from paper_2506_03437_b300.serving import Server, skewed_stream
+    torch.cuda.set_device(0)
+    n0, n_comp = args.start, 2000
+    C = synth.mixture_centers(n_comp, D, 1240)
+    X, _ = synth.mixture_samples(C, n0, SIGMA, 1241)
+    ids = np.arange(n0, dtype=np.int64)
+    n_leaf = int(round(n0 ** 0.5))
+    ix = I.Index(D, n_leaf=n_leaf, n_parent=int(round(n_leaf ** 0.5)), kmeans_iters=ITERS, seed=SEED,
+                 f_M_leaf=F_M_LEAF, f_M_parent=F_M_PARENT)
+    ix.build(torch.from_numpy(X).cuda(), torch.from_numpy(ids).cuda())
+    # scan latency lambda(s) per (query, partition): 2 us + 45 ns per 128-d FP32 row, from the
+    # search kernel's per-CTA scan rate measured by bench.py (about 11 GB/s per resident query)
+    maint = dict(lam_sizes=[0, 100_000], lam_us=[2.0, 2.0 + 0.045 * 100_000], tau_us=0.25, alpha=0.9,
+                 refine_radius=50, refine_iters=1, s_min=max(1, n0 // n_leaf // 8))
+    print(f"serve: built {n0} x {D} ({n_leaf} leaves)", file=sys.stderr, flush=True)
+    # saturation: a closed burst of queries
+    burst = skewed_stream(C, ids, 20_000, SIGMA, 1242, p_query=1.0, p_insert=0.0, rate=None)
+    srv = Server(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4)
+    sat = srv.run(burst)["search_qps"]
+    sat = max(sat, srv.run(burst)["search_qps"])
+    rate = args.serve_load * sat / 0.9          # ops/s so that queries arrive at serve_load x saturation
+    ops = skewed_stream(C, ids, args.ops, SIGMA, 1243, rate=rate)
+    srv = Server(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4, maintain_every=100_000,
+                 maint_args=maint)
+    with Clocks(0) as clk:
+        st = srv.run(ops)
+    line = {"metric": "serving p50/p99 latency and QPS (dynamic skewed stream)",
+            "value": st["search_qps"], "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": round(1e3 * st["wall_s"], 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic skewed stream",
+            "config": {"workload": f"serve_{n0}x{D}_{args.ops}ops", "start_vectors": n0, "ops": args.ops,
+                       "load": args.serve_load, "saturation_qps": sat, "arrival_rate_ops": round(rate, 1),
+                       "n_leaf": n_leaf, "streams": 4, "max_batch": 2048},
+            "latency": st, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="aps", choices=["aps", "assign"],
-                    help="aps: the APS search (default); assign: tensor-core nearest-centroid assignment")
+    ap.add_argument("--workload", default="aps", choices=["aps", "assign", "serve"],
+                    help="aps: the APS search (default); assign: tensor-core nearest-centroid assignment; "
+                         "serve: the continuous-batching request loop on a dynamic skewed stream")
+    ap.add_argument("--ops", type=int, default=1_000_000, help="operations of the serving stream")
+    ap.add_argument("--serve-load", type=float, default=0.5, help="query arrival rate / saturation")
+    ap.add_argument("--start", type=int, default=2_000_000, help="vectors in the index when the stream starts")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -413,6 +461,8 @@ def main():
         run_reference(args)
     elif args.workload == "assign":
         run_assign(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

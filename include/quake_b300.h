@@ -21,7 +21,9 @@
  *  - No C++ exception crosses the ABI.  A failing call returns a non-zero
  *    qk_status and leaves a message for qk_last_error() (thread-local).
  *  - Calls on one index are not thread-safe; use one index per host thread or
- *    serialise the calls.
+ *    serialise the calls.  Searches with device buffers may be in flight on up
+ *    to 16 streams at once; insert, delete, maintain and build must not overlap
+ *    a search in flight (synchronise its stream first).
  */
 #ifndef QUAKE_B300_H
 #define QUAKE_B300_H

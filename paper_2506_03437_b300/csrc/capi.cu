@@ -16,6 +16,7 @@
 #include "capvol.cuh"
 #include "common.cuh"
 #include "index.cuh"
+#include "trace.h"
 
 namespace qk {
 
@@ -93,20 +94,23 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Temporary device buffer freed on scope exit (set-up paths only).
+// Temporary device buffer, stream-ordered: taken from the device's memory
+// pool on stream s and given back, in stream order, on scope exit, so that
+// no call waits for the whole device.
 struct Tmp {
   void* p = nullptr;
-  Tmp() = default;
+  cudaStream_t s;
+  explicit Tmp(cudaStream_t st) : s(st) {}
   Tmp(const Tmp&) = delete;
   ~Tmp() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
   }
   template <class T>
   qk_status alloc(size_t count, T** out) {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     if (count == 0) count = 1;
-    QK_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    QK_CUDA(cudaMallocAsync(&p, count * sizeof(T), s));
     *out = static_cast<T*>(p);
     return QK_OK;
   }
@@ -164,6 +168,9 @@ static int32_t n_candidates(double f, int32_t n) {
 // Rows reserved per partition: its size plus room for inserts.
 static int64_t capacity_for(int64_t size) { return size + std::max<int64_t>(16, size / 4); }
 
+// Free rows behind the last partition of a fresh arena (1/8 of the reserved rows).
+static int64_t tail_rows(int64_t reserved) { return std::max<int64_t>(1024, reserved / 8); }
+
 static void free_structure(qk_index* ix) {
   dfree(ix->vec0);
   dfree(ix->ids0);
@@ -189,8 +196,8 @@ static qk_status group_rows(const float* rows, const int64_t* ids, int64_t n, in
                             int32_t K, bool slack, int32_t* status, float** vec, int64_t** ids_out,
                             int64_t** off, int32_t** size, std::vector<int64_t>& h_off,
                             std::vector<int32_t>& h_size, std::vector<int64_t>* h_cap, int64_t* cap_rows,
-                            cudaStream_t s, bool skip_unlabelled) {
-  Tmp tc;
+                            int64_t* used_rows, cudaStream_t s, bool skip_unlabelled) {
+  Tmp tc(s);
   int32_t* counts = nullptr;
   QK_TRY(tc.alloc<int32_t>(K, &counts));
   QK_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * K, s));
@@ -214,9 +221,12 @@ static qk_status group_rows(const float* rows, const int64_t* ids, int64_t n, in
     if (h_cap) (*h_cap)[j] = c;
     o += c;
   }
-  *cap_rows = o;
-  QK_TRY(dalloc(vec, (size_t)o * d));
-  QK_TRY(dalloc(ids_out, (size_t)o));
+  const int64_t total = o + (slack ? tail_rows(o) : 0);
+  *cap_rows = total;
+  if (used_rows) *used_rows = o;
+  QK_TRY(dalloc(vec, (size_t)total * d));
+  QK_TRY(dalloc(ids_out, (size_t)total));
+  QK_CUDA(cudaMemsetAsync(*ids_out, 0xff, sizeof(int64_t) * (size_t)total, s));   // id -1 in unused rows
   QK_TRY(dalloc(off, (size_t)K));
   QK_TRY(dalloc(size, (size_t)K));
   QK_CUDA(cudaMemcpyAsync(*off, h_off.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, s));
@@ -235,9 +245,12 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
                   bool skip_unlabelled) {
   const int d = ix->cfg.d;
   const int32_t N0 = ix->cfg.n_leaf, N1 = ix->cfg.n_parent;
+  Trace tr("install");
   free_structure(ix);
   QK_TRY(group_rows(X, ids, n, d, leaf_of_row, N0, true, ix->status, &ix->vec0, &ix->ids0, &ix->off0,
-                    &ix->size0, ix->h_off0, ix->h_size0, &ix->h_cap_part0, &ix->cap0, s, skip_unlabelled));
+                    &ix->size0, ix->h_off0, ix->h_size0, &ix->h_cap_part0, &ix->cap0, &ix->used0, s,
+                    skip_unlabelled));
+  ix->holes0 = 0;
   QK_TRY(dalloc(&ix->cent0, (size_t)N0 * d));
   QK_CUDA(cudaMemcpyAsync(ix->cent0, C0, sizeof(float) * (size_t)N0 * d, cudaMemcpyDeviceToDevice, s));
   if (ix->cfg.storage != QK_STORE_F32) {
@@ -248,7 +261,7 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
   QK_TRY(dalloc(&ix->hits0, (size_t)N0));
   QK_CUDA(cudaMemsetAsync(ix->hits0, 0, sizeof(unsigned long long) * N0, s));
   if (N1 > 0) {
-    Tmp tl;
+    Tmp tl(s);
     int64_t* leaf_ids = nullptr;
     QK_TRY(tl.alloc<int64_t>(N0, &leaf_ids));
     std::vector<int64_t> seq(N0);
@@ -256,12 +269,13 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
     QK_CUDA(cudaMemcpyAsync(leaf_ids, seq.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
     int64_t cap1 = 0;
     QK_TRY(group_rows(C0, leaf_ids, N0, d, parent_of_leaf, N1, false, ix->status, &ix->vec1, &ix->ids1,
-                      &ix->off1, &ix->size1, ix->h_off1, ix->h_size1, nullptr, &cap1, s, false));
+                      &ix->off1, &ix->size1, ix->h_off1, ix->h_size1, nullptr, &cap1, nullptr, s, false));
     QK_TRY(dalloc(&ix->cent1, (size_t)N1 * d));
     QK_CUDA(cudaMemcpyAsync(ix->cent1, C1, sizeof(float) * (size_t)N1 * d, cudaMemcpyDeviceToDevice, s));
     QK_TRY(dalloc(&ix->hits1, (size_t)N1));
     QK_CUDA(cudaMemsetAsync(ix->hits1, 0, sizeof(unsigned long long) * N1, s));
   }
+  tr.mark("arena");
   // id map, built from the arena so that it records the real slots
   std::vector<int64_t>& h_ids = ix->h_ids0;
   h_ids.assign((size_t)ix->cap0, -1);
@@ -279,6 +293,7 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
       }
     }
   }
+  tr.mark("id_map");
   ix->n = n;
   ix->n_leaf = N0;
   ix->n_parent = N1;
@@ -310,7 +325,7 @@ static void splitmix_init_rows(int64_t n, int32_t K, uint64_t seed, std::vector<
 // are re-scored exactly; otherwise the SIMT kernel compares every centroid.
 qk_status assign_nearest(const float* X, int64_t n, int d, const float* C, int K, int32_t* assign, cudaStream_t s) {
   if (K < 32 || d % 32 != 0 || n <= 0) return launch_kmeans_assign(X, n, d, C, K, assign, nullptr, s);
-  Tmp tn, tc_, ts;
+  Tmp tn(s), tc_(s), ts(s);
   float* cnorm = nullptr;
   int32_t* cand = nullptr;
   int32_t* st = nullptr;
@@ -334,7 +349,7 @@ qk_status assign_nearest(const float* X, int64_t n, int d, const float* C, int K
 // (device, K x d) when it is given.
 qk_status kmeans(const float* X, int64_t n, int d, int32_t K, int iters, uint64_t seed, float* C, int32_t* assign,
                  cudaStream_t s, const float* C_init) {
-  Tmp t_rows, t_c2, t_sums, t_counts;
+  Tmp t_rows(s), t_c2(s), t_sums(s), t_counts(s);
   int64_t* rows = nullptr;
   float* C2 = nullptr;
   double* sums = nullptr;
@@ -376,42 +391,89 @@ static qk_status check_ready(const qk_index* ix) {
 // Gives every level-0 partition room for need[j] rows: partitions whose
 // capacity is exceeded get capacity_for(need[j]); the arena is re-laid out
 // into fresh memory (all partitions keep their slots).
+// Makes room for need[j] rows in every partition j.  A partition that
+// outgrows its reserved rows moves, alone, to the free tail of the arena with
+// fresh room (its old rows become a hole).  When the tail is too small the
+// arena is compacted into a new allocation with a fresh tail.  Offsets on
+// host and device, the id mirror and the low-precision copy follow the rows.
 static qk_status grow_arena(qk_index* ix, const std::vector<int32_t>& need, cudaStream_t s) {
   const int d = ix->cfg.d;
   const int32_t N0 = ix->n_leaf;
-  std::vector<int64_t> cap(ix->h_cap_part0), off(N0);
+  const int rb = ix->lp0 ? d * elem_bytes(ix->cfg.storage) : 0;
+  std::vector<int64_t> cap(ix->h_cap_part0);
+  std::vector<int32_t> moved;
+  int64_t extra = 0;
   for (int32_t j = 0; j < N0; ++j)
-    if (need[j] > cap[j]) cap[j] = capacity_for(need[j]);
-  int64_t total = 0;
-  for (int32_t j = 0; j < N0; ++j) {
-    off[j] = total;
-    total += cap[j];
+    if (need[j] > cap[j]) {
+      cap[j] = capacity_for(need[j]);
+      moved.push_back(j);
+      extra += cap[j];
+    }
+  if (moved.empty()) return QK_OK;
+  if (ix->used0 + extra <= ix->cap0) {
+    const int32_t m = (int32_t)moved.size();
+    std::vector<int64_t> offs(2 * (size_t)m);   // old offsets, then new offsets
+    std::vector<int32_t> sz(m);
+    int64_t o = ix->used0;
+    for (int32_t i = 0; i < m; ++i) {
+      const int32_t j = moved[i];
+      offs[i] = ix->h_off0[j];
+      offs[m + i] = o;
+      sz[i] = ix->h_size0[j];
+      o += cap[j];
+      ix->holes0 += ix->h_cap_part0[j];
+    }
+    Tmp toffs(s), tsz(s);
+    int64_t* doffs = nullptr;
+    int32_t* dsz = nullptr;
+    QK_TRY(toffs.alloc<int64_t>(offs.size(), &doffs));
+    QK_TRY(tsz.alloc<int32_t>((size_t)m, &dsz));
+    QK_CUDA(cudaMemcpyAsync(doffs, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice, s));
+    QK_CUDA(cudaMemcpyAsync(dsz, sz.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    // source and destination rows are disjoint: the destinations lie in the tail
+    QK_TRY(launch_relayout(ix->vec0, ix->ids0, doffs, doffs + m, dsz, m, d, ix->vec0, ix->ids0, s));
+    if (ix->lp0) QK_TRY(launch_relayout_bytes(ix->lp0, doffs, doffs + m, dsz, m, rb, ix->lp0, s));
+    for (int32_t i = 0; i < m; ++i) {
+      const int32_t j = moved[i];
+      for (int32_t t = 0; t < sz[i]; ++t) {
+        ix->h_ids0[offs[m + i] + t] = ix->h_ids0[offs[i] + t];
+        ix->h_ids0[offs[i] + t] = -1;
+      }
+      ix->h_off0[j] = offs[m + i];
+    }
+    QK_CUDA(cudaMemcpyAsync(ix->off0, ix->h_off0.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
+    QK_CUDA(cudaStreamSynchronize(s));
+    ix->used0 = o;
+    ix->h_cap_part0 = cap;
+    return QK_OK;
   }
+  // compaction into a new arena
+  std::vector<int64_t> off(N0);
+  int64_t reserved = 0;
+  for (int32_t j = 0; j < N0; ++j) {
+    off[j] = reserved;
+    reserved += cap[j];
+  }
+  const int64_t total = reserved + tail_rows(reserved);
   float* nvec = nullptr;
   int64_t* nids = nullptr;
-  Tmp toff;
+  unsigned char* nlp = nullptr;
+  Tmp toff(s);
   int64_t* doff = nullptr;
-  QK_TRY(dalloc(&nvec, (size_t)total * d));
-  qk_status st = dalloc(&nids, (size_t)total);
+  qk_status st = dalloc(&nvec, (size_t)total * d);
+  if (st == QK_OK) st = dalloc(&nids, (size_t)total);
+  if (st == QK_OK && ix->lp0) st = dalloc(&nlp, (size_t)total * rb);
   if (st == QK_OK) st = toff.alloc<int64_t>(N0, &doff);
   if (st != QK_OK) {
     dfree(nvec);
     dfree(nids);
+    dfree(nlp);
     return st;
   }
+  QK_CUDA(cudaMemsetAsync(nids, 0xff, sizeof(int64_t) * (size_t)total, s));
   QK_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
   QK_TRY(launch_relayout(ix->vec0, ix->ids0, ix->off0, doff, ix->size0, N0, d, nvec, nids, s));
-  unsigned char* nlp = nullptr;
-  if (ix->lp0) {
-    const int rb = d * elem_bytes(ix->cfg.storage);
-    st = dalloc(&nlp, (size_t)total * rb);
-    if (st != QK_OK) {
-      dfree(nvec);
-      dfree(nids);
-      return st;
-    }
-    QK_TRY(launch_relayout_bytes(ix->lp0, ix->off0, doff, ix->size0, N0, rb, nlp, s));
-  }
+  if (ix->lp0) QK_TRY(launch_relayout_bytes(ix->lp0, ix->off0, doff, ix->size0, N0, rb, nlp, s));
   QK_CUDA(cudaMemcpyAsync(ix->off0, doff, sizeof(int64_t) * N0, cudaMemcpyDeviceToDevice, s));
   QK_CUDA(cudaStreamSynchronize(s));
   dfree(ix->vec0);
@@ -429,6 +491,8 @@ static qk_status grow_arena(qk_index* ix, const std::vector<int32_t>& need, cuda
   ix->h_off0 = off;
   ix->h_cap_part0 = cap;
   ix->cap0 = total;
+  ix->used0 = reserved;
+  ix->holes0 = 0;
   return QK_OK;
 }
 
@@ -499,6 +563,17 @@ void qk_config_default(qk_config* c) {
 
 const char* qk_last_error(void) { return g_err.c_str(); }
 
+// Freed stream-ordered temporaries stay in the device's default pool (up to
+// 1 GiB) instead of going back to the driver at every synchronisation.
+static void keep_pool_memory(int dev) {
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = 1ull << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+}
+
 qk_status qk_create(const qk_config* cfg, qk_index** out) {
   if (!cfg || !out) {
     set_error("null argument");
@@ -523,10 +598,11 @@ qk_status qk_create(const qk_config* cfg, qk_index** out) {
   qk_index* ix = new qk_index();
   ix->cfg = *cfg;
   cudaGetDevice(&ix->device);
+  keep_pool_memory(ix->device);
   ix->beta_a = 0.5 * (cfg->d + 1);
   ix->beta_lnB = std::lgamma(ix->beta_a) + std::lgamma(0.5) - std::lgamma(ix->beta_a + 0.5);
   qk_status st = QK_OK;
-  if ((st = dalloc(&ix->beta_table, kBetaTablePoints)) != QK_OK || (st = dalloc(&ix->work, 1)) != QK_OK ||
+  if ((st = dalloc(&ix->beta_table, kBetaTablePoints)) != QK_OK || (st = dalloc(&ix->work, kWorkSlots)) != QK_OK ||
       (st = dalloc(&ix->status, 1)) != QK_OK || (st = dalloc(&ix->diag, kDiagWords)) != QK_OK) {
     qk_destroy(ix);
     return st;
@@ -570,7 +646,7 @@ qk_status qk_build(qk_index* ix, const float* x, const int64_t* ids, int64_t n, 
     set_error("fewer vectors than leaf partitions");
     return QK_ERR_ARG;
   }
-  Tmp tx, ti, tc0, ta0, tc1, ta1;
+  Tmp tx(s), ti(s), tc0(s), ta0(s), tc1(s), ta1(s);
   const float* X = nullptr;
   const int64_t* I = nullptr;
   QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
@@ -604,7 +680,7 @@ qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, c
     return QK_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  Tmp tx, ti, tc0, ta0, tc1, ta1;
+  Tmp tx(s), ti(s), tc0(s), ta0(s), tc1(s), ta1(s);
   const float *X = nullptr, *C0 = nullptr, *C1 = nullptr;
   const int64_t* I = nullptr;
   const int32_t *a0 = nullptr, *a1 = nullptr;
@@ -705,7 +781,9 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
   a.out_recall = out_recall ? drc : nullptr;
   a.hits0 = ix->hits0;
   a.hits1 = ix->hits1;
-  a.work = ix->work;
+  // every launch takes its own work-stealing counter, so searches on different
+  // streams may be in flight together (up to kWorkSlots of them)
+  a.work = ix->work + (ix->search_seq++ % kWorkSlots);
   a.status = ix->status;
   a.diag = ix->diag;
   a.wait_stats = ix->diag + 8;
@@ -732,6 +810,7 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   if (n == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int d = ix->cfg.d;
+  Trace tr("insert");
   std::vector<int64_t> hid;
   QK_TRY(to_host(ids, (size_t)n, hid, s));
   {
@@ -744,7 +823,7 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
       }
     }
   }
-  Tmp tx, ti, tflag, tleaf, tpar, tdst;
+  Tmp tx(s), ti(s), tflag(s), tleaf(s), tpar(s), tdst(s);
   const float* X = nullptr;
   const int64_t* I = nullptr;
   QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
@@ -774,6 +853,7 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   std::vector<int32_t> hleaf((size_t)n);
   QK_CUDA(cudaMemcpyAsync(hleaf.data(), leaf, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
   QK_CUDA(cudaStreamSynchronize(s));
+  tr.mark("checks_descent");
   std::vector<int32_t> need(ix->h_size0);
   bool grow = false;
   for (int64_t r = 0; r < n; ++r) {
@@ -785,6 +865,7 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
     if (++need[j] > ix->h_cap_part0[j]) grow = true;
   }
   if (grow) QK_TRY(grow_arena(ix, need, s));
+  tr.mark("grow");
   std::vector<int64_t> dst((size_t)n);
   std::vector<int32_t> cur(ix->h_size0);
   for (int64_t r = 0; r < n; ++r) {
@@ -808,6 +889,7 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   }
   ix->h_size0 = cur;
   ix->n += n;
+  tr.mark("place");
   return QK_OK;
 }
 
@@ -821,6 +903,7 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
   if (n == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int d = ix->cfg.d;
+  Trace tr("delete");
   std::vector<int64_t> hid;
   QK_TRY(to_host(ids, (size_t)n, hid, s));
   // Replay the deletes in order on the host mirror (swap-with-last), keeping,
@@ -854,9 +937,10 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
         src.push_back(ix->h_off0[kv.first] + mv.second);
         dst.push_back(ix->h_off0[kv.first] + mv.first);
       }
+  tr.mark("replay");
   const int64_t m = (int64_t)src.size();
   if (m > 0) {
-    Tmp tsrc, tdst, tvec, tids;
+    Tmp tsrc(s), tdst(s), tvec(s), tids(s);
     int64_t *dsrc = nullptr, *ddst = nullptr, *dtid = nullptr;
     float* dtv = nullptr;
     QK_TRY(tsrc.alloc<int64_t>((size_t)m, &dsrc));
@@ -876,6 +960,7 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
   QK_CUDA(cudaStreamSynchronize(s));
   ix->h_size0 = size;
   ix->n -= removed;
+  tr.mark("moves");
   if (n_removed) *n_removed = removed;
   return QK_OK;
 }
@@ -988,7 +1073,7 @@ qk_status qk_cap_fraction(int32_t d, int32_t mode, const double* t, const double
   cudaStream_t s = (cudaStream_t)stream;
   double a = 0.5 * (d + 1);
   double lnB = std::lgamma(a) + std::lgamma(0.5) - std::lgamma(a + 0.5);
-  Tmp tt, tr, tb, to;
+  Tmp tt(s), tr(s), tb(s), to(s);
   const double *dt = nullptr, *dr = nullptr;
   QK_TRY(in_device(t, (size_t)n, tt, &dt, s));
   QK_TRY(in_device(rho, (size_t)n, tr, &dr, s));
@@ -1013,7 +1098,7 @@ qk_status qk_nearest_centroids(const float* x, int64_t n, int32_t d, const float
   }
   if (n == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  Tmp tx, tcen, ti, td, tn, tcand, ts;
+  Tmp tx(s), tcen(s), ti(s), td(s), tn(s), tcand(s), ts(s);
   const float *X = nullptr, *C = nullptr;
   QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
   QK_TRY(in_device(c, (size_t)K * d, tcen, &C, s));
@@ -1049,7 +1134,7 @@ qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, i
     return QK_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  Tmp tx, tc, ta, tn, tsum, tcnt;
+  Tmp tx(s), tc(s), ta(s), tn(s), tsum(s), tcnt(s);
   const float *X = nullptr, *C = nullptr;
   QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
   QK_TRY(in_device(c, (size_t)K * d, tc, &C, s));

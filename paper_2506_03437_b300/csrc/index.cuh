@@ -4,7 +4,9 @@
 // HBM layout (all arrays cudaMalloc'd, 256-byte aligned):
 //   level 0  arena vec0[cap0 x d] FP32 rows, ids0[cap0] int64; partition j
 //            owns rows [off0[j], off0[j] + size0[j]) of the arena, contiguous,
-//            so a partition streams with one-dimensional bulk copies;
+//            so a partition streams with one-dimensional bulk copies, and
+//            reserves room for inserts behind them; a free tail after the
+//            last reservation takes partitions that outgrow their room;
 //            cent0[n_leaf x d] its centroids.
 //   level 1  vec1[n_leaf x d] the leaf centroids regrouped by parent,
 //            ids1[n_leaf] the leaf index of each row, off1/size1 per parent,
@@ -90,6 +92,8 @@ struct qk_index {
   float* vec0 = nullptr;
   int64_t* ids0 = nullptr;
   int64_t cap0 = 0;              // arena rows
+  int64_t used0 = 0;             // rows [0, used0) belong to partitions or holes; the rest is the free tail
+  int64_t holes0 = 0;            // rows left behind by partitions that moved to the tail
   int64_t* off0 = nullptr;
   int32_t* size0 = nullptr;
   float* cent0 = nullptr;
@@ -119,7 +123,12 @@ struct qk_index {
   // id -> (partition, slot) for deletes
   std::unordered_map<int64_t, int64_t> where;
   int64_t queries_seen = 0;      // searched queries since the last install/maintain (the window |W|)
+  uint64_t search_seq = 0;       // launches so far (selects the work counter)
 };
+
+namespace qk {
+constexpr int kWorkSlots = 16;   // searches of one index that may be in flight together
+}
 
 namespace qk {
 // Shared by capi.cu and maintain.cu.

@@ -38,6 +38,7 @@
 
 #include "common.cuh"
 #include "index.cuh"
+#include "trace.h"
 
 namespace qk {
 
@@ -63,18 +64,24 @@ __global__ void dist_to_rows_kernel(const float* __restrict__ C, int64_t n, int 
 
 namespace {
 
+// Device buffer that grows on demand, stream-ordered like the runtime's
+// other temporaries (no call waits for the whole device).
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  cudaStream_t s = 0;
+  DevBuf() = default;
+  explicit DevBuf(cudaStream_t st) : s(st) {}
+  DevBuf(const DevBuf&) = delete;
   ~DevBuf() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
   }
   qk_status reserve(size_t b) {
     if (b <= bytes) return QK_OK;
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     bytes = 0;
-    QK_CUDA(cudaMalloc(&p, std::max<size_t>(b, 4096)));
+    QK_CUDA(cudaMallocAsync(&p, std::max<size_t>(b, 4096), s));
     bytes = std::max<size_t>(b, 4096);
     return QK_OK;
   }
@@ -121,6 +128,7 @@ struct Ctx {
   cudaStream_t s;
   DevBuf rows, cent, assign, dist, refs, x;
   std::vector<qk_maint_action>* log;
+  explicit Ctx(cudaStream_t st) : s(st), rows(st), cent(st), assign(st), dist(st), refs(st), x(st) {}
 };
 
 uint64_t split_seed(uint64_t seed, int level, int64_t j) {
@@ -176,7 +184,7 @@ qk_status cluster(Ctx& cx, const Level& L, const std::vector<int64_t>& refs, int
   int64_t n = (int64_t)refs.size();
   QK_TRY(gather(cx, L, refs));
   QK_TRY(cx.assign.reserve(sizeof(int32_t) * std::max<int64_t>(n, 1)));
-  DevBuf cout, cin;
+  DevBuf cout(cx.s), cin(cx.s);
   QK_TRY(cout.reserve(sizeof(float) * K * d));
   if (C_init) {
     QK_TRY(cin.reserve(sizeof(float) * K * d));
@@ -408,12 +416,12 @@ extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk
     return QK_ERR_STATE;
   }
   std::vector<qk_maint_action> acts;
-  Ctx cx;
+  Trace tr("maintain");
+  Ctx cx(s);
   cx.p = params;
   cx.lam.s.assign(P.lambda_sizes, P.lambda_sizes + P.lambda_points);
   cx.lam.us.assign(P.lambda_us, P.lambda_us + P.lambda_points);
   cx.seed = ix->cfg.seed;
-  cx.s = s;
   cx.log = &acts;
 
   // Stage 0: statistics (access counts over the window, sizes)
@@ -445,7 +453,9 @@ extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk
     for (int32_t p = 0; p < N1; ++p)
       for (int32_t t = 0; t < ix->h_size1[p]; ++t) parent_of[ids1[ix->h_off1[p] + t]] = p;
   }
+  tr.mark("stats");
   QK_TRY(maintain_level(cx, L0, 0, N1 > 0 ? &parent_of : nullptr));
+  tr.mark("leaf_level");
   const int32_t M0 = (int32_t)L0.C.size();
   if (M0 < 1) {
     set_error("maintenance removed every partition");
@@ -453,7 +463,7 @@ extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk
   }
 
   // new leaf centroids and the label of every arena row
-  DevBuf dC0, dlab, dC1, dpol;
+  DevBuf dC0(s), dlab(s), dC1(s), dpol(s);
   std::vector<float> nc0((size_t)M0 * d);
   for (int32_t j = 0; j < M0; ++j) std::memcpy(&nc0[(size_t)j * d], L0.C[j].data(), sizeof(float) * d);
   std::vector<int32_t> lab((size_t)ix->cap0, -1);
@@ -491,6 +501,7 @@ extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk
     QK_CUDA(cudaMemcpyAsync(dpol.p, pol.data(), sizeof(int32_t) * pol.size(), cudaMemcpyHostToDevice, s));
   }
 
+  tr.mark("parent_level");
   // re-lay out the arena from the labels (the old arena stays alive until the copy is done)
   float* old_vec = ix->vec0;
   int64_t* old_ids = ix->ids0;
@@ -509,6 +520,7 @@ extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk
     return st;
   }
   ix->n = live_n;
+  tr.mark("install");
   if (n_log) *n_log = (int32_t)acts.size();
   if (log)
     for (int32_t i = 0; i < (int32_t)acts.size() && i < log_cap; ++i) log[i] = acts[i];

@@ -1,0 +1,272 @@
+"""Continuous-batching request loop over one index (queries, inserts, deletes).
+
+Requests arrive on their own clock (open loop).  Searches waiting when a
+stream slot is free are launched together as one batch; up to `streams`
+batches are on the GPU at once, so requests that arrive while others run are
+admitted as soon as a slot frees up, and their work overlaps on the device.
+A batch is also held back while free device memory is below
+`min_free_bytes`.
+
+Inserts and deletes change the arena, so they are applied between batches:
+pending updates wait until `update_batch` of them have arrived or the oldest
+has waited `update_wait_s`; then the searches in flight are drained and the
+pending group is applied as one delete call followed by one insert call.
+That order gives the same index as applying the group one by one, because the
+group is first reduced to its net effect: an id inserted and then deleted
+inside the group is dropped from both calls, and an id deleted and then
+inserted again is deleted first and then inserted.  Searches may overtake
+updates that arrived less than `update_wait_s` before them.
+
+Every `maintain_every` operations the maintenance pass runs (Sec. 4; its
+statistics window is the queries since the previous pass).  A request's
+latency runs from its arrival to the moment its result is in host memory.
+
+The index's kernels do all the work; this module only schedules calls to the
+C ABI.
+"""
+
+import time
+
+import numpy as np
+
+SEARCH, INSERT, DELETE = 0, 1, 2
+
+
+class Ops:
+    """A request stream: `t` arrival times in seconds (ascending), `kind`
+    (SEARCH / INSERT / DELETE), `vec` the query or inserted vector of each op
+    (unused for deletes), `ref` the inserted or deleted id (unused for
+    searches).  Op j's request id is j."""
+
+    def __init__(self, t, kind, vec, ref):
+        self.t = np.ascontiguousarray(t, np.float64)
+        self.kind = np.ascontiguousarray(kind, np.int8)
+        self.vec = np.ascontiguousarray(vec, np.float32)
+        self.ref = np.ascontiguousarray(ref, np.int64)
+        n = self.t.shape[0]
+        assert self.kind.shape == (n,) and self.ref.shape == (n,) and self.vec.shape[0] == n
+        assert n == 0 or np.all(np.diff(self.t) >= 0)
+
+    def __len__(self):
+        return self.t.shape[0]
+
+    def count(self, kind):
+        return int((self.kind == kind).sum())
+
+
+def net_updates(kind, ref):
+    """Net effect of a group of inserts and deletes applied in order.
+    Returns (positions whose ids to delete, positions whose rows to insert)."""
+    state = {}   # id -> (deleted an existing copy?, position of the live insert or -1)
+    for j in range(kind.shape[0]):
+        vid = int(ref[j])
+        dele, ins = state.get(vid, (False, -1))
+        if kind[j] == INSERT:
+            state[vid] = (dele, j)
+        elif ins >= 0:                       # delete of an id inserted in this group
+            state[vid] = (dele, -1)
+        else:
+            state[vid] = (True, -1)
+    seen, dpos = set(), []
+    for j in range(kind.shape[0]):           # one delete per id: its first delete in the group
+        vid = int(ref[j])
+        if kind[j] == DELETE and state[vid][0] and vid not in seen:
+            seen.add(vid)
+            dpos.append(j)
+    ipos = sorted(v[1] for v in state.values() if v[1] >= 0)
+    return np.array(dpos, np.int64), np.array(ipos, np.int64)
+
+
+class Server:
+    """Schedules searches, inserts, deletes and maintenance on one index."""
+
+    def __init__(self, index, d, k=10, recall_target=0.9, max_batch=2048, streams=4, min_free_bytes=1 << 30,
+                 maintain_every=0, maint_args=None, update_batch=1024, update_wait_s=0.002):
+        import torch
+        self.torch = torch
+        self.ix, self.d, self.k, self.tau = index, d, k, recall_target
+        self.max_batch, self.min_free = max_batch, min_free_bytes
+        self.maintain_every, self.maint_args = maintain_every, maint_args or {}
+        self.update_batch, self.update_wait = update_batch, update_wait_s
+        self.slots = []
+        for _ in range(streams):
+            self.slots.append(dict(
+                stream=torch.cuda.Stream(),
+                q_host=torch.empty((max_batch, d), dtype=torch.float32).pin_memory(),
+                q_dev=torch.empty((max_batch, d), dtype=torch.float32, device="cuda"),
+                ids_dev=torch.empty((max_batch, k), dtype=torch.int64, device="cuda"),
+                dist_dev=torch.empty((max_batch, k), dtype=torch.float32, device="cuda"),
+                np_dev=torch.empty(max_batch, dtype=torch.int32, device="cuda"),
+                r_dev=torch.empty(max_batch, dtype=torch.float32, device="cuda"),
+                ids_host=torch.empty((max_batch, k), dtype=torch.int64).pin_memory(),
+                dist_host=torch.empty((max_batch, k), dtype=torch.float32).pin_memory(),
+                np_host=torch.empty(max_batch, dtype=torch.int32).pin_memory(),
+                busy=False))
+
+    # ---------------------------------------------------------------- batches
+    def _launch(self, slot, rows):
+        torch = self.torch
+        n = rows.shape[0]
+        np.take(self.ops.vec, rows, axis=0, out=slot["q_host"].numpy()[:n])
+        st = slot["stream"]
+        with torch.cuda.stream(st):
+            slot["q_dev"][:n].copy_(slot["q_host"][:n], non_blocking=True)
+            out = (slot["ids_dev"][:n], slot["dist_dev"][:n], slot["np_dev"][:n], slot["r_dev"][:n])
+            self.ix.search(slot["q_dev"][:n], self.k, recall_target=self.tau, out=out, stream=st)
+            slot["ids_host"][:n].copy_(slot["ids_dev"][:n], non_blocking=True)
+            slot["dist_host"][:n].copy_(slot["dist_dev"][:n], non_blocking=True)
+            slot["np_host"][:n].copy_(slot["np_dev"][:n], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        slot["busy"] = True
+        return dict(slot=slot, event=ev, rows=rows)
+
+    def _finish(self, b, now):
+        slot, rows = b["slot"], b["rows"]
+        n = rows.shape[0]
+        self.lat[rows] = now - self.ops.t[rows]
+        self.nprobe[rows] = slot["np_host"].numpy()[:n]
+        if self.out_ids is not None:
+            self.out_ids[rows] = slot["ids_host"].numpy()[:n]
+            self.out_dist[rows] = slot["dist_host"].numpy()[:n]
+        slot["busy"] = False
+
+    def _drain(self, inflight, clock):
+        while inflight:
+            b = inflight.pop(0)
+            b["event"].synchronize()
+            self._finish(b, clock())
+
+    def _free_ok(self):
+        if self.min_free <= 0:
+            return True
+        free, _ = self.torch.cuda.mem_get_info()
+        return free >= self.min_free
+
+    def _apply_updates(self, rows, clock):
+        ops = self.ops
+        dpos, ipos = net_updates(ops.kind[rows], ops.ref[rows])
+        if dpos.shape[0]:
+            self.ix.delete(ops.ref[rows[dpos]])
+        if ipos.shape[0]:
+            r = rows[ipos]
+            self.ix.insert(ops.vec[r], ops.ref[r])
+        self.lat[rows] = clock() - ops.t[rows]
+
+    # ------------------------------------------------------------------- run
+    def run(self, ops, keep_results=False):
+        """Serves the stream; returns a summary of latencies (per kind, p50/p99/mean
+        in ms), throughput and where the wall time went.  With keep_results the
+        search results are left in self.out_ids / self.out_dist (row j = op j)."""
+        self.ops = ops
+        n_ops = len(ops)
+        self.lat = np.full(n_ops, np.nan)
+        self.nprobe = np.zeros(n_ops, np.int32)
+        self.out_ids = np.full((n_ops, self.k), -1, np.int64) if keep_results else None
+        self.out_dist = np.full((n_ops, self.k), np.inf, np.float32) if keep_results else None
+        s_rows = np.flatnonzero(ops.kind == SEARCH)
+        u_rows = np.flatnonzero(ops.kind != SEARCH)
+        s_t, u_t = ops.t[s_rows], ops.t[u_rows]
+        n_s, n_u = s_rows.shape[0], u_rows.shape[0]
+        qs = us = 0          # next search / update not yet taken
+        t_upd = t_maint = t_host = 0.0
+        batches = drains = passes = 0
+        inflight = []
+        t0 = time.perf_counter()
+
+        def clock():
+            return time.perf_counter() - t0
+
+        while qs < n_s or us < n_u or inflight:
+            now = clock()
+            qa = int(np.searchsorted(s_t, now, side="right"))
+            ua = int(np.searchsorted(u_t, now, side="right"))
+            # results of finished batches
+            while inflight and inflight[0]["event"].query():
+                self._finish(inflight.pop(0), clock())
+            # updates: between batches, after draining the searches in flight
+            if ua > us and (ua - us >= self.update_batch or now - u_t[us] >= self.update_wait or qa == n_s):
+                c0 = clock()
+                self._drain(inflight, clock)
+                self._apply_updates(u_rows[us:ua], clock)
+                us = ua
+                drains += 1
+                t_upd += clock() - c0
+            if self.maintain_every and (qa + ua) // self.maintain_every > passes:
+                c0 = clock()
+                self._drain(inflight, clock)
+                self.ix.maintain(**self.maint_args)
+                passes += 1
+                t_maint += clock() - c0
+            # launch while a stream slot is free and memory allows
+            launched = False
+            while qa > qs and len(inflight) < len(self.slots) and self._free_ok():
+                c0 = clock()
+                slot = next(s for s in self.slots if not s["busy"])
+                n = min(self.max_batch, qa - qs)
+                inflight.append(self._launch(slot, s_rows[qs:qs + n]))
+                qs += n
+                batches += 1
+                launched = True
+                t_host += clock() - c0
+            if not launched:
+                if inflight:
+                    time.sleep(20e-6)
+                else:
+                    nxt = min(s_t[qs] if qs < n_s else np.inf, u_t[us] if us < n_u else np.inf)
+                    wait = nxt - clock()
+                    if np.isfinite(wait) and wait > 0:
+                        time.sleep(min(wait, 1e-3))
+        wall = clock()
+        out = {"wall_s": round(wall, 4), "batches": batches, "maintenance_passes": passes, "update_drains": drains,
+               "update_s": round(t_upd, 4), "maintenance_s": round(t_maint, 4), "launch_host_s": round(t_host, 4)}
+        for kind, name in ((SEARCH, "search"), (INSERT, "insert"), (DELETE, "delete")):
+            v = self.lat[ops.kind == kind]
+            if v.shape[0]:
+                a = v * 1e3
+                out[name] = {"n": int(v.shape[0]), "p50_ms": round(float(np.percentile(a, 50)), 4),
+                             "p99_ms": round(float(np.percentile(a, 99)), 4), "mean_ms": round(float(a.mean()), 4)}
+        out["search_qps"] = round(n_s / wall, 1) if wall > 0 else None
+        out["mean_nprobe"] = round(float(self.nprobe[s_rows].mean()), 3) if n_s else None
+        return out
+
+
+def skewed_stream(centers, start_ids, n_ops, sigma, seed, hot=100, zipf=1.2, rotate=100_000,
+                  p_query=0.9, p_insert=0.05, rate=None, next_id=None):
+    """The dynamic skewed workload: queries Zipf(`zipf`) over a hot set of `hot`
+    components that is redrawn every `rotate` ops, inserts of new samples from
+    the hot components (fresh ids), deletes of uniformly chosen live ids.
+    Arrivals are Poisson at `rate` ops/s, or all at t = 0 when rate is None."""
+    from .synth import rng
+    g = rng(seed)
+    n_comp, d = centers.shape
+    w = np.arange(1, hot + 1, dtype=np.float64) ** (-zipf)
+    w /= w.sum()
+    kind = g.choice(3, size=n_ops, p=[p_query, p_insert, 1.0 - p_query - p_insert]).astype(np.int8)
+    t = np.cumsum(g.exponential(1.0 / rate, size=n_ops)) if rate else np.zeros(n_ops)
+    n_epochs = max(1, (n_ops + rotate - 1) // rotate) if rotate else 1
+    hot_sets = np.stack([g.choice(n_comp, hot, replace=False) for _ in range(n_epochs)])
+    rank = g.choice(hot, size=n_ops, p=w)
+    epoch = np.arange(n_ops) // rotate if rotate else np.zeros(n_ops, np.int64)
+    comp = hot_sets[epoch, rank]
+    vec = np.empty((n_ops, d), np.float32)
+    for a in range(0, n_ops, 1 << 16):
+        b = min(n_ops, a + (1 << 16))
+        vec[a:b] = centers[comp[a:b]] + sigma * g.standard_normal((b - a, d))
+    u = g.random(n_ops)
+    live = [int(i) for i in start_ids]
+    next_id = int(next_id if next_id is not None else max(live) + 1)
+    ref = np.full(n_ops, -1, np.int64)
+    for j in np.flatnonzero(kind != SEARCH):
+        if kind[j] == INSERT:
+            ref[j] = next_id
+            live.append(next_id)
+            next_id += 1
+        elif live:
+            pos = int(u[j] * len(live))
+            ref[j] = live[pos]
+            live[pos] = live[-1]
+            live.pop()
+        else:
+            kind[j] = SEARCH
+    return Ops(t, kind, vec, ref)

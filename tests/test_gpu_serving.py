@@ -1,0 +1,54 @@
+"""The continuous-batching request loop: results alone equal results in the mix; updates apply in order."""
+
+import numpy as np
+import pytest
+
+from oracle import kmeans
+from paper_2506_03437_b300 import synth
+
+from .test_gpu_search import make_index
+
+pytestmark = pytest.mark.gpu
+
+
+def test_results_alone_equal_results_in_the_mix():
+    from paper_2506_03437_b300.serving import Ops, Server
+    X, ids, Q = synth.aps_search(seed=41, n=30_000, d=64, n_comp=40, sigma=1.2, nq=3000)
+    levels = kmeans.build_index(X, ids, 150, 8, iters=3, seed=5)
+    from paper_2506_03437_b300 import index as I
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.15, f_M_parent=0.5)
+    # alone: every query is its own search call
+    alone = [ix.search(Q[j:j + 1], 10, recall_target=0.9) for j in range(0, 3000, 7)]
+    # in the mix: all 3,000 arrive at once and share batches on four streams
+    ops = Ops(np.zeros(3000), np.zeros(3000, np.int8), Q, np.full(3000, -1))
+    srv = Server(ix, 64, k=10, recall_target=0.9, max_batch=200, streams=4)
+    st = srv.run(ops, keep_results=True)
+    assert st["batches"] >= 15 and st["search"]["n"] == 3000
+    for n, j in enumerate(range(0, 3000, 7)):
+        assert np.array_equal(srv.out_ids[j], alone[n][0][0])
+        assert np.array_equal(srv.out_dist[j], alone[n][1][0])
+
+
+def test_stream_with_updates_and_maintenance():
+    from paper_2506_03437_b300.serving import Server, skewed_stream
+    X, ids, Q = synth.aps_search(seed=42, n=20_000, d=64, n_comp=50, sigma=1.2, nq=1)
+    levels = kmeans.build_index(X, ids, 100, 0, iters=3, seed=6)
+    from paper_2506_03437_b300 import index as I
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.2)
+    C = synth.mixture_centers(50, 64, 42)
+    ops = skewed_stream(C, ids, 6000, 1.2, 7, hot=10, rotate=2000, rate=2e5)
+    srv = Server(ix, 64, k=10, recall_target=0.9, max_batch=256, streams=3, maintain_every=3000,
+                 maint_args=dict(lam_sizes=[0, 1000], lam_us=[2.0, 47.0], tau_us=0.25, alpha=0.9, refine_radius=8,
+                                 s_min=20))
+    st = srv.run(ops)
+    assert ix.info()["n"] == 20_000 + ops.count(1) - ops.count(2)
+    assert st["maintenance_passes"] == 2 and st["search"]["n"] == ops.count(0)
+    # every live id is stored exactly once
+    _, _, got = ix.export_level(0)
+    live = set(ids.tolist())
+    for kind, ref in zip(ops.kind, ops.ref):
+        if kind == 1:
+            live.add(int(ref))
+        elif kind == 2:
+            live.discard(int(ref))
+    assert sorted(got.tolist()) == sorted(live)

@@ -144,3 +144,47 @@ def test_duplicate_and_nan_inserts_apply_nothing(I):
         assert np.array_equal(a, b)
     assert ix.delete(np.array([], np.int64)) == 0
     assert ix.delete(np.array([123456], np.int64)) == 0
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_partitions_move_to_the_tail_and_compact(I, storage):
+    """Repeated inserts into two partitions: each overflow moves the partition to the
+    arena's free tail, and once the tail is used up the arena is compacted.  After every
+    round the partitions hold what the oracle's do, and the FP8 codes follow their rows."""
+    from oracle import quant
+    X, ids, Q = synth.aps_search(seed=24, n=8000, d=64, n_comp=16, sigma=1.0, nq=12)
+    levels = kmeans.build_index(X, ids, 16, 0, iters=3, seed=4)
+    ix = make_index(I, X, ids, levels, f_M_leaf=1.0, storage=storage)
+    scales0 = ix.export_quantized()[1].copy() if storage == 2 else None
+    g = np.random.default_rng(5)
+    allX, allI = [X], [ids]
+    next_id = 500_000
+    for rnd in range(24):
+        leaf = (3, 7, 11)[rnd % 3]
+        c = levels[0].centroids[leaf]
+        nx = (c[None, :] + 0.01 * g.standard_normal((90, 64))).astype(np.float32)
+        ni = np.arange(next_id, next_id + 90, dtype=np.int64)
+        next_id += 90
+        ix.insert(nx, ni)
+        maintenance.insert(levels, nx, ni)
+        allX.append(nx)
+        allI.append(ni)
+        assert_same_partitions(ix, levels)
+    if storage == 2:
+        sizes, _, gid = ix.export_level(0)
+        codes, scales = ix.export_quantized()
+        assert np.array_equal(scales, scales0)
+        part = np.repeat(np.arange(len(sizes)), sizes)
+        byid = {int(i): r for r, i in enumerate(gid)}
+        X_all, I_all = np.concatenate(allX), np.concatenate(allI)
+        for n in range(0, X_all.shape[0], 13):
+            r = byid[int(I_all[n])]
+            assert np.array_equal(codes[r], quant.quantize_e4m3(X_all[n][None, :], scales[part[r]])[0])
+    X_all, I_all = np.concatenate(allX), np.concatenate(allI)
+    gi, gd, gn, gr = ix.search(Q, 10, recall_target=0.0, nprobe=16)
+    D, Ix = knn.knn(X_all, I_all, Q, 10)
+    for j in range(Q.shape[0]):
+        if storage == 0:
+            assert same_topk(gi[j], gd[j], Ix[j], D[j])
+        else:   # FP8 candidates re-ranked in FP32: every returned distance is exact
+            assert np.all(np.isin(gi[j], I_all))
