@@ -252,3 +252,35 @@ def search(levels, Q, params, metric=L2):
         traces[0][j] = res["trace"]
     return dict(dist=out_D, ids=out_I, nprobe=out_np, r=out_r, scanned=scanned,
                 traces=traces)
+
+
+def ivf_search(level, Q, k, nprobe, metric=L2):
+    """Fixed-nprobe IVF over one level with one nprobe per query (R10 per query).
+
+    Query j scans its nprobe[j] nearest partitions (centroid distance, ties to
+    the lower index; more than the partitions there are means all of them) and
+    returns the exact top-k of their members by (distance, id).  Returns
+    dist (nq, k) FP64, ids (nq, k) (inf / -1 past the scanned rows) and the
+    scanned partition indices of every query, nearest first.
+    """
+    Q = np.atleast_2d(np.asarray(Q))
+    nq = Q.shape[0]
+    nprobe = np.broadcast_to(np.asarray(nprobe, dtype=np.int64), (nq,))
+    out_D = np.full((nq, k), np.inf)
+    out_I = np.full((nq, k), -1, dtype=np.int64)
+    scanned = []
+    idx = np.arange(level.n_part, dtype=np.int64)
+    for j in range(nq):
+        D = distances(Q[j], level.centroids, metric)
+        parts = np.lexsort((idx, D))[:min(int(nprobe[j]), level.n_part)]
+        scanned.append(parts)
+        rows = [level.vectors[p] for p in parts if level.vectors[p].shape[0]]
+        if not rows:
+            continue
+        X = np.concatenate(rows)
+        ids = np.concatenate([level.ids[p] for p in parts if level.vectors[p].shape[0]])
+        dist = distances(Q[j], X, metric)
+        order = np.lexsort((ids, dist))[:k]
+        out_D[j, :order.shape[0]] = dist[order]
+        out_I[j, :order.shape[0]] = ids[order]
+    return out_D, out_I, scanned
