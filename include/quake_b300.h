@@ -343,6 +343,97 @@ qk_status qk_maintain(qk_index* index, const qk_maint_params* params, qk_maint_a
 qk_status qk_kmeans_step_noalloc(const float* x, int64_t n, int32_t d, const float* c, int32_t K,
                                  float* c_new, int32_t* assign, int32_t* counts, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched fixed-nprobe search (Sec. 3 top-down search with a fixed nprobe per
+ * query, for a batch of queries each with its own nprobe; single level: the
+ * nprobe nearest leaf centroids of each query are scanned).
+ *
+ * A plan owns the device workspace of batches of up to max_nq queries with
+ * k results and nprobe values up to max_nprobe, so that a batch allocates
+ * nothing and never waits on the host: the whole batch is one fixed sequence
+ * of device steps, which qk_batch_capture records as one CUDA graph.
+ *
+ * Steps of a batch (all on the GPU):
+ *   1. approximate distances of every query to every leaf centroid on the
+ *      tensor cores (tcgen05, TF32 operands, FP32 accumulation);
+ *   2. per query, the nprobe nearest centroids by exact FP32 distance: every
+ *      centroid whose approximate distance is within a bound of the TF32
+ *      error of the nprobe-th one is re-scored exactly, ties to the lower
+ *      index, so the selection equals an exact FP32 selection;
+ *   3. the (query, partition) pairs grouped by partition into units of one
+ *      partition x G queries x chunk_rows rows, largest partitions first;
+ *   4. one persistent launch scans the units: each row tile is read once from
+ *      HBM for the unit's G queries, each query keeping its top-k;
+ *   5. per query, the top-k over its units by (distance, id).
+ * Distances are FP32 squared L2 from the direct differences.  Outputs are
+ * nq x k rows sorted by (distance, id); a query whose scanned partitions hold
+ * fewer than k rows gets (id -1, +inf) in the remaining slots.
+ *
+ * Conventions: every buffer is 16-byte aligned device memory; calls are
+ * stream-ordered and return before the GPU finishes; device-side errors
+ * (an nprobe outside [1, max_nprobe], a bounded wait that expired) are
+ * recorded in the index's status word and reported by qk_check.  A plan
+ * follows the index's inserts, deletes and maintenance by itself on the next
+ * qk_batch_search; a captured graph does not (qk_batch_replay then returns
+ * QK_ERR_STATE: capture again).  Calls on one plan must not overlap.  L2
+ * metric and FP32 storage only.
+ * ------------------------------------------------------------------------ */
+typedef struct qk_batch qk_batch;
+
+/* Tile shapes of the grouped scan. */
+typedef struct {
+  int32_t queries_per_warp;  /* 1, 2 or 4 (4 needs d <= 512): G = 8 x this queries per unit */
+  int32_t tile_rows;         /* rows per shared-memory tile (3 tiles in flight, <= 200 KB together) */
+  int32_t chunk_rows;        /* rows per unit (>= tile_rows, >= 1024) */
+} qk_batch_tiles;
+
+/* Creates a plan for the (built or loaded) index.  max_nq >= 1, 1 <= k <= 32,
+ * 1 <= max_nprobe <= 2048.  Errors: QK_ERR_ARG (sizes, IP metric or
+ * low-precision storage), QK_ERR_STATE (empty index), QK_ERR_OOM. */
+qk_status qk_batch_create(qk_index* index, int64_t max_nq, int32_t k, int32_t max_nprobe, qk_batch** out);
+void qk_batch_destroy(qk_batch* plan);
+
+/* Current tile shapes / set them (QK_ERR_ARG for an invalid shape). */
+qk_status qk_batch_get_tiles(const qk_batch* plan, qk_batch_tiles* out);
+qk_status qk_batch_set_tiles(qk_batch* plan, const qk_batch_tiles* tiles);
+
+/* One batch: q (nq x d FP32), nprobe[nq] (int32, each in [1, max_nprobe];
+ * values above the number of leaves scan every leaf), out_ids (nq x k int64),
+ * out_dist (nq x k FP32).  0 <= nq <= max_nq. */
+qk_status qk_batch_search(qk_batch* plan, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
+                          float* out_dist, void* stream);
+
+/* Runs the batch once, then records it on `stream` (a created stream, not
+ * the legacy default stream) as a CUDA graph bound to these buffers. */
+qk_status qk_batch_capture(qk_batch* plan, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
+                           float* out_dist, void* stream);
+/* Launches the captured graph on `stream`. */
+qk_status qk_batch_replay(qk_batch* plan, void* stream);
+
+/* Times every valid tile shape (queries_per_warp x tile_rows x chunk_rows
+ * from {1,2,4} x {16,32,64} x {1024,4096,16384}) on this batch, reps runs
+ * each after one warm-up, keeps the fastest in the plan and returns it.
+ * Synchronises the stream. */
+qk_status qk_batch_autotune(qk_batch* plan, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
+                            float* out_dist, int32_t reps, qk_batch_tiles* chosen, void* stream);
+
+/* Stage timing of uncaptured batches: with timing on, qk_batch_search records
+ * CUDA events on its stream between its steps; qk_batch_stage_times waits for
+ * the last batch and writes five durations in milliseconds: centroid scoring
+ * (norms + tensor-core distances), selection, grouping, grouped scan, merge.
+ * QK_ERR_STATE if no batch ran with timing on. */
+qk_status qk_batch_set_timing(qk_batch* plan, int32_t on);
+qk_status qk_batch_stage_times(qk_batch* plan, float* ms);
+
+/* Fixed-nprobe search with one nprobe per query through the per-query search
+ * kernel (one CTA per query; the comparison point of the batched path):
+ * like qk_search with recall_target <= 0, but query i scans its nprobe[i]
+ * nearest leaves.  nprobe may be host or device memory (read on the host:
+ * the call synchronises on a device array); every value >= 1.  Single-level
+ * index only (QK_ERR_STATE otherwise). */
+qk_status qk_search_nprobe(qk_index* index, const float* q, int64_t nq, int32_t k, const int32_t* nprobe,
+                           int64_t* out_ids, float* out_dist, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

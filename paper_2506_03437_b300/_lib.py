@@ -25,6 +25,9 @@ EXPORTS = [
     "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load",
     "qk_search", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_export_quantized", "qk_get_hits", "qk_cap_fraction",
     "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain", "qk_nearest_centroids",
+    "qk_search_nprobe", "qk_batch_create", "qk_batch_destroy", "qk_batch_get_tiles", "qk_batch_set_tiles",
+    "qk_batch_search", "qk_batch_capture", "qk_batch_replay", "qk_batch_autotune", "qk_batch_set_timing",
+    "qk_batch_stage_times",
 ]
 
 
@@ -49,6 +52,10 @@ class QkMaintParams(C.Structure):
 class QkMaintAction(C.Structure):
     _fields_ = [("level", C.c_int32), ("kind", C.c_int32), ("partition", C.c_int32),
                 ("committed", C.c_int32), ("estimate", C.c_double), ("delta", C.c_double)]
+
+
+class QkBatchTiles(C.Structure):
+    _fields_ = [("queries_per_warp", C.c_int32), ("tile_rows", C.c_int32), ("chunk_rows", C.c_int32)]
 
 
 class QkError(RuntimeError):
@@ -83,6 +90,17 @@ def _load():
         "qk_kmeans_step_noalloc": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, vp]),
         "qk_maintain": (i32, [vp, C.POINTER(QkMaintParams), C.POINTER(QkMaintAction), i32,
                               C.POINTER(C.c_int32), vp]),
+        "qk_search_nprobe": (i32, [vp, vp, i64, i32, vp, vp, vp, vp]),
+        "qk_batch_create": (i32, [vp, i64, i32, i32, C.POINTER(vp)]),
+        "qk_batch_destroy": (None, [vp]),
+        "qk_batch_get_tiles": (i32, [vp, C.POINTER(QkBatchTiles)]),
+        "qk_batch_set_tiles": (i32, [vp, C.POINTER(QkBatchTiles)]),
+        "qk_batch_search": (i32, [vp, vp, i64, vp, vp, vp, vp]),
+        "qk_batch_capture": (i32, [vp, vp, i64, vp, vp, vp, vp]),
+        "qk_batch_replay": (i32, [vp, vp]),
+        "qk_batch_set_timing": (i32, [vp, i32]),
+        "qk_batch_stage_times": (i32, [vp, vp]),
+        "qk_batch_autotune": (i32, [vp, vp, i64, vp, vp, vp, i32, C.POINTER(QkBatchTiles), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -294,6 +294,7 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
     }
   }
   tr.mark("id_map");
+  ++ix->version;
   ix->n = n;
   ix->n_leaf = N0;
   ix->n_parent = N1;
@@ -533,6 +534,10 @@ static qk_status read_device_status(qk_index* ix, cudaStream_t s) {
     set_error("a bounded device wait expired: " + what);
     return QK_ERR_TIMEOUT;
   }
+  if (st == DEV_BAD_ARG) {   // an argument only the device reads (a per-query nprobe, a buffer bound)
+    set_error("invalid argument found on the device: " + what);
+    return QK_ERR_ARG;
+  }
   set_error("internal consistency check failed: " + what);
   return QK_ERR_INTERNAL;
 }
@@ -695,8 +700,11 @@ qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, c
   return install(ix, X, I, n, C0, a0, C1, a1, s, false);
 }
 
-qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
-                    int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall, void* stream) {
+// The search of qk_search; nprobe_q (device, optional) gives fixed-nprobe
+// mode one nprobe per query, nprobe then being their maximum.
+static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
+                             const int32_t* nprobe_q, int64_t* out_ids, float* out_dist, int32_t* out_nprobe,
+                             float* out_recall, void* stream) {
   QK_TRY(check_ready(ix));
   if (nq < 0 || k < 1 || k > 1024 || (nq > 0 && (!q || !out_ids || !out_dist))) {
     set_error("invalid search arguments");
@@ -751,6 +759,7 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
   a.lv[1] = DevLevel{ix->vec1, ix->ids1, ix->off1, ix->size1, ix->cent1, ix->n_parent};
   const bool fixed = !(recall_target > 0.f);
   a.fixed_nprobe = fixed ? nprobe : 0;
+  a.nprobe_q = fixed ? nprobe_q : nullptr;
   if (a.L == 1) {
     a.root = ix->cent0;
     a.n_root = ix->n_leaf;
@@ -799,6 +808,40 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
     return read_device_status(ix, s);
   }
   return QK_OK;
+}
+
+qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
+                    int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall, void* stream) {
+  return search_impl(ix, q, nq, k, recall_target, nprobe, nullptr, out_ids, out_dist, out_nprobe, out_recall, stream);
+}
+
+qk_status qk_search_nprobe(qk_index* ix, const float* q, int64_t nq, int32_t k, const int32_t* nprobe,
+                           int64_t* out_ids, float* out_dist, void* stream) {
+  QK_TRY(check_ready(ix));
+  if (ix->n_parent != 0) {
+    set_error("per-query nprobe needs a single-level index");
+    return QK_ERR_STATE;
+  }
+  if (nq < 0 || (nq > 0 && !nprobe)) {
+    set_error("invalid search arguments");
+    return QK_ERR_ARG;
+  }
+  if (nq == 0) return QK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int32_t> h;
+  QK_TRY(to_host(nprobe, (size_t)nq, h, s));
+  int32_t mx = 0;
+  for (int32_t v : h) {
+    if (v < 1) {
+      set_error("every nprobe must be >= 1");
+      return QK_ERR_ARG;
+    }
+    mx = std::max(mx, v);
+  }
+  Tmp tn(s);
+  const int32_t* dn = nullptr;
+  QK_TRY(in_device(nprobe, (size_t)nq, tn, &dn, s));
+  return search_impl(ix, q, nq, k, 0.0f, std::min(mx, ix->n_leaf), dn, out_ids, out_dist, nullptr, nullptr, stream);
 }
 
 qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n, void* stream) {
@@ -889,6 +932,7 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   }
   ix->h_size0 = cur;
   ix->n += n;
+  ++ix->version;
   tr.mark("place");
   return QK_OK;
 }
@@ -960,6 +1004,7 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
   QK_CUDA(cudaStreamSynchronize(s));
   ix->h_size0 = size;
   ix->n -= removed;
+  ++ix->version;
   tr.mark("moves");
   if (n_removed) *n_removed = removed;
   return QK_OK;

@@ -56,6 +56,7 @@ struct SearchArgs {
   double tau1 = 0.99;            // recall target of level 1
   double tau_rho = 0.01;
   int32_t fixed_nprobe = 0;      // > 0: fixed-nprobe mode at level 0
+  const int32_t* nprobe_q = nullptr;   // fixed-nprobe mode: one nprobe per query (else fixed_nprobe)
   int32_t beta_mode = 0;
   const double* beta_table = nullptr;
   double beta_a = 0.0, beta_lnB = 0.0;
@@ -124,6 +125,7 @@ struct qk_index {
   std::unordered_map<int64_t, int64_t> where;
   int64_t queries_seen = 0;      // searched queries since the last install/maintain (the window |W|)
   uint64_t search_seq = 0;       // launches so far (selects the work counter)
+  uint64_t version = 0;          // bumped by every change of the partitions (install, insert, delete)
 };
 
 namespace qk {

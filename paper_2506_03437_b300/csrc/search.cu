@@ -822,8 +822,8 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
       b.aps(args.lv[1], M, args.k1, args.k1, args.tau1, 0, args.hits1, 0, args.lv[0].cent, r, np);
       M = b.take_candidates();
     }
-    b.aps(args.lv[0], M, args.k0, args.kq, args.tau0, args.fixed_nprobe, args.hits0, args.mode0, args.lv[0].vec, r,
-          np);
+    const int fixed = args.nprobe_q ? args.nprobe_q[qi] : args.fixed_nprobe;
+    b.aps(args.lv[0], M, args.k0, args.kq, args.tau0, fixed, args.hits0, args.mode0, args.lv[0].vec, r, np);
     if (b.aborted) break;
     if (args.mode0 != 0) b.rerank(args.lv[0].vec, args.lv[0].ids);
     int rc = sc.r_count;

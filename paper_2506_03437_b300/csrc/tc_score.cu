@@ -20,6 +20,8 @@
 // let the loads of slice s+1 overlap the MMAs of slice s.  The epilogue reads
 // the accumulator with tcgen05.ld (each warp its 32 TMEM lanes = 32 rows).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 #include <stdint.h>
 
@@ -127,13 +129,18 @@ __global__ void row_norms_kernel(const float* __restrict__ C, int64_t K, int d, 
   if (lane == 0) out[w] = acc;
 }
 
-// Approximate top-T candidates per row (see the file comment).
-template <int T>
+// Approximate top-T candidates per row (see the file comment).  With kStore
+// the epilogue instead writes every approximate distance to dout (row r,
+// centroid c at dout[r * ldd + c]), and blockIdx.y selects the range of
+// `span` centroids (a multiple of the tile width) that this CTA sweeps.
+template <int T, bool kStore>
 __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float* __restrict__ X, int64_t n, int d,
                                                                      const float* __restrict__ C, int K,
                                                                      const float* __restrict__ cnorm, int metric,
                                                                      int32_t* __restrict__ cand,
-                                                                     int32_t* __restrict__ status) {
+                                                                     int32_t* __restrict__ status,
+                                                                     float* __restrict__ dout, int64_t ldd,
+                                                                     int span) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
   float* scn = reinterpret_cast<float*>(smem + 2 * (kSliceA + kSliceB));   // ||c||^2 of the tile
@@ -165,11 +172,13 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
     bi[i] = -1;
   }
   const int nslices = d / kKS;
+  const int n_begin = kStore ? (int)blockIdx.y * span : 0;
+  const int n_end = kStore ? min(K, n_begin + span) : K;
   uint32_t phase[2] = {0u, 0u};
   uint32_t issued[2] = {0u, 0u};   // commits outstanding per buffer (0 or 1)
   bool ok = true;
 
-  for (int n0 = 0; n0 < K && ok; n0 += kN) {
+  for (int n0 = n_begin; n0 < n_end && ok; n0 += kN) {
     for (int ks = 0; ks < nslices; ++ks) {
       const int b = ks & 1;
       // the buffer is free once the MMAs that read it have completed
@@ -241,6 +250,23 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
     for (int c0 = half * (kN / 2); c0 < (half + 1) * (kN / 2); c0 += 8) {
       float v[8];
       tc::tmem_ld8(lane_addr + c0, v);
+      if (kStore) {
+        float o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) o[i] = metric == QK_METRIC_L2 ? fmaf(-2.f, v[i], scn[c0 + i]) : -v[i];
+        if (my_row < n) {
+          float* dst = dout + my_row * ldd + n0 + c0;
+          if (n0 + c0 + 8 <= K && (ldd & 3) == 0) {   // 16-byte aligned: ldd and n0 + c0 are multiples of 4
+            reinterpret_cast<float4*>(dst)[0] = make_float4(o[0], o[1], o[2], o[3]);
+            reinterpret_cast<float4*>(dst)[1] = make_float4(o[4], o[5], o[6], o[7]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (n0 + c0 + i < K) dst[i] = o[i];
+          }
+        }
+        continue;
+      }
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         int col = n0 + c0 + i;
@@ -266,8 +292,11 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
     __syncthreads();      // every lane read before the next tile's MMAs overwrite TMEM
     fence_after_sync();
   }
-  // merge the two halves of every row: the second half passes its list through
-  // shared memory (the operand buffers are idle now)
+  if (kStore) {
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kN);
+    return;
+  }
   // both halves' lists go to shared memory (the operand buffers are idle now)
   float* xd = reinterpret_cast<float*>(smem) + half * kM * T;
   int32_t* xi = reinterpret_cast<int32_t*>(smem + 2 * kM * T * 4) + half * kM * T;
@@ -358,13 +387,15 @@ qk_status launch_tc_nearest(const float* X, int64_t n, int d, const float* C, in
   QK_CUDA(cudaGetLastError());
   unsigned grid = (unsigned)((n + tc::kM - 1) / tc::kM);
   if (k == 1) {
-    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<tc::kT1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<tc::kT1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tc::kSmem));
-    tc_candidates_kernel<tc::kT1><<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, cand, status);
+    tc_candidates_kernel<tc::kT1, false>
+        <<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, cand, status, nullptr, 0, 0);
   } else {
-    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<tc::kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<tc::kT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tc::kSmem));
-    tc_candidates_kernel<tc::kT><<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, cand, status);
+    tc_candidates_kernel<tc::kT, false>
+        <<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, cand, status, nullptr, 0, 0);
   }
   QK_CUDA(cudaGetLastError());
   rescore_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, d, C, cand, metric, k, out_idx, out_dist);
@@ -373,5 +404,39 @@ qk_status launch_tc_nearest(const float* X, int64_t n, int d, const float* C, in
 }
 
 int tc_candidates_per_row() { return tc::kT; }
+
+// Approximate distance matrix (L2: ||c||^2 - 2 <x, c>, without ||x||^2; IP:
+// -<x, c>) of every row against every centroid, written to dout with row
+// stride ldd (>= K).  cnorm must hold the centroids' squared norms.  The
+// centroids are split over blockIdx.y in spans of whole tiles so that a small
+// number of 128-row tiles still covers every SM.
+qk_status launch_tc_distances(const float* X, int64_t n, int d, const float* C, int K, const float* cnorm, int metric,
+                              float* dout, int64_t ldd, int32_t* status, int n_sm, cudaStream_t s) {
+  if (n <= 0 || K <= 0) return QK_OK;
+  if (d % tc::kKS != 0 || ldd < K) return QK_ERR_ARG;
+  const int64_t row_tiles = (n + tc::kM - 1) / tc::kM;
+  const int col_tiles = (K + tc::kN - 1) / tc::kN;
+  int splits = (int)std::min<int64_t>(col_tiles, std::max<int64_t>(1, (4LL * n_sm + row_tiles - 1) / row_tiles));
+  const int tiles_per_split = (col_tiles + splits - 1) / splits;
+  splits = (col_tiles + tiles_per_split - 1) / tiles_per_split;
+  static bool attr_set = false;   // set once, outside any stream capture (the first call is never captured)
+  if (!attr_set) {
+    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::kSmem));
+    attr_set = true;
+  }
+  dim3 grid((unsigned)row_tiles, (unsigned)splits);
+  tc_candidates_kernel<1, true><<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, nullptr, status,
+                                                                      dout, ldd, tiles_per_split * tc::kN);
+  QK_CUDA(cudaGetLastError());
+  return QK_OK;
+}
+
+qk_status launch_row_norms(const float* C, int64_t K, int d, float* out, cudaStream_t s) {
+  if (K <= 0) return QK_OK;
+  row_norms_kernel<<<(unsigned)((K * 32 + 255) / 256), 256, 0, s>>>(C, K, d, out);
+  QK_CUDA(cudaGetLastError());
+  return QK_OK;
+}
 
 }  // namespace qk

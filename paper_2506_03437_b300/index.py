@@ -94,6 +94,23 @@ class Index:
                                 L.ptr(oi), L.ptr(od), L.ptr(on), L.ptr(orr), L.stream_ptr(stream)))
         return out
 
+    def search_nprobe(self, q, k, nprobe, out=None, stream=None):
+        """Fixed-nprobe search, one nprobe per query, through the per-query kernel.
+        Returns (ids, dist) on the device of `q`."""
+        q = _as(q, np.float32)
+        nprobe = _as(nprobe, np.int32)
+        nq = int(q.shape[0])
+        if out is None:
+            if hasattr(q, "data_ptr"):
+                import torch
+                out = (torch.empty((nq, k), dtype=torch.int64, device=q.device),
+                       torch.empty((nq, k), dtype=torch.float32, device=q.device))
+            else:
+                out = (np.empty((nq, k), np.int64), np.empty((nq, k), np.float32))
+        L.check(L.lib.qk_search_nprobe(self._h, L.ptr(q), nq, int(k), L.ptr(nprobe), L.ptr(out[0]), L.ptr(out[1]),
+                                       L.stream_ptr(stream)))
+        return out
+
     def maintain(self, lam_sizes, lam_us, tau_us=0.25, alpha=0.9, refine_radius=50, refine_iters=1,
                  split_iters=10, s_min=0, refine=True, window=0, stream=None):
         """Runs the maintenance pass; returns the list of considered actions as dicts."""
@@ -196,3 +213,80 @@ def nearest_centroids(x, c, k, metric=L.METRIC_L2):
     dist = np.empty((n, k), np.float32)
     L.check(L.lib.qk_nearest_centroids(L.ptr(x), n, d, L.ptr(c), c.shape[0], metric, k, L.ptr(idx), L.ptr(dist), None))
     return idx, dist
+
+
+class BatchPlan:
+    """Workspace and tile shapes of the batched fixed-nprobe search of one index
+    (qk_batch_* in include/quake_b300.h).  Every array is a CUDA tensor."""
+
+    def __init__(self, index, max_nq, k, max_nprobe):
+        h = C.c_void_p()
+        L.check(L.lib.qk_batch_create(index._h, int(max_nq), int(k), int(max_nprobe), C.byref(h)))
+        self._h, self.index, self.k = h, index, int(k)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib.qk_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def tiles(self):
+        t = L.QkBatchTiles()
+        L.check(L.lib.qk_batch_get_tiles(self._h, C.byref(t)))
+        return (t.queries_per_warp, t.tile_rows, t.chunk_rows)
+
+    @tiles.setter
+    def tiles(self, v):
+        t = L.QkBatchTiles(*[int(x) for x in v])
+        L.check(L.lib.qk_batch_set_tiles(self._h, C.byref(t)))
+
+    def _out(self, q, out):
+        if out is not None:
+            return out
+        import torch
+        nq = int(q.shape[0])
+        return (torch.empty((nq, self.k), dtype=torch.int64, device=q.device),
+                torch.empty((nq, self.k), dtype=torch.float32, device=q.device))
+
+    def search(self, q, nprobe, out=None, stream=None):
+        """(ids, dist) of the batch; q (nq x d FP32) and nprobe (nq int32) on the GPU."""
+        q, nprobe = _as(q, np.float32), _as(nprobe, np.int32)
+        out = self._out(q, out)
+        L.check(L.lib.qk_batch_search(self._h, L.ptr(q), int(q.shape[0]), L.ptr(nprobe), L.ptr(out[0]),
+                                      L.ptr(out[1]), L.stream_ptr(stream)))
+        return out
+
+    def capture(self, q, nprobe, out, stream):
+        """Records one batch over these buffers as a CUDA graph on `stream`."""
+        q, nprobe = _as(q, np.float32), _as(nprobe, np.int32)
+        L.check(L.lib.qk_batch_capture(self._h, L.ptr(q), int(q.shape[0]), L.ptr(nprobe), L.ptr(out[0]),
+                                       L.ptr(out[1]), L.stream_ptr(stream)))
+
+    def replay(self, stream):
+        L.check(L.lib.qk_batch_replay(self._h, L.stream_ptr(stream)))
+
+    STAGES = ("scoring", "selection", "grouping", "scan", "merge")
+
+    def set_timing(self, on=True):
+        L.check(L.lib.qk_batch_set_timing(self._h, 1 if on else 0))
+
+    def stage_times(self):
+        """Milliseconds of each step of the last timed batch (waits for it)."""
+        ms = np.zeros(5, np.float32)
+        L.check(L.lib.qk_batch_stage_times(self._h, L.ptr(ms)))
+        return dict(zip(self.STAGES, ms.tolist()))
+
+    def autotune(self, q, nprobe, out=None, reps=2, stream=None):
+        """Times every valid tile shape on this batch and keeps the fastest; returns it."""
+        q, nprobe = _as(q, np.float32), _as(nprobe, np.int32)
+        out = self._out(q, out)
+        t = L.QkBatchTiles()
+        L.check(L.lib.qk_batch_autotune(self._h, L.ptr(q), int(q.shape[0]), L.ptr(nprobe), L.ptr(out[0]),
+                                        L.ptr(out[1]), int(reps), C.byref(t), L.stream_ptr(stream)))
+        return (t.queries_per_warp, t.tile_rows, t.chunk_rows)
