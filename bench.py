@@ -408,7 +408,11 @@ def run_batch(args):
     plan = I.BatchPlan(ix, nq, k, np_hi)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        tiles = plan.autotune(Qd, npd, reps=1, stream=stream)
+        if args.tiles:
+            plan.tiles = tuple(int(x) for x in args.tiles.split(","))
+            tiles = plan.tiles
+        else:
+            tiles = plan.autotune(Qd, npd, reps=1, stream=stream)
         # stage times of uncaptured runs (CUDA events between the steps)
         plan.set_timing(True)
         stages = []
@@ -494,7 +498,8 @@ def run_batch(args):
         "config": {"workload": f"batch_{n}x{d}_{n_part}part_zipf1.0_{nq}q_nprobe1-{np_hi}_k{k}",
                    "n": n, "d": d, "partitions": n_part, "sizes_min_max": [int(sizes.min()), int(sizes.max())],
                    "queries": nq, "nprobe_mean": round(float(nprobe.mean()), 2), "k": k,
-                   "tiles": {"queries_per_warp": tiles[0], "tile_rows": tiles[1], "chunk_rows": tiles[2]},
+                   "tiles": {"queries_per_warp": tiles[0], "tile_rows": tiles[1], "chunk_rows": tiles[2],
+                             "chosen_by": "flag" if args.tiles else "autotuner"},
                    "stage_ms": stage_ms, "recall_at_10_vs_fp64": round(rec, 4),
                    "items": int(sum(min(int(x), n_part) for x in nprobe)), "rows_scanned": int(sel_rows),
                    "unique_partition_bytes": int(uniq_bytes),
@@ -596,6 +601,8 @@ def main():
     ap.add_argument("--n-batch", type=int, default=5_000_000, help="rows of the batching workload")
     ap.add_argument("--parts", type=int, default=20_000, help="partitions of the batching workload")
     ap.add_argument("--loop-queries", type=int, default=128, help="queries timed in the per-query launch loop")
+    ap.add_argument("--tiles", default="", help="queries_per_warp,tile_rows,chunk_rows for the batching "
+                                                 "workload instead of the autotuner's choice")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
