@@ -9,10 +9,10 @@ library):
       result.  For inner product it is the Euclidean distance from q to that
       result's vector, ||q - x_k||.
   R2  t_i, the distance from q to the bisector of c_0 and c_i, is
-      (D_i - D_0) / (2 ||c_i - c_0||) for L2 with D = squared distance, and
-      (D_i - D_0) / ||c_i - c_0|| for inner product with D = -<q, c>
-      (the bisector of the max-inner-product cells passes through the
-      origin).  Coincident centroids give t_i = 0.
+      (D_i - D_0) / (2 ||c_i - c_0||) with D the squared Euclidean centroid
+      distance, whatever the metric: the partitions are k-means cells
+      (Sec. 3), whose boundaries are the Euclidean bisectors of their
+      centroids.  Coincident centroids give t_i = 0.
   R3  p_0 = prod_j (1 - u_j) over the raw cap fractions u_j; the remaining
       mass 1 - p_0 is spread in proportion to the normalised v_i = u_i / sum u
       (Eq. 8-9).  With sum u = 0, p_0 = 1 and every p_i = 0.
@@ -35,6 +35,12 @@ library):
       (distance, index), are the next level's S.
   R10 Fixed-nprobe search (Faiss-IVF style, used for the plain-IVF workload)
       scans the first nprobe candidates of S in centroid order.
+  R11 With inner product the tree is searched in the geometry it was built
+      in: centroids are scored by squared Euclidean distance at every level,
+      and the upper levels' result sets are ranked the same way.  Only the
+      base rows (level 0) are ranked by -<q, x>, and rho is ||q - x_k|| (R1).
+      On unit-norm rows and queries -<q, x> = (||q - x||^2 - 2) / 2, so
+      there the inner-product search coincides with the L2 search.
 """
 
 import math
@@ -64,14 +70,15 @@ def n_candidates(f, n):
     return int(max(1, min(n, math.ceil(f * n))))
 
 
-def bisector_distances(D, C, metric):
-    """t_i for every candidate (R2); D[0] and C[0] belong to the nearest centroid."""
+def bisector_distances(D, C):
+    """t_i for every candidate (R2); D are squared Euclidean centroid distances and
+    D[0], C[0] belong to the nearest centroid."""
     D = np.asarray(D, dtype=np.float64)
     C = np.asarray(C, dtype=np.float64)
     diff = C - C[0][None, :]
     cd = np.sqrt((diff * diff).sum(axis=1))
     num = D - D[0]
-    den = 2.0 * cd if metric == L2 else cd
+    den = 2.0 * cd
     t = np.zeros_like(D)
     nz = den > 0.0
     t[nz] = num[nz] / den[nz]
@@ -137,7 +144,8 @@ def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
     q        query vector
     level    kmeans.Level whose partitions are scanned
     cand     candidate partition indices S, nearest first (position 0 = c_0)
-    cand_D   their centroid distances D_i (same convention as the scan)
+    cand_D   their squared Euclidean centroid distances D_i (R11)
+    metric   ranks the level's rows (L2 for upper levels, R11)
     Returns a dict: dist, ids (R sorted), scanned (positions in scan order),
     r (final estimate), trace (decision margins for parity checks).
     """
@@ -160,7 +168,7 @@ def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
             scan(pos)
         return dict(dist=R.dist, ids=R.ids, scanned=order, r=float("nan"), trace=trace)
 
-    t = bisector_distances(cand_D, level.centroids[np.asarray(cand)], metric)
+    t = bisector_distances(cand_D, level.centroids[np.asarray(cand)])
 
     scan(0)
     while not R.full() and not scanned.all():                       # R4
@@ -195,9 +203,10 @@ def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
     return dict(dist=R.dist, ids=R.ids, scanned=order, r=float(r), trace=trace)
 
 
-def root_candidates(q, top_level, f, metric):
-    """Score the single top partition (all centroids of the top level) and keep M."""
-    D = distances(q, top_level.centroids, metric)
+def root_candidates(q, top_level, f):
+    """Score the single top partition (all centroids of the top level, squared
+    Euclidean distance, R11) and keep M."""
+    D = distances(q, top_level.centroids, L2)
     idx = np.arange(D.shape[0], dtype=np.int64)
     M = n_candidates(f, D.shape[0])
     order = np.lexsort((idx, D))[:M]
@@ -229,15 +238,15 @@ def search(levels, Q, params, metric=L2):
         top = levels[L - 1]
         if L == 1:
             if fixed:                                                    # R10
-                cand, cD = root_candidates(q, top, 1.0, metric)
+                cand, cD = root_candidates(q, top, 1.0)
                 cand, cD = cand[:fixed], cD[:fixed]
             else:
-                cand, cD = root_candidates(q, top, params.f_M[0], metric)
+                cand, cD = root_candidates(q, top, params.f_M[0])
         else:
-            cand1, cD1 = root_candidates(q, top, params.f_M[1], metric)
+            cand1, cD1 = root_candidates(q, top, params.f_M[1])
             k1 = n_candidates(params.f_M[0], levels[0].n_part)
             res1 = aps_level(q, levels[1], list(cand1), cD1, k1, params.upper_recall,
-                             params, d, metric, table)
+                             params, d, L2, table)                      # R11
             scanned[1][j] = [int(cand1[p]) for p in res1["scanned"]]
             traces[1][j] = res1["trace"]
             cand, cD = res1["ids"], res1["dist"]
@@ -257,8 +266,9 @@ def search(levels, Q, params, metric=L2):
 def ivf_search(level, Q, k, nprobe, metric=L2):
     """Fixed-nprobe IVF over one level with one nprobe per query (R10 per query).
 
-    Query j scans its nprobe[j] nearest partitions (centroid distance, ties to
-    the lower index; more than the partitions there are means all of them) and
+    Query j scans its nprobe[j] nearest partitions (squared Euclidean centroid
+    distance, R11; ties to the lower index; more than the partitions there are
+    means all of them) and
     returns the exact top-k of their members by (distance, id).  Returns
     dist (nq, k) FP64, ids (nq, k) (inf / -1 past the scanned rows) and the
     scanned partition indices of every query, nearest first.
@@ -271,7 +281,7 @@ def ivf_search(level, Q, k, nprobe, metric=L2):
     scanned = []
     idx = np.arange(level.n_part, dtype=np.int64)
     for j in range(nq):
-        D = distances(Q[j], level.centroids, metric)
+        D = distances(Q[j], level.centroids, L2)
         parts = np.lexsort((idx, D))[:min(int(nprobe[j]), level.n_part)]
         scanned.append(parts)
         rows = [level.vectors[p] for p in parts if level.vectors[p].shape[0]]

@@ -200,7 +200,7 @@ def test_probabilities_hand_case_2d():
         nrm = (ci - c0) / np.linalg.norm(ci - c0)
         return float(np.dot(m - q, nrm))
 
-    t = aps.bisector_distances(D, C, knn.L2)
+    t = aps.bisector_distances(D, C)
     assert t[1] == pytest.approx(0.0, abs=1e-15)
     assert t[2] == pytest.approx(t_geom(C[0], C[2]), abs=1e-14) and t[2] == pytest.approx(4 / math.sqrt(10))
     assert t[3] == pytest.approx(2.0)
@@ -222,14 +222,23 @@ def test_probabilities_degenerate():
     assert p.tolist() == [1.0, 0.0, 0.0]
 
 
-def test_bisector_inner_product_case():
-    # max-IP cells of c0 and ci are split by the plane <x, c0 - ci> = 0 through the origin
-    q = np.array([2.0, 1.0])
-    C = np.array([[1.0, 0.0], [0.0, 1.0]])
-    D = -(C @ q)
-    t = aps.bisector_distances(D, C, knn.IP)
-    n = (C[0] - C[1]) / np.linalg.norm(C[0] - C[1])
-    assert t[1] == pytest.approx(float(np.dot(q, n)))
+def test_inner_product_on_the_unit_sphere_is_the_l2_search():
+    # on unit-norm rows and queries -<q, x> = (||q - x||^2 - 2) / 2: same order, and
+    # rho = ||q - x_k|| either way (R1, R11), so two-level APS must make the same choices
+    X, ids, Q = synth.plain_ivf(seed=12, n=4000, d=16, n_comp=20, sigma=0.5, nq=25)
+    X, Q = synth.unit_rows(X), synth.unit_rows(Q)
+    levels = kmeans.build_index(X, ids, 40, 6, iters=4, seed=3)
+    prm = aps.Params(k=10, recall_target=0.9, f_M=(0.2, 0.5), beta_mode="exact")
+    r2 = aps.search(levels, Q, prm, metric=knn.L2)
+    ri = aps.search(levels, Q, prm, metric=knn.IP)
+    same = sum(r2["scanned"][0][j] == ri["scanned"][0][j] and np.array_equal(r2["ids"][j], ri["ids"][j])
+               for j in range(Q.shape[0]))
+    assert same >= Q.shape[0] - 1          # FP64 rounding may flip one near-tied decision
+    # unit_rows normalises in FP32, so the norms are 1 to about 1e-7
+    np.testing.assert_allclose(ri["dist"], (r2["dist"] - 2.0) / 2.0, atol=1e-6)
+    # and IP recall against brute force is that of L2
+    D, I = knn.knn(X, ids, Q, 10, metric=knn.IP)
+    assert np.mean([len(set(ri["ids"][j]) & set(I[j])) for j in range(25)]) >= 8.0
 
 
 def _small_index(seed=4, n=3000, d=8, n_leaf=30, n_parent=0):
@@ -284,7 +293,7 @@ def test_aps_order_is_descending_p_without_recompute():
     prm = aps.Params(k=10, recall_target=0.999, f_M=(0.5,), tau_rho=1e30, beta_mode="exact")
     for j in range(Q.shape[0]):
         q = Q[j].astype(np.float64)
-        cand, cD = aps.root_candidates(q, lv[0], 0.5, knn.L2)
+        cand, cD = aps.root_candidates(q, lv[0], 0.5)
         res = aps.aps_level(q, lv[0], list(cand), cD, 10, 0.999, prm, 8, knn.L2, None)
         sc = res["scanned"]
         # find where R first held k results, then p is frozen: the rest is by descending p
@@ -294,7 +303,7 @@ def test_aps_order_is_descending_p_without_recompute():
         for p in sc[: first + 1]:
             c = cand[p]
             R.add(knn.distances(q, lv[0].vectors[c], knn.L2), lv[0].ids[c], lv[0].vectors[c])
-        t = aps.bisector_distances(cD, lv[0].centroids[cand], knn.L2)
+        t = aps.bisector_distances(cD, lv[0].centroids[cand])
         pr = aps.probabilities(t, math.sqrt(R.dist[9]), 8, "exact")
         rest = [p for p in range(len(cand)) if p not in sc[: first + 1]]
         want = sorted(rest, key=lambda p: (-pr[p], p))
