@@ -24,8 +24,11 @@
 //      (a partition is contiguous in the arena, so a tile is one copy); each
 //      of the 8 warps holds QW of the unit's queries in registers and keeps
 //      their top-k for the unit, so every tile is read from HBM once for all G
-//      queries.  A per-query bound (the best k-th distance any finished unit
-//      of the query has reported) prunes candidates across units.
+//      queries.  When the unit has fewer queries than G, the busy warps'
+//      query sets are replicated over the idle warps, the replicas split the
+//      rows of every tile, and their lists are merged at the end of the unit.
+//      A per-query bound (the best k-th distance any finished unit of the
+//      query has reported) prunes candidates across units.
 //   5. Merge, one warp per query: the top-k over its units' candidates.
 // Distances are FP32 sums of squared differences, like the per-query search.
 #include <cuda_runtime.h>
@@ -167,6 +170,7 @@ struct UnitInfo {
   int64_t unit;
   int64_t base;     // arena row of the chunk's first row
   int32_t p, qb, nq, row0, rows;
+  int32_t nw, rep;  // warps holding distinct queries; copies of each (nw * rep <= 8)
 };
 
 template <int D, int QW>
@@ -183,6 +187,7 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
   float* qbd = reinterpret_cast<float*>(full + kStages);              // G x kBuf
   int32_t* qbr = reinterpret_cast<int32_t*>(qbd + G * kBuf);          // G x kBuf
   UnitInfo* su = reinterpret_cast<UnitInfo*>(qbr + G * kBuf);
+  int32_t* s_n = reinterpret_cast<int32_t*>(su + 1);                  // G: list length after the unit
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int part = lane % TPR, rsub = lane / TPR;
@@ -221,6 +226,8 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
         u.row0 = c * a.CH;
         u.rows = min(a.CH, sp - u.row0);
         u.base = a.off[p] + u.row0;
+        u.nw = (u.nq + QW - 1) / QW;
+        u.rep = kWarps / u.nw;
         // the first tiles of the unit
         const int ntiles = (u.rows + a.TR - 1) / a.TR;
         for (int t = 0; t < kStages && t < ntiles; ++t) {
@@ -238,7 +245,10 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
     if (u.unit >= n_units) break;
     const int ntiles = (u.rows + a.TR - 1) / a.TR;
 
-    // this warp's queries: slots warp * QW + j of the unit's group
+    // this warp's queries: slots qg * QW + j of the unit's group; copy rc of
+    // them scans row steps rc, rc + rep, ... of every tile
+    const bool busy = warp < u.nw * u.rep;
+    const int qg = busy ? warp % u.nw : 0, rc = busy ? warp / u.nw : 0;
     float4 qv[QW][F4];
     float tau[QW];
     int cnt[QW];
@@ -246,8 +256,8 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
     bool any = false;
 #pragma unroll
     for (int j = 0; j < QW; ++j) {
-      const int slot = warp * QW + j;
-      qid[j] = slot < u.nq ? a.qlist[u.qb + slot] : -1;
+      const int slot = qg * QW + j;
+      qid[j] = busy && slot < u.nq ? a.qlist[u.qb + slot] : -1;
       const float4* q4 = reinterpret_cast<const float4*>(a.Q + (qid[j] < 0 ? 0 : qid[j]) * D);
 #pragma unroll
       for (int f = 0; f < F4; ++f) qv[j][f] = q4[part + TPR * f];
@@ -270,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
       const int rows_t = min(a.TR, u.rows - t * a.TR);
       const float* tile = tiles + st * tile_floats;
       if (any) {
-        for (int r0 = 0; r0 < rows_t; r0 += RS) {
+        for (int r0 = rc * RS; r0 < rows_t; r0 += u.rep * RS) {
           const int rr = r0 + rsub;
           const bool rv = rr < rows_t;
           const float4* x4 = reinterpret_cast<const float4*>(tile + (rv ? rr : 0) * D);
@@ -340,13 +350,31 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
           }
       break;
     }
-    // the unit's top-k of each query -> its candidate slots
+    // every copy sorts its lists down to k; copy 0 of each query set takes in
+    // the other copies' lists and writes the unit's top-k to the candidates
 #pragma unroll
     for (int j = 0; j < QW; ++j) {
       if (qid[j] < 0) continue;
+      const int n = warp_compact(qbd + (warp * QW + j) * kBuf, qbr + (warp * QW + j) * kBuf, cnt[j], a.k, lane);
+      if (lane == 0) s_n[warp * QW + j] = n;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < QW; ++j) {
+      if (qid[j] < 0 || rc != 0) continue;
       float* bd = qbd + (warp * QW + j) * kBuf;
       int32_t* br = qbr + (warp * QW + j) * kBuf;
-      const int n = warp_compact(bd, br, cnt[j], a.k, lane);
+      int n = s_n[warp * QW + j];
+      for (int c = 1; c < u.rep; ++c) {   // n <= k and the copy's list <= k: at most 64 entries
+        const int w2 = qg + c * u.nw;
+        const int n2 = s_n[w2 * QW + j];
+        if (lane < n2) {
+          bd[n + lane] = qbd[(w2 * QW + j) * kBuf + lane];
+          br[n + lane] = qbr[(w2 * QW + j) * kBuf + lane];
+        }
+        __syncwarp();
+        n = warp_compact(bd, br, n + n2, a.k, lane);
+      }
       int64_t slot = 0;
       if (lane == 0) slot = a.qcoff[qid[j]] + atomicAdd(&a.qcnt[qid[j]], a.k);
       slot = __shfl_sync(0xffffffffu, slot, 0);
@@ -832,7 +860,8 @@ bool dim_ok(int d) {
 template <int D, int QW>
 size_t scan_smem(int TR) {
   return sizeof(float) * bt::kStages * (size_t)TR * D + sizeof(uint64_t) * bt::kStages +
-         (sizeof(float) + sizeof(int32_t)) * (size_t)bt::kWarps * QW * bt::kBuf + sizeof(bt::UnitInfo) + 16;
+         (sizeof(float) + sizeof(int32_t)) * (size_t)bt::kWarps * QW * bt::kBuf + sizeof(bt::UnitInfo) +
+         sizeof(int32_t) * bt::kWarps * QW + 16;
 }
 
 // Launches the scan with (SMs x CTAs an SM holds) CTAs.  The attribute and

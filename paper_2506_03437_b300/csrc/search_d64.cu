@@ -1,0 +1,6 @@
+// The search kernel for d = 64 (8 lanes per row, 2 float4 of the query per lane).
+#include "search_impl.cuh"
+
+namespace qk {
+template qk_status launch_one<8, 2>(const SearchArgs& a, cudaStream_t stream);
+}  // namespace qk

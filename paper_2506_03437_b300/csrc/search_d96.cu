@@ -1,0 +1,6 @@
+// The search kernel for d = 96 (8 lanes per row, 3 float4 of the query per lane).
+#include "search_impl.cuh"
+
+namespace qk {
+template qk_status launch_one<8, 3>(const SearchArgs& a, cudaStream_t stream);
+}  // namespace qk

@@ -122,3 +122,26 @@ def zipf_partitions(seed=1238, n=5_000_000, d=256, n_part=20_000, a=1.0, lo=10, 
     u = g.uniform(np.log(nprobe_lo), np.log(nprobe_hi + 1), size=nq)
     nprobe = np.clip(np.floor(np.exp(u)).astype(np.int32), nprobe_lo, nprobe_hi)
     return X, np.arange(n, dtype=np.int64), lab, Q, nprobe
+
+
+def unit_mixture_cuda(seed=1237, n=10_000_000, d=768, n_comp=5000, s=1.0, nq=1024, chunk=1 << 20):
+    """Precision workload, generated on the GPU (torch Philox, seeded): n unit-norm rows
+    x = normalize(mu_c + (s / sqrt(d)) g) around n_comp directions mu uniform on the sphere,
+    component uniform per row, and nq queries from the same mixture.  Returns CUDA tensors
+    (X, Q) in FP32.  The mean cosine between a row and its direction is about 1/sqrt(1 + s^2)."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    mu = torch.randn((n_comp, d), generator=g, device="cuda")
+    mu /= mu.norm(dim=1, keepdim=True)
+    scale = s / d ** 0.5
+
+    def draw(m):
+        out = torch.empty((m, d), dtype=torch.float32, device="cuda")
+        for a in range(0, m, chunk):
+            b = min(m, a + chunk)
+            lab = torch.randint(0, n_comp, (b - a,), generator=g, device="cuda")
+            x = mu[lab] + scale * torch.randn((b - a, d), generator=g, device="cuda")
+            out[a:b] = x / x.norm(dim=1, keepdim=True)
+        return out
+    return draw(n), draw(nq)

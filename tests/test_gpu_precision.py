@@ -101,3 +101,23 @@ def test_inner_product_aps_matches_oracle(I):
     orc = aps.search(levels, Q, aps.Params(k=10, recall_target=0.9, f_M=(0.15, 0.5)), metric=knn.IP)
     n_ok, n_exc = compare_search(out, orc, 10)
     assert n_exc <= 0.05 * Q.shape[0]
+
+
+def test_inner_product_on_the_unit_sphere_is_the_l2_search(I):
+    """Reading R11 on the GPU: with unit-norm rows and queries, the two-level inner-product
+    search makes the L2 search's choices and its distances are (d_L2 - 2) / 2; recall
+    against FP64 brute force is high for both."""
+    X, ids, Q = synth.aps_search(seed=35, n=60_000, d=256, n_comp=300, sigma=1.0, nq=200)
+    X, Q = synth.unit_rows(X), synth.unit_rows(Q)
+    levels = kmeans.build_index(X, ids, 200, 12, iters=4, seed=5)
+    l2 = make(I, X, ids, levels, metric=0, f_M_leaf=0.1, f_M_parent=0.25)
+    ip = make(I, X, ids, levels, metric=1, f_M_leaf=0.1, f_M_parent=0.25)
+    a = l2.search(Q, 10, recall_target=0.9)
+    b = ip.search(Q, 10, recall_target=0.9)
+    same = np.mean([np.array_equal(a[0][j], b[0][j]) and a[2][j] == b[2][j] for j in range(Q.shape[0])])
+    assert same >= 0.97
+    ok = a[0] >= 0
+    np.testing.assert_allclose(b[1][ok], (a[1][ok] - 2.0) / 2.0, atol=2e-5)
+    D, Ix = knn.knn(X, ids, Q, 10, metric=knn.IP)
+    rec = np.mean([len(set(b[0][j]) & set(Ix[j])) / 10 for j in range(Q.shape[0])])
+    assert rec >= 0.85
