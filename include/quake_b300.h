@@ -317,6 +317,27 @@ typedef struct {
 qk_status qk_maintain(qk_index* index, const qk_maint_params* params, qk_maint_action* log, int32_t log_cap,
                       int32_t* n_log, void* stream);
 
+/* The same pass in two steps, so that searches need not wait for it (a
+ * copy-on-write view of the index; the paper runs maintenance beside the
+ * searches, Sec. 4 and Sec. 8):
+ *  - qk_maintain_prepare plans the pass and builds the resulting partitions
+ *    (arena, centroids, parent level, id map) into separate device memory.
+ *    It only reads the index, so searches of the index may run on other
+ *    streams (or other host threads) meanwhile; inserts and deletes must
+ *    not.  The log arguments are as for qk_maintain.  Returns when the new
+ *    structure is complete.  It needs room for a second arena.
+ *  - qk_maintain_commit makes the prepared structure the index's and frees
+ *    the old one.  No search of the index may be in flight.  It is quick
+ *    (pointer and host-state exchange plus freeing the old arena).
+ *    QK_ERR_STATE if nothing was prepared, or if the index changed (insert,
+ *    delete, build, load, maintenance) after the prepare: the prepared pass
+ *    is then discarded.
+ * The statistics window of the next pass starts at the commit.  Preparing
+ * again discards an earlier prepared pass. */
+qk_status qk_maintain_prepare(qk_index* index, const qk_maint_params* params, qk_maint_action* log,
+                              int32_t log_cap, int32_t* n_log, void* stream);
+qk_status qk_maintain_commit(qk_index* index, void* stream);
+
 /*
  * Allocation-free Lloyd step.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory while they run

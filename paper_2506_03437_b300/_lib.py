@@ -27,7 +27,7 @@ EXPORTS = [
     "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain", "qk_nearest_centroids",
     "qk_search_nprobe", "qk_batch_create", "qk_batch_destroy", "qk_batch_get_tiles", "qk_batch_set_tiles",
     "qk_batch_search", "qk_batch_capture", "qk_batch_replay", "qk_batch_autotune", "qk_batch_set_timing",
-    "qk_batch_stage_times",
+    "qk_batch_stage_times", "qk_maintain_prepare", "qk_maintain_commit",
 ]
 
 
@@ -91,6 +91,9 @@ def _load():
         "qk_maintain": (i32, [vp, C.POINTER(QkMaintParams), C.POINTER(QkMaintAction), i32,
                               C.POINTER(C.c_int32), vp]),
         "qk_search_nprobe": (i32, [vp, vp, i64, i32, vp, vp, vp, vp]),
+        "qk_maintain_prepare": (i32, [vp, C.POINTER(QkMaintParams), C.POINTER(QkMaintAction), i32,
+                                      C.POINTER(C.c_int32), vp]),
+        "qk_maintain_commit": (i32, [vp, vp]),
         "qk_batch_create": (i32, [vp, i64, i32, i32, C.POINTER(vp)]),
         "qk_batch_destroy": (None, [vp]),
         "qk_batch_get_tiles": (i32, [vp, C.POINTER(QkBatchTiles)]),

@@ -190,6 +190,42 @@ static void free_structure(qk_index* ix) {
   ix->where.clear();
 }
 
+void release_structure(qk_index* ix) { free_structure(ix); }
+
+void swap_structure(qk_index* a, qk_index* b) {
+  using std::swap;
+  swap(a->vec0, b->vec0);
+  swap(a->ids0, b->ids0);
+  swap(a->cap0, b->cap0);
+  swap(a->used0, b->used0);
+  swap(a->holes0, b->holes0);
+  swap(a->off0, b->off0);
+  swap(a->size0, b->size0);
+  swap(a->cent0, b->cent0);
+  swap(a->lp0, b->lp0);
+  swap(a->lp_scale0, b->lp_scale0);
+  swap(a->h_off0, b->h_off0);
+  swap(a->h_cap_part0, b->h_cap_part0);
+  swap(a->h_size0, b->h_size0);
+  swap(a->h_ids0, b->h_ids0);
+  swap(a->vec1, b->vec1);
+  swap(a->ids1, b->ids1);
+  swap(a->off1, b->off1);
+  swap(a->size1, b->size1);
+  swap(a->cent1, b->cent1);
+  swap(a->h_size1, b->h_size1);
+  swap(a->h_off1, b->h_off1);
+  swap(a->hits0, b->hits0);
+  swap(a->hits1, b->hits1);
+  swap(a->where, b->where);
+  swap(a->n, b->n);
+  swap(a->n_leaf, b->n_leaf);
+  swap(a->n_parent, b->n_parent);
+  swap(a->cfg.n_leaf, b->cfg.n_leaf);
+  swap(a->cfg.n_parent, b->cfg.n_parent);
+  swap(a->ready, b->ready);
+}
+
 // Groups `rows` (n x d, device) by label into a fresh arena.  Returns the
 // arena, its partition offsets/sizes on host and device.
 static qk_status group_rows(const float* rows, const int64_t* ids, int64_t n, int d, const int32_t* lab,
@@ -629,6 +665,11 @@ qk_status qk_create(const qk_config* cfg, qk_index** out) {
 
 void qk_destroy(qk_index* ix) {
   if (!ix) return;
+  if (ix->pending) {
+    free_structure(ix->pending);
+    delete ix->pending;
+    ix->pending = nullptr;
+  }
   free_structure(ix);
   dfree(ix->beta_table);
   dfree(ix->work);

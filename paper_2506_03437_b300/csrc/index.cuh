@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <unordered_map>
 #include <vector>
 
@@ -123,9 +124,13 @@ struct qk_index {
   qk::Buffer stage_in, stage_out;
   // id -> (partition, slot) for deletes
   std::unordered_map<int64_t, int64_t> where;
-  int64_t queries_seen = 0;      // searched queries since the last install/maintain (the window |W|)
+  std::atomic<int64_t> queries_seen{0};   // searched queries since the last install/maintain (the window |W|)
   uint64_t search_seq = 0;       // launches so far (selects the work counter)
   uint64_t version = 0;          // bumped by every change of the partitions (install, insert, delete)
+  // a maintenance pass planned and built by qk_maintain_prepare, not yet
+  // committed, and the index version it was planned from
+  qk_index* pending = nullptr;
+  uint64_t pending_version = 0;
 };
 
 namespace qk {
@@ -140,5 +145,9 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
                   const int32_t* leaf_of_row, const float* C1, const int32_t* parent_of_leaf, cudaStream_t s,
                   bool skip_unlabelled);
 bool is_device_ptr(const void* p);
+// Exchanges the partition structure (arena, levels, host mirrors, id map,
+// counters) of two index objects; frees an object's structure.
+void swap_structure(qk_index* a, qk_index* b);
+void release_structure(qk_index* ix);
 qk_status assign_nearest(const float* X, int64_t n, int d, const float* C, int K, int32_t* assign, cudaStream_t s);
 }  // namespace qk

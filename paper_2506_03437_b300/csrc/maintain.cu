@@ -387,8 +387,12 @@ qk_status maintain_level(Ctx& cx, Level& L, int level_no, std::vector<int32_t>* 
 
 using namespace qk;
 
-extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk_maint_action* log, int32_t log_cap,
-                                 int32_t* n_log, void* stream) {
+// The pass up to its new structure: both levels are planned and the new
+// arena, centroids, parent level and id map are built into *out, a fresh
+// index object.  ix is only read, so searches of ix may run meanwhile.
+static qk_status maintain_plan(qk_index* ix, const qk_maint_params* params, qk_maint_action* log, int32_t log_cap,
+                               int32_t* n_log, void* stream, qk_index** out) {
+  *out = nullptr;
   if (!ix || !params) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -410,7 +414,7 @@ extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk
     }
   cudaStream_t s = (cudaStream_t)stream;
   const int d = ix->cfg.d;
-  const int64_t window = P.window > 0 ? P.window : ix->queries_seen;
+  const int64_t window = P.window > 0 ? P.window : ix->queries_seen.load();
   if (window < 1) {
     set_error("no queries in the statistics window");
     return QK_ERR_STATE;
@@ -502,27 +506,88 @@ extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk
   }
 
   tr.mark("parent_level");
-  // re-lay out the arena from the labels (the old arena stays alive until the copy is done)
-  float* old_vec = ix->vec0;
-  int64_t* old_ids = ix->ids0;
-  const int64_t old_cap = ix->cap0, live_n = ix->n;
-  ix->vec0 = nullptr;
-  ix->ids0 = nullptr;
-  qk_config keep_cfg = ix->cfg;
-  ix->cfg.n_leaf = M0;
-  ix->cfg.n_parent = M1;
-  qk_status st = install(ix, old_vec, old_ids, old_cap, dC0.as<float>(), dlab.as<int32_t>(),
+  // the new structure, laid out from the labels into a fresh object (the live
+  // arena is only read)
+  qk_index* nx = new qk_index();
+  nx->cfg = ix->cfg;
+  nx->cfg.n_leaf = M0;
+  nx->cfg.n_parent = M1;
+  nx->device = ix->device;
+  DevBuf nst(s);             // the install's own status word (the live one may be in use by searches)
+  QK_TRY(nst.reserve(sizeof(int32_t)));
+  QK_CUDA(cudaMemsetAsync(nst.p, 0, sizeof(int32_t), s));
+  nx->status = nst.as<int32_t>();
+  qk_status st = install(nx, ix->vec0, ix->ids0, ix->cap0, dC0.as<float>(), dlab.as<int32_t>(),
                          N1 > 0 ? dC1.as<float>() : nullptr, N1 > 0 ? dpol.as<int32_t>() : nullptr, s, true);
-  cudaFree(old_vec);
-  cudaFree(old_ids);
+  nx->status = nullptr;
   if (st != QK_OK) {
-    ix->cfg = keep_cfg;
+    release_structure(nx);
+    delete nx;
     return st;
   }
-  ix->n = live_n;
+  nx->n = ix->n;
+  *out = nx;
   tr.mark("install");
   if (n_log) *n_log = (int32_t)acts.size();
   if (log)
     for (int32_t i = 0; i < (int32_t)acts.size() && i < log_cap; ++i) log[i] = acts[i];
   return QK_OK;
+}
+
+// Makes nx's structure the index's and frees the old one.  Nothing may still
+// read the old arena (no search of the index in flight).
+static qk_status commit_structure(qk_index* ix, qk_index* nx, cudaStream_t s) {
+  QK_CUDA(cudaStreamSynchronize(s));
+  swap_structure(ix, nx);
+  release_structure(nx);
+  delete nx;
+  ix->queries_seen = 0;
+  ++ix->version;
+  return QK_OK;
+}
+
+static void discard_pending(qk_index* ix) {
+  if (!ix->pending) return;
+  release_structure(ix->pending);
+  delete ix->pending;
+  ix->pending = nullptr;
+}
+
+extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk_maint_action* log, int32_t log_cap,
+                                 int32_t* n_log, void* stream) {
+  qk_index* nx = nullptr;
+  QK_TRY(maintain_plan(ix, params, log, log_cap, n_log, stream, &nx));
+  discard_pending(ix);
+  return commit_structure(ix, nx, (cudaStream_t)stream);
+}
+
+extern "C" qk_status qk_maintain_prepare(qk_index* ix, const qk_maint_params* params, qk_maint_action* log,
+                                         int32_t log_cap, int32_t* n_log, void* stream) {
+  if (!ix) {
+    set_error("null index");
+    return QK_ERR_ARG;
+  }
+  discard_pending(ix);
+  const uint64_t v = ix->version;
+  qk_index* nx = nullptr;
+  QK_TRY(maintain_plan(ix, params, log, log_cap, n_log, stream, &nx));
+  QK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  ix->pending = nx;
+  ix->pending_version = v;
+  return QK_OK;
+}
+
+extern "C" qk_status qk_maintain_commit(qk_index* ix, void* stream) {
+  if (!ix || !ix->pending) {
+    set_error("no prepared maintenance pass");
+    return QK_ERR_STATE;
+  }
+  if (ix->pending_version != ix->version) {
+    discard_pending(ix);
+    set_error("the index changed after qk_maintain_prepare: the prepared pass was discarded");
+    return QK_ERR_STATE;
+  }
+  qk_index* nx = ix->pending;
+  ix->pending = nullptr;
+  return commit_structure(ix, nx, (cudaStream_t)stream);
 }

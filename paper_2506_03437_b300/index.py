@@ -111,9 +111,8 @@ class Index:
                                        L.stream_ptr(stream)))
         return out
 
-    def maintain(self, lam_sizes, lam_us, tau_us=0.25, alpha=0.9, refine_radius=50, refine_iters=1,
-                 split_iters=10, s_min=0, refine=True, window=0, stream=None):
-        """Runs the maintenance pass; returns the list of considered actions as dicts."""
+    def _maint(self, fn, lam_sizes, lam_us, tau_us, alpha, refine_radius, refine_iters, split_iters, s_min, refine,
+               window, stream):
         ls = np.ascontiguousarray(lam_sizes, np.float64)
         lu = np.ascontiguousarray(lam_us, np.float64)
         p = L.QkMaintParams()
@@ -125,10 +124,26 @@ class Index:
         cap = 1 << 16
         log = (L.QkMaintAction * cap)()
         n = C.c_int32()
-        L.check(L.lib.qk_maintain(self._h, C.byref(p), log, cap, C.byref(n), L.stream_ptr(stream)))
+        L.check(fn(self._h, C.byref(p), log, cap, C.byref(n), L.stream_ptr(stream)))
         return [dict(level=a.level, kind=("split", "merge")[a.kind], partition=a.partition,
                      committed=bool(a.committed), estimate=a.estimate, delta=a.delta)
                 for a in log[:min(n.value, cap)]]
+
+    def maintain(self, lam_sizes, lam_us, tau_us=0.25, alpha=0.9, refine_radius=50, refine_iters=1,
+                 split_iters=10, s_min=0, refine=True, window=0, stream=None):
+        """Runs the maintenance pass; returns the list of considered actions as dicts."""
+        return self._maint(L.lib.qk_maintain, lam_sizes, lam_us, tau_us, alpha, refine_radius, refine_iters,
+                           split_iters, s_min, refine, window, stream)
+
+    def maintain_prepare(self, lam_sizes, lam_us, tau_us=0.25, alpha=0.9, refine_radius=50, refine_iters=1,
+                         split_iters=10, s_min=0, refine=True, window=0, stream=None):
+        """Plans the pass and builds its partitions aside (searches may run meanwhile);
+        returns the action list.  maintain_commit() then installs it."""
+        return self._maint(L.lib.qk_maintain_prepare, lam_sizes, lam_us, tau_us, alpha, refine_radius,
+                           refine_iters, split_iters, s_min, refine, window, stream)
+
+    def maintain_commit(self, stream=None):
+        L.check(L.lib.qk_maintain_commit(self._h, L.stream_ptr(stream)))
 
     def check(self, stream=None):
         """Waits for this index's kernels on `stream`; raises if a device check failed."""

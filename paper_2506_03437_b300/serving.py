@@ -18,13 +18,19 @@ inserted again is deleted first and then inserted.  Searches may overtake
 updates that arrived less than `update_wait_s` before them.
 
 Every `maintain_every` operations the maintenance pass runs (Sec. 4; its
-statistics window is the queries since the previous pass).  A request's
-latency runs from its arrival to the moment its result is in host memory.
+statistics window is the queries since the previous pass).  With
+`concurrent_maintenance` (the default) the pass is prepared by a host thread
+on its own stream while searches go on (qk_maintain_prepare builds the new
+partitions aside); updates wait meanwhile, and once the pass is ready the
+searches in flight are drained and it is committed.  Otherwise the searches
+in flight are drained and the whole pass runs in place.  A request's latency
+runs from its arrival to the moment its result is in host memory.
 
 The index's kernels do all the work; this module only schedules calls to the
 C ABI.
 """
 
+import threading
 import time
 
 import numpy as np
@@ -81,9 +87,13 @@ class Server:
     """Schedules searches, inserts, deletes and maintenance on one index."""
 
     def __init__(self, index, d, k=10, recall_target=0.9, max_batch=2048, streams=4, min_free_bytes=1 << 30,
-                 maintain_every=0, maint_args=None, update_batch=1024, update_wait_s=0.002):
+                 maintain_every=0, maint_args=None, update_batch=1024, update_wait_s=0.002,
+                 concurrent_maintenance=True):
         import torch
         self.torch = torch
+        self.concurrent = concurrent_maintenance
+        self.device = torch.cuda.current_device()
+        self.maint_stream = torch.cuda.Stream()
         self.ix, self.d, self.k, self.tau = index, d, k, recall_target
         self.max_batch, self.min_free = max_batch, min_free_bytes
         self.maintain_every, self.maint_args = maintain_every, maint_args or {}
@@ -143,6 +153,13 @@ class Server:
         free, _ = self.torch.cuda.mem_get_info()
         return free >= self.min_free
 
+    def _prepare(self, prep):
+        try:
+            self.torch.cuda.set_device(self.device)   # the CUDA device is per host thread
+            self.ix.maintain_prepare(stream=self.maint_stream, **self.maint_args)
+        except Exception as e:   # re-raised by the request loop
+            prep[1] = e
+
     def _apply_updates(self, rows, clock):
         ops = self.ops
         dpos, ipos = net_updates(ops.kind[rows], ops.ref[rows])
@@ -169,35 +186,66 @@ class Server:
         s_t, u_t = ops.t[s_rows], ops.t[u_rows]
         n_s, n_u = s_rows.shape[0], u_rows.shape[0]
         qs = us = 0          # next search / update not yet taken
-        t_upd = t_maint = t_host = 0.0
+        t_upd = t_maint = t_host = t_prep = 0.0
         batches = drains = passes = 0
         inflight = []
+        prep = None          # the maintenance pass being prepared: [thread, error, start time]
+        searched = 0         # queries launched since the last pass (its statistics window)
+        min_window = max(1, min(1000, self.maintain_every // 10)) if self.maintain_every else 1
         t0 = time.perf_counter()
 
         def clock():
             return time.perf_counter() - t0
 
-        while qs < n_s or us < n_u or inflight:
+        while qs < n_s or us < n_u or inflight or prep is not None:
             now = clock()
             qa = int(np.searchsorted(s_t, now, side="right"))
             ua = int(np.searchsorted(u_t, now, side="right"))
             # results of finished batches
             while inflight and inflight[0]["event"].query():
                 self._finish(inflight.pop(0), clock())
+            # a prepared maintenance pass: drain, commit, then updates may go on
+            if prep is not None and not prep[0].is_alive():
+                c0 = clock()
+                self._drain(inflight, clock)
+                if prep[1] is not None:
+                    raise prep[1]
+                self.ix.maintain_commit(stream=self.maint_stream)
+                passes += 1
+                searched = 0
+                t_maint += clock() - c0
+                t_prep += c0 - prep[2]
+                prep = None
             # updates: between batches, after draining the searches in flight
-            if ua > us and (ua - us >= self.update_batch or now - u_t[us] >= self.update_wait or qa == n_s):
+            if prep is None and ua > us and (ua - us >= self.update_batch or now - u_t[us] >= self.update_wait
+                                             or qa == n_s):
                 c0 = clock()
                 self._drain(inflight, clock)
                 self._apply_updates(u_rows[us:ua], clock)
                 us = ua
                 drains += 1
                 t_upd += clock() - c0
-            if self.maintain_every and (qa + ua) // self.maintain_every > passes:
-                c0 = clock()
-                self._drain(inflight, clock)
-                self.ix.maintain(**self.maint_args)
-                passes += 1
-                t_maint += clock() - c0
+            if (self.maintain_every and prep is None and (qa + ua) // self.maintain_every > passes
+                    and searched >= min_window):
+                if self.concurrent:
+                    # pending updates first, so the pass plans from the current index
+                    if ua > us:
+                        c0 = clock()
+                        self._drain(inflight, clock)
+                        self._apply_updates(u_rows[us:ua], clock)
+                        us = ua
+                        drains += 1
+                        t_upd += clock() - c0
+                    prep = [None, None, clock()]
+                    prep[0] = threading.Thread(target=self._prepare, args=(prep,), daemon=True)
+                    prep[0].start()
+                else:
+                    c0 = clock()
+                    self._drain(inflight, clock)
+                    self.ix.maintain(**self.maint_args)
+                    passes += 1
+                    searched = 0
+                    t_maint += clock() - c0
             # launch while a stream slot is free and memory allows
             launched = False
             while qa > qs and len(inflight) < len(self.slots) and self._free_ok():
@@ -206,6 +254,7 @@ class Server:
                 n = min(self.max_batch, qa - qs)
                 inflight.append(self._launch(slot, s_rows[qs:qs + n]))
                 qs += n
+                searched += n
                 batches += 1
                 launched = True
                 t_host += clock() - c0
@@ -219,7 +268,9 @@ class Server:
                         time.sleep(min(wait, 1e-3))
         wall = clock()
         out = {"wall_s": round(wall, 4), "batches": batches, "maintenance_passes": passes, "update_drains": drains,
-               "update_s": round(t_upd, 4), "maintenance_s": round(t_maint, 4), "launch_host_s": round(t_host, 4)}
+               "update_s": round(t_upd, 4), "maintenance_stall_s": round(t_maint, 4),
+               "maintenance_prepare_s": round(t_prep, 4), "launch_host_s": round(t_host, 4),
+               "concurrent_maintenance": self.concurrent}
         for kind, name in ((SEARCH, "search"), (INSERT, "insert"), (DELETE, "delete")):
             v = self.lat[ops.kind == kind]
             if v.shape[0]:

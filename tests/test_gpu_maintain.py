@@ -108,3 +108,51 @@ def test_maintain_needs_statistics(I):
     with pytest.raises(L.QkError) as e:
         ix.maintain([10, 5], [1.0, 2.0], window=10)
     assert e.value.status == L.ERR_ARG
+
+
+def test_prepare_then_commit_equals_maintain_and_searches_run_meanwhile(I):
+    """qk_maintain_prepare + qk_maintain_commit give the index qk_maintain gives.  Between
+    them the index still answers from its old partitions, also from another host thread,
+    and a change of the index discards the prepared pass."""
+    import threading
+    from paper_2506_03437_b300 import _lib as L
+    X, ids, Q = scenario()
+    levels = kmeans.build_index(X, ids, 24, 5, iters=5, seed=11)
+    kw = dict(tau_us=0.01, alpha=0.9, refine_radius=4, s_min=120, split_iters=8, window=600)
+    a = make_index(I, X, ids, levels, f_M_leaf=0.25, f_M_parent=1.0, seed=1234)
+    b = make_index(I, X, ids, levels, f_M_leaf=0.25, f_M_parent=1.0, seed=1234)
+    for ix in (a, b):
+        ix.search(Q, 10, recall_target=0.0, nprobe=2)
+    before = b.search(Q[:50], 10, recall_target=0.9)
+    log_a = a.maintain([0, 1000], [5.0, 55.0], **kw)
+    # the prepare runs on a worker thread while this thread keeps searching
+    out = {}
+    t = threading.Thread(target=lambda: out.update(log=b.maintain_prepare([0, 1000], [5.0, 55.0], **kw)))
+    t.start()
+    during = [b.search(Q[:50], 10, recall_target=0.9) for _ in range(3)]
+    t.join()
+    for r in during + [b.search(Q[:50], 10, recall_target=0.9)]:   # still the old partitions
+        assert np.array_equal(r[0], before[0]) and np.array_equal(r[2], before[2])
+    b.maintain_commit()
+    assert [(x["level"], x["kind"], x["partition"], x["committed"]) for x in out["log"]] == \
+           [(x["level"], x["kind"], x["partition"], x["committed"]) for x in log_a]
+    for lv in (0, 1):
+        sa, ca, ia = a.export_level(lv)
+        sb, cb, ib = b.export_level(lv)
+        assert np.array_equal(sa, sb) and np.array_equal(ca, cb)
+        off = np.concatenate([[0], np.cumsum(sa)])
+        for j in range(len(sa)):
+            assert set(ia[off[j]:off[j + 1]].tolist()) == set(ib[off[j]:off[j + 1]].tolist())
+    ra, rb = a.search(Q, 10, recall_target=0.9), b.search(Q, 10, recall_target=0.9)
+    assert np.array_equal(ra[0], rb[0])
+    # nothing prepared, or the index changed after the prepare: refused
+    with pytest.raises(L.QkError) as e:
+        b.maintain_commit()
+    assert e.value.status == L.ERR_STATE
+    b.search(Q, 10, recall_target=0.0, nprobe=2)
+    n_leaf = b.info()["n_leaf"]
+    b.maintain_prepare([0, 1000], [5.0, 55.0], **kw)
+    b.insert(X[:3] + 0.01, np.array([10 ** 7, 10 ** 7 + 1, 10 ** 7 + 2], np.int64))
+    with pytest.raises(L.QkError) as e:
+        b.maintain_commit()
+    assert e.value.status == L.ERR_STATE and b.info()["n_leaf"] == n_leaf

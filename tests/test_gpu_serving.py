@@ -29,7 +29,8 @@ def test_results_alone_equal_results_in_the_mix():
         assert np.array_equal(srv.out_dist[j], alone[n][1][0])
 
 
-def test_stream_with_updates_and_maintenance():
+@pytest.mark.parametrize("concurrent", [False, True])
+def test_stream_with_updates_and_maintenance(concurrent):
     from paper_2506_03437_b300.serving import Server, skewed_stream
     X, ids, Q = synth.aps_search(seed=42, n=20_000, d=64, n_comp=50, sigma=1.2, nq=1)
     levels = kmeans.build_index(X, ids, 100, 0, iters=3, seed=6)
@@ -38,11 +39,15 @@ def test_stream_with_updates_and_maintenance():
     C = synth.mixture_centers(50, 64, 42)
     ops = skewed_stream(C, ids, 6000, 1.2, 7, hot=10, rotate=2000, rate=2e5)
     srv = Server(ix, 64, k=10, recall_target=0.9, max_batch=256, streams=3, maintain_every=3000,
+                 concurrent_maintenance=concurrent,
                  maint_args=dict(lam_sizes=[0, 1000], lam_us=[2.0, 47.0], tau_us=0.25, alpha=0.9, refine_radius=8,
                                  s_min=20))
     st = srv.run(ops)
     assert ix.info()["n"] == 20_000 + ops.count(1) - ops.count(2)
-    assert st["maintenance_passes"] == 2 and st["search"]["n"] == ops.count(0)
+    # in place, a pass runs every 3,000 operations; prepared beside the searches, a pass
+    # also needs queries since the previous one, so the stream's end may leave one out
+    assert (st["maintenance_passes"] == 2 if not concurrent else st["maintenance_passes"] >= 1)
+    assert st["search"]["n"] == ops.count(0)
     # every live id is stored exactly once
     _, _, got = ix.export_level(0)
     live = set(ids.tolist())
