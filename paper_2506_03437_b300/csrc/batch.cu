@@ -112,9 +112,41 @@ __device__ __forceinline__ void warp_sort64(float& d0, I& i0, float& d1, I& i1, 
   }
 }
 
+// Bitonic sort of 32 (distance, index) pairs, one per lane, ascending.
+template <class I>
+__device__ __forceinline__ void warp_sort32(float& d, I& i, int lane) {
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const float od = __shfl_xor_sync(0xffffffffu, d, stride);
+      const I oi = __shfl_xor_sync(0xffffffffu, i, stride);
+      const bool up = (lane & size) == 0 || size == 32;
+      const bool lower = (lane & stride) == 0;
+      if ((lower == up) == pair_less(od, oi, d, i)) {
+        d = od;
+        i = oi;
+      }
+    }
+  }
+}
+
 // Sorts the warp's buffer of n <= 64 entries and keeps its first min(n, k).
 template <class I>
 __device__ __forceinline__ int warp_compact(float* bd, I* bi, int n, int k, int lane) {
+  if (n <= 32) {   // one entry per lane: the shorter network
+    float d = lane < n ? bd[lane] : INFINITY;
+    I i = lane < n ? bi[lane] : (I)0x7fffffff;
+    __syncwarp();
+    warp_sort32(d, i, lane);
+    const int keep = n < k ? n : k;
+    if (lane < keep) {
+      bd[lane] = d;
+      bi[lane] = i;
+    }
+    __syncwarp();
+    return keep;
+  }
   float d0 = lane < n ? bd[lane] : INFINITY, d1 = lane + 32 < n ? bd[lane + 32] : INFINITY;
   I i0 = lane < n ? bi[lane] : (I)0x7fffffff, i1 = lane + 32 < n ? bi[lane + 32] : (I)0x7fffffff;
   __syncwarp();
@@ -284,9 +316,9 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
           const int rr = r0 + rsub;
           const bool rv = rr < rows_t;
           const float4* x4 = reinterpret_cast<const float4*>(tile + (rv ? rr : 0) * D);
-          float acc[QW];
+          float acc[QW], acc2[QW];   // two independent FMA chains per query
 #pragma unroll
-          for (int j = 0; j < QW; ++j) acc[j] = 0.f;
+          for (int j = 0; j < QW; ++j) acc[j] = acc2[j] = 0.f;
 #pragma unroll
           for (int f = 0; f < F4; ++f) {
             const float4 x = x4[part + TPR * f];
@@ -295,13 +327,15 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
               float e = qv[j][f].x - x.x;
               acc[j] = fmaf(e, e, acc[j]);
               e = qv[j][f].y - x.y;
-              acc[j] = fmaf(e, e, acc[j]);
+              acc2[j] = fmaf(e, e, acc2[j]);
               e = qv[j][f].z - x.z;
               acc[j] = fmaf(e, e, acc[j]);
               e = qv[j][f].w - x.w;
-              acc[j] = fmaf(e, e, acc[j]);
+              acc2[j] = fmaf(e, e, acc2[j]);
             }
           }
+#pragma unroll
+          for (int j = 0; j < QW; ++j) acc[j] += acc2[j];
 #pragma unroll
           for (int j = 0; j < QW; ++j) {
 #pragma unroll
