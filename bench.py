@@ -49,7 +49,7 @@ STORAGE = "f32"
 # (dram__bytes_read.sum + dram__bytes_write.sum).  It belongs to the kernel
 # sources with this hash; once they change the figure is no longer reported.
 TRAFFIC_BYTES = 120.66e9 + 0.393e9
-TRAFFIC_KERNEL_HASH = "8573adfc9aa7d22f"
+TRAFFIC_KERNEL_HASH = "4ea9064cea95f825"
 KERNEL_SOURCES = ["search_impl.cuh", "common.cuh", "capvol.cuh", "index.cuh"]
 
 
@@ -180,6 +180,31 @@ def run_ours(args):
             break
         tau = round(tau + 0.01, 2)
     mean_nprobe = on.double().mean().item()
+    # the fixed-nprobe path for comparison: the smallest nprobe whose mean recall@10 is >= 0.9
+    fixed = None
+    if not args.no_fixed:
+        lo, hi = 1, N_LEAF
+        while lo < hi:
+            mid = (lo + hi) // 2
+            fi, _, _, _ = ix.search(Qd, K, recall_target=0.0, nprobe=mid, stream=stream)
+            if recall(torch, X64, Qd, fi, gtD, K) >= 0.9:
+                hi = mid
+            else:
+                lo = mid + 1
+        fo = ix.search(Qd, K, recall_target=0.0, nprobe=lo, stream=stream)
+        frec = recall(torch, X64, Qd, fo[0], gtD, K)
+        for _ in range(args.warmup):
+            ix.search(Qd, K, recall_target=0.0, nprobe=lo, out=fo, stream=stream)
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for a_, b_ in fev:
+            a_.record(stream)
+            ix.search(Qd, K, recall_target=0.0, nprobe=lo, out=fo, stream=stream)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        fs = sum(a_.elapsed_time(b_) for a_, b_ in fev) / 1e3 / args.steps
+        fixed = {"nprobe": lo, "recall_at_10": round(frec, 4), "value": round(NQ / fs, 1), "unit": "queries/s",
+                 "ms_per_step": round(1e3 * fs, 4)}
     del X64
 
     sizes0, _, _ = ix.export_level(0)
@@ -248,6 +273,7 @@ def run_ours(args):
             "data": "synthetic (seeded Gaussian mixture; stands in for Sift1M-shaped data)",
             "config": {"workload": WORKLOAD, "n": N, "d": D, "n_leaf": N_LEAF, "n_parent": N_PARENT,
                        "queries_per_step": NQ, "k": K, "recall_target": tau, "recall_at_10": round(rec, 4),
+                       "fixed_nprobe_path": fixed,
                        "mean_nprobe": round(mean_nprobe, 2), "f_M": [F_M_LEAF, F_M_PARENT],
                        "tau_rho": 0.01, "upper_recall": 0.99, "beta": "table", "build_s": round(build_s, 2),
                        "storage": args.storage, "rerank": args.rerank if args.storage != "f32" else None,
@@ -671,6 +697,60 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Per-level recall targets on the APS workload (the synthetic counterpart of the paper's
+    per-level sweep, Sec. 8): the index is built once; for every upper-level target tau_1 the same
+    partitions are loaded with that target, and every leaf target tau_0 is timed.  Reports
+    recall@10 against FP64 brute force, mean nprobe and queries/s for each pair."""
+    import torch
+    from paper_2506_03437_b300 import index as I
+    torch.cuda.set_device(0)
+    X, ids, Q = synth.aps_search(n=N, d=D, n_comp=N_COMP, sigma=SIGMA, nq=NQ)
+    Xd, idd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(ids).cuda(), torch.from_numpy(Q).cuda()
+    base = I.Index(D, n_leaf=N_LEAF, n_parent=N_PARENT, kmeans_iters=ITERS, seed=SEED,
+                   f_M_leaf=F_M_LEAF, f_M_parent=F_M_PARENT)
+    base.build(Xd, idd)
+    s0, C0, i0 = base.export_level(0)
+    s1, C1, i1 = base.export_level(1)
+    lor = np.empty(N, np.int32)
+    lor[i0] = np.repeat(np.arange(N_LEAF, dtype=np.int32), s0)
+    pol = np.empty(N_LEAF, np.int32)
+    pol[i1] = np.repeat(np.arange(N_PARENT, dtype=np.int32), s1)
+    del base
+    gtD, X64 = gt_fp64(torch, Xd, Qd, K)
+    stream = torch.cuda.current_stream()
+    grid = []
+    with Clocks(0) as clk:
+        for t1 in (0.8, 0.9, 0.95, 0.99, 1.0):
+            ix = I.Index(D, n_leaf=N_LEAF, n_parent=N_PARENT, kmeans_iters=ITERS, seed=SEED,
+                         f_M_leaf=F_M_LEAF, f_M_parent=F_M_PARENT, upper_recall=t1)
+            ix.load(Xd, idd, leaf_centroids=C0, leaf_of_row=lor, parent_centroids=C1, parent_of_leaf=pol)
+            for t0 in (0.8, 0.9, 0.95, 0.99):
+                oi, od, on, orr = ix.search(Qd, K, recall_target=t0, stream=stream)
+                rec = recall(torch, X64, Qd, oi, gtD, K)
+                out = (oi, od, on, orr)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    ix.search(Qd, K, recall_target=t0, out=out, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                grid.append({"tau_1": t1, "tau_0": t0, "recall_at_10": round(rec, 4),
+                             "mean_nprobe": round(on.double().mean().item(), 2), "qps": round(NQ / ms * 1e3, 1)})
+            ix.check(stream)
+            del ix
+    best = max((g for g in grid if g["recall_at_10"] >= 0.9), key=lambda g: g["qps"], default=None)
+    print(json.dumps({
+        "metric": "per-level recall-target sweep (QPS and recall@10 per (tau_1, tau_0))",
+        "value": best["qps"] if best else None, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Gaussian mixture; stands in for Sift1M-shaped data)",
+        "config": {"workload": WORKLOAD, "best_at_recall_0.9": best, "grid": grid},
+        "clocks": clk.summary()}), flush=True)
+
+
 def run_serve(args):
     """Dynamic skewed stream (start 2M x 128 from 2,000 components; 90% queries, 5% inserts,
     5% deletes; Zipf(1.2) over a hot set of 100 components rotating every 100,000 operations;
@@ -721,7 +801,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="aps", choices=["aps", "assign", "serve", "batch", "precision"],
+    ap.add_argument("--workload", default="aps", choices=["aps", "assign", "serve", "batch", "precision", "sweep"],
                     help="aps: the APS search (default); assign: tensor-core nearest-centroid assignment; "
                          "serve: the continuous-batching request loop on a dynamic skewed stream")
     ap.add_argument("--ops", type=int, default=1_000_000, help="operations of the serving stream")
@@ -743,6 +823,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-queries", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fixed", action="store_true", help="skip the fixed-nprobe comparison of the APS workload")
     ap.add_argument("--n", type=int, default=1_000_000, help="vectors (smaller for profiling runs)")
     ap.add_argument("--nq", type=int, default=10_000, help="queries per step")
     ap.add_argument("--leaves", type=int, default=1000)
@@ -767,6 +848,8 @@ def main():
         run_batch(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 
