@@ -137,6 +137,30 @@ def recall(torch, X64, Qd, ids, gtD, k, rtol=1e-5):
     return (hit.sum(1).double() / k).mean().item()
 
 
+def max_over_ranks(values, world, device):
+    """Every rank's timings replaced by their maximum over the ranks (the job ends with the
+    slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units of all ranks (each rank processes its own units_per_rank) per second."""
+    return world * units_per_rank / seconds
+
+
+def rank_queries(rank):
+    """The queries of one rank: rank 0 searches the workload's own queries, rank r > 0 an
+    independent batch from the same mixture (weak scaling, no shared data path)."""
+    if rank == 0:
+        return synth.aps_queries(1236, D, N_COMP, SIGMA, NQ)
+    return synth.aps_queries(1236, D, N_COMP, SIGMA, NQ, stream=rank)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -152,7 +176,7 @@ def run_ours(args):
 
     X, ids, Q = synth.aps_search(n=N, d=D, n_comp=N_COMP, sigma=SIGMA, nq=NQ)
     if rank > 0:   # each rank searches its own queries from the same mixture
-        Q = synth.aps_queries(1236, D, N_COMP, SIGMA, NQ, stream=rank)
+        Q = rank_queries(rank)
     Xd = torch.from_numpy(X).to(dev)
     idd = torch.from_numpy(ids).to(dev)
     Qd = torch.from_numpy(Q).to(dev)
@@ -257,12 +281,9 @@ def run_ours(args):
         ix.search(Qh, K, recall_target=tau, out=oh, stream=stream)
     e2e_s = time.perf_counter() - t0
 
-    t = torch.tensor([dev_s, e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_s, e2e_s = t.tolist()
-    qps = world * NQ * args.steps / dev_s
-    e2e_qps = world * NQ * args.steps / e2e_s
+    dev_s, e2e_s = max_over_ranks([dev_s, e2e_s], world, dev)
+    qps = whole_job_rate(NQ * args.steps, world, dev_s)
+    e2e_qps = whole_job_rate(NQ * args.steps, world, e2e_s)
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(qps, 1), "unit": "queries/s", "n_gpus": world,
