@@ -220,11 +220,21 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
   int32_t* qbr = reinterpret_cast<int32_t*>(qbd + G * kBuf);          // G x kBuf
   UnitInfo* su = reinterpret_cast<UnitInfo*>(qbr + G * kBuf);
   int32_t* s_n = reinterpret_cast<int32_t*>(su + 1);                  // G: list length after the unit
+  int32_t* s_done = s_n + G;                 // per stage: busy warps done with its current tile
+  uint32_t* s_fills = reinterpret_cast<uint32_t*>(s_done + kStages);   // per stage: copies issued so far
+  uint32_t* s_pending = s_fills + kStages;   // stages with a copy in flight
+  int32_t* s_abort = reinterpret_cast<int32_t*>(s_pending + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int part = lane % TPR, rsub = lane / TPR;
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      s_done[s] = 0;
+      s_fills[s] = 0;
+    }
+    *s_pending = 0;
+    *s_abort = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -232,9 +242,6 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
 #pragma unroll
   for (int s = 0; s < kStages; ++s) phase[s] = 0u;
   const int64_t n_units = *a.n_units;
-  unsigned pending = 0;   // thread 0: stages with a copy in flight
-  int failed = -1;        // the stage whose wait ran out
-  bool aborted = false;   // block-uniform: a wait ran out in some thread
 
   for (;;) {
     if (tid == 0) {
@@ -267,7 +274,8 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
           const uint32_t bytes = (uint32_t)rows_t * D * 4;
           mbar_arrive_expect_tx(&full[t], bytes);
           bulk_g2s(tiles + t * tile_floats, a.vec + (u.base + (int64_t)t * a.TR) * D, bytes, &full[t]);
-          pending |= 1u << t;
+          ++s_fills[t];
+          atomicOr(s_pending, 1u << t);
         }
       }
       *su = u;
@@ -298,17 +306,26 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
       any |= qid[j] >= 0;
     }
 
+    // No CTA-wide barrier per tile: each busy warp counts itself done with a
+    // stage, and the last of them refills it, so warps may run up to
+    // kStages - 1 tiles apart.  Idle warps only keep their phase bits in step.
+    const int nbusy = u.nw * u.rep;
     for (int t = 0; t < ntiles; ++t) {
       const int st = t % kStages;
+      if (!busy) {
+        phase[st] ^= 1u;
+        continue;
+      }
       const bool arrived = mbar_wait_bounded(&full[st], phase[st]);
-      if (arrived) pending &= ~(1u << st);
       phase[st] ^= 1u;
-      if (!__syncthreads_and(arrived)) {   // the same answer in every thread
-        if (!arrived) failed = st;
-        if (tid == 0) atomicExch(a.status, DEV_TIMEOUT);
-        aborted = true;
+      if (!__all_sync(0xffffffffu, arrived)) {   // the warp gives up together
+        if (lane == 0) {
+          atomicExch(a.status, DEV_TIMEOUT);
+          atomicExch(s_abort, 1);
+        }
         break;
       }
+      if (lane == 0) atomicAnd(s_pending, ~(1u << st));
       const int rows_t = min(a.TR, u.rows - t * a.TR);
       const float* tile = tiles + st * tile_floats;
       if (any) {
@@ -363,25 +380,30 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
           }
         }
       }
-      __syncthreads();   // every warp is done with this stage
-      if (tid == 0 && t + kStages < ntiles) {
-        const int tn = t + kStages;
-        const int rows_n = min(a.TR, u.rows - tn * a.TR);
-        const uint32_t bytes = (uint32_t)rows_n * D * 4;
-        mbar_arrive_expect_tx(&full[st], bytes);
-        bulk_g2s(tiles + st * tile_floats, a.vec + (u.base + (int64_t)tn * a.TR) * D, bytes, &full[st]);
-        pending |= 1u << st;
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();   // this warp's reads of the stage come before its count
+        if (atomicAdd(&s_done[st], 1) == nbusy - 1) {   // the last busy warp: the stage is free
+          s_done[st] = 0;
+          if (t + kStages < ntiles && !*(volatile int32_t*)s_abort) {
+            const int tn = t + kStages;
+            const int rows_n = min(a.TR, u.rows - tn * a.TR);
+            const uint32_t bytes = (uint32_t)rows_n * D * 4;
+            mbar_arrive_expect_tx(&full[st], bytes);
+            bulk_g2s(tiles + st * tile_floats, a.vec + (u.base + (int64_t)tn * a.TR) * D, bytes, &full[st]);
+            ++s_fills[st];
+            atomicOr(s_pending, 1u << st);
+          }
+        }
       }
     }
-    if (aborted) {
-      // tiles issued after the one that timed out may still be arriving: wait
-      // for them (bounded) before the CTA leaves
+    __syncthreads();   // every warp is done with the unit's tiles
+    if (*s_abort) {
+      // copies still in flight: wait for them (bounded) before the CTA leaves;
+      // the n-th copy of a stage completes the phase of parity (n - 1) & 1
       if (tid == 0)
         for (int s2 = 0; s2 < kStages; ++s2)
-          if (pending & (1u << s2)) {
-            const uint32_t ph = s2 == failed ? phase[s2] ^ 1u : phase[s2];   // the failed stage flipped already
-            if (mbar_wait_bounded(&full[s2], ph)) pending &= ~(1u << s2);
-          }
+          if (*s_pending & (1u << s2)) mbar_wait_bounded(&full[s2], (s_fills[s2] - 1u) & 1u);
       break;
     }
     // every copy sorts its lists down to k; copy 0 of each query set takes in
@@ -895,7 +917,7 @@ template <int D, int QW>
 size_t scan_smem(int TR) {
   return sizeof(float) * bt::kStages * (size_t)TR * D + sizeof(uint64_t) * bt::kStages +
          (sizeof(float) + sizeof(int32_t)) * (size_t)bt::kWarps * QW * bt::kBuf + sizeof(bt::UnitInfo) +
-         sizeof(int32_t) * bt::kWarps * QW + 16;
+         sizeof(int32_t) * bt::kWarps * QW + sizeof(int32_t) * (2 * bt::kStages + 2) + 16;
 }
 
 // Launches the scan with (SMs x CTAs an SM holds) CTAs.  The attribute and
