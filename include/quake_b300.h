@@ -447,11 +447,13 @@ qk_status qk_batch_set_timing(qk_batch* plan, int32_t on);
 qk_status qk_batch_stage_times(qk_batch* plan, float* ms);
 
 /* Fixed-nprobe search with one nprobe per query through the per-query search
- * kernel (one CTA per query; the comparison point of the batched path):
- * like qk_search with recall_target <= 0, but query i scans its nprobe[i]
- * nearest leaves.  nprobe may be host or device memory (read on the host:
- * the call synchronises on a device array); every value >= 1.  Single-level
- * index only (QK_ERR_STATE otherwise). */
+ * kernel (one CTA per query; the comparison point of the batched path and of
+ * the per-query "oracle nprobe"): like qk_search with recall_target <= 0, but
+ * query i scans the first nprobe[i] leaves of its candidate list S (with one
+ * level: its nprobe[i] nearest leaves; with two: the upper level's APS result,
+ * so at most ceil(f_M_leaf * n_leaf) leaves).  nprobe may be host or device
+ * memory (read on the host: the call synchronises on a device array); every
+ * value >= 1. */
 qk_status qk_search_nprobe(qk_index* index, const float* q, int64_t nq, int32_t k, const int32_t* nprobe,
                            int64_t* out_ids, float* out_dist, void* stream);
 

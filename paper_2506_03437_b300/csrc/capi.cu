@@ -859,10 +859,6 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
 qk_status qk_search_nprobe(qk_index* ix, const float* q, int64_t nq, int32_t k, const int32_t* nprobe,
                            int64_t* out_ids, float* out_dist, void* stream) {
   QK_TRY(check_ready(ix));
-  if (ix->n_parent != 0) {
-    set_error("per-query nprobe needs a single-level index");
-    return QK_ERR_STATE;
-  }
   if (nq < 0 || (nq > 0 && !nprobe)) {
     set_error("invalid search arguments");
     return QK_ERR_ARG;

@@ -214,3 +214,20 @@ def test_many_queries_per_cta_long_partitions(I):
     orc = aps.search(levels, Q[sel], aps.Params(k=10, recall_target=0.9, f_M=(0.5,)))
     n_ok, n_exc = compare_search((gi[sel], gd[sel], gn[sel], gr[sel]), orc, 10)
     assert n_exc <= 0.03 * len(sel)
+
+
+def test_per_query_nprobe_on_two_levels_equals_fixed_nprobe(I):
+    """qk_search_nprobe with every query at nprobe n is the fixed-nprobe search at n (also with
+    a parent level, where the leaves come from the upper level's APS), and mixed values match
+    per query."""
+    X, ids, Q = synth.aps_search(seed=61, n=30_000, d=64, n_comp=60, sigma=1.2, nq=120)
+    levels = kmeans.build_index(X, ids, 100, 8, iters=3, seed=9)
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.2, f_M_parent=0.5)
+    per = np.random.default_rng(2).integers(1, 12, 120).astype(np.int32)
+    gi, gd = ix.search_nprobe(Q, 10, per)
+    for n in (1, 4, 11):
+        fi, fd, fn, _ = ix.search(Q, 10, recall_target=0.0, nprobe=n)
+        ui, ud = ix.search_nprobe(Q, 10, np.full(120, n, np.int32))
+        assert np.array_equal(ui, fi) and np.array_equal(ud, fd)
+        sel = per == n
+        assert np.array_equal(gi[sel], fi[sel])
