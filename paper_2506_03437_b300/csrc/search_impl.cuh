@@ -39,8 +39,11 @@ namespace qk {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kStages = 4;
 constexpr int kBufCap = 256;
+
+// Tiles in flight per CTA: four, or three when four tiles would take more than
+// 64 KB (large d), so that two CTAs still fit on an SM.
+__host__ __device__ constexpr int stages_for(int tile_floats) { return tile_floats * 4 * 4 > 65536 ? 3 : 4; }
 
 __host__ __device__ inline int next_pow2(int x) {
   int p = 1;
@@ -61,8 +64,8 @@ struct SmemLayout {
       o += bytes;
       return at;
     };
-    stages = take(sizeof(float) * (size_t)tile_floats * kStages, 128);
-    bars = take(sizeof(uint64_t) * kStages, 8);
+    stages = take(sizeof(float) * (size_t)tile_floats * stages_for(tile_floats), 128);
+    bars = take(sizeof(uint64_t) * stages_for(tile_floats), 8);
     q = take(sizeof(float) * d, 16);
     sd = take(sizeof(float) * sortn, 16);
     sid = take(sizeof(int64_t) * sortn, 16);
@@ -120,6 +123,7 @@ struct Block {
   static constexpr int D = NV * 4 * TPR;
   static constexpr int ROWS = kThreads / TPR;
   static constexpr int TILE = ROWS * D;
+  static constexpr int STAGES = stages_for(TILE);
 
   float* stages;
   uint64_t* bars;
@@ -350,7 +354,7 @@ struct Block {
   template <class E>
   __device__ void issue(const unsigned char* rows, int32_t nrows, int t, uint32_t g) {
     constexpr int RT = ROWS * (4 / E::kBytes);
-    int st = g % kStages;
+    int st = g % STAGES;
     int r0 = t * RT;
     int nr = nrows - r0 < RT ? nrows - r0 : RT;
     uint32_t bytes = (uint32_t)nr * D * E::kBytes;
@@ -378,7 +382,7 @@ struct Block {
     int ntiles = (nrows + RT - 1) / RT;
     uint32_t g0 = consumed;
     if (tid == 0) {
-      int pre = ntiles < kStages ? ntiles : kStages;
+      int pre = ntiles < STAGES ? ntiles : STAGES;
       for (int t = 0; t < pre; ++t) issue<E>(rows, nrows, t, g0 + t);
       s->issued = g0 + pre;
     }
@@ -387,10 +391,10 @@ struct Block {
     bool tmo = false;     // this thread's wait on a tile expired
     for (int t = 0; t < ntiles; ++t) {
       uint32_t g = g0 + t;
-      int st = g % kStages;
+      int st = g % STAGES;
       if (!tmo) {
         long long waited = 0;
-        if (!mbar_wait_bounded(&bars[st], (g / kStages) & 1u, &waited)) {
+        if (!mbar_wait_bounded(&bars[st], (g / STAGES) & 1u, &waited)) {
           tmo = true;
           if (atomicCAS(status, 0, DEV_TIMEOUT) == 0) {
             diag[0] = DEV_TIMEOUT;
@@ -461,9 +465,9 @@ struct Block {
       }
       buffered += __syncthreads_count(surv);
       ++consumed;
-      if (tid == 0 && !tmo && t + kStages < ntiles) {
-        issue<E>(rows, nrows, t + kStages, g + kStages);
-        s->issued = g + kStages + 1;
+      if (tid == 0 && !tmo && t + STAGES < ntiles) {
+        issue<E>(rows, nrows, t + STAGES, g + STAGES);
+        s->issued = g + STAGES + 1;
       }
       // merge when the buffer could overflow, or as soon as R can first be
       // filled (the threshold then turns finite and filters the rest)
@@ -791,7 +795,7 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
   b.warp = threadIdx.x >> 5;
   b.consumed = 0;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(&b.bars[i], 1);
+    for (int i = 0; i < B::STAGES; ++i) mbar_init(&b.bars[i], 1);
     fence_mbar_init();
     sc.issued = 0;
   }
@@ -852,8 +856,8 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
     atomicMax(reinterpret_cast<unsigned long long*>(args.wait_stats), (unsigned long long)b.max_wait);
   // after an abort, wait (bounded) for copies still in flight before exiting
   if (threadIdx.x == 0 && b.aborted) {
-    uint32_t lo = sc.issued > kStages ? sc.issued - kStages : 0;
-    for (uint32_t g = lo; g < sc.issued; ++g) mbar_wait_bounded(&b.bars[g % kStages], (g / kStages) & 1u);
+    uint32_t lo = sc.issued > B::STAGES ? sc.issued - B::STAGES : 0;
+    for (uint32_t g = lo; g < sc.issued; ++g) mbar_wait_bounded(&b.bars[g % B::STAGES], (g / B::STAGES) & 1u);
   }
 }
 
