@@ -813,7 +813,8 @@ def run_serve(args):
     measured saturation rate.  Reports p50/p99 latency and QPS."""
     import torch
     from paper_2506_03437_b300 import index as I
-    from paper_2506_03437_b300.serving import Server, skewed_stream
+    from paper_2506_03437_b300.serving import NativeServer, Server, skewed_stream
+    Srv = NativeServer if args.server == "native" else Server
     torch.cuda.set_device(0)
     n0, n_comp = args.start, 2000
     C = synth.mixture_centers(n_comp, D, 1240)
@@ -830,13 +831,13 @@ def run_serve(args):
     print(f"serve: built {n0} x {D} ({n_leaf} leaves)", file=sys.stderr, flush=True)
     # saturation: a closed burst of queries
     burst = skewed_stream(C, ids, 20_000, SIGMA, 1242, p_query=1.0, p_insert=0.0, rate=None)
-    srv = Server(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4)
+    srv = Srv(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4)
     sat = srv.run(burst)["search_qps"]
     sat = max(sat, srv.run(burst)["search_qps"])
     rate = args.serve_load * sat / 0.9          # ops/s so that queries arrive at serve_load x saturation
     ops = skewed_stream(C, ids, args.ops, SIGMA, 1243, rate=rate)
-    srv = Server(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4, maintain_every=100_000,
-                 maint_args=maint, update_wait_s=args.update_wait)
+    srv = Srv(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4, maintain_every=100_000,
+              maint_args=maint, update_wait_s=args.update_wait)
     with Clocks(0) as clk:
         st = srv.run(ops)
     line = {"metric": "serving p50/p99 latency and QPS (dynamic skewed stream)",
@@ -845,7 +846,7 @@ def run_serve(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic skewed stream",
             "config": {"workload": f"serve_{n0}x{D}_{args.ops}ops", "start_vectors": n0, "ops": args.ops,
                        "load": args.serve_load, "saturation_qps": sat, "arrival_rate_ops": round(rate, 1),
-                       "update_wait_s": args.update_wait,
+                       "update_wait_s": args.update_wait, "server": args.server,
                        "n_leaf": n_leaf, "streams": 4, "max_batch": 2048},
             "latency": st, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -863,6 +864,8 @@ def main():
     ap.add_argument("--ops", type=int, default=1_000_000, help="operations of the serving stream")
     ap.add_argument("--serve-load", type=float, default=0.5, help="query arrival rate / saturation")
     ap.add_argument("--start", type=int, default=2_000_000, help="vectors in the index when the stream starts")
+    ap.add_argument("--server", default="native", choices=["native", "python"],
+                    help="the scheduler in the library (qk_server_*) or the Python loop of serving.py")
     ap.add_argument("--update-wait", type=float, default=0.01,
                     help="seconds the oldest pending update may wait before a group is applied")
     ap.add_argument("--n-batch", type=int, default=5_000_000, help="rows of the batching workload")

@@ -457,6 +457,73 @@ qk_status qk_batch_stage_times(qk_batch* plan, float* ms);
 qk_status qk_search_nprobe(qk_index* index, const float* q, int64_t nq, int32_t k, const int32_t* nprobe,
                            int64_t* out_ids, float* out_dist, void* stream);
 
+/* ------------------------------------------------------------------------
+ * The serving loop (continuous batching over one index; the paper serves
+ * queries and updates together with maintenance beside them, Sec. 4 and
+ * Sec. 8).  Callers submit searches, inserts and deletes from any host thread
+ * and get a ticket per request; a scheduler thread owned by the server does
+ * all GPU work through this ABI:
+ *  - waiting searches launch together as one batch whenever one of `streams`
+ *    slots is free (pinned staging, device buffers, one stream per slot), so
+ *    batches overlap and new requests join the next free slot; a batch is held
+ *    back while free device memory is below min_free_bytes;
+ *  - updates wait until update_batch are pending or the oldest has waited
+ *    update_wait_s, then the searches in flight are drained and the group is
+ *    applied as its net effect (one delete call, one insert call);
+ *  - every maintain_every requests a maintenance pass runs with *maint: with
+ *    concurrent_maintenance it is prepared by a worker thread beside the
+ *    searches (qk_maintain_prepare; updates wait meanwhile) and committed at
+ *    the next drain, otherwise it runs in place.
+ * A request's latency runs from its submission to the moment its result is in
+ * host memory.  Inserted ids must be new (a duplicate fails the whole group and
+ * stops the server).  The index must not be used directly while a server runs
+ * on it.
+ * ------------------------------------------------------------------------ */
+typedef struct qk_server qk_server;
+
+typedef struct {
+  int32_t k;                       /* results per search (<= 1024) */
+  float recall_target;             /* APS target of every search */
+  int32_t max_batch;               /* searches per batch */
+  int32_t streams;                 /* batch slots (1..16) */
+  int64_t min_free_bytes;          /* admission: free device memory needed to launch a batch */
+  int64_t maintain_every;          /* requests between maintenance passes (0: never) */
+  int32_t update_batch;            /* pending updates that trigger a group */
+  double update_wait_s;            /* longest wait of a pending update before its group is applied */
+  int32_t concurrent_maintenance;  /* 1: prepare passes beside the searches */
+  const qk_maint_params* maint;    /* pass parameters (copied; required when maintain_every > 0) */
+} qk_server_config;
+
+typedef struct {
+  int64_t searches, inserts, deletes;   /* completed requests */
+  int64_t batches, update_groups, maintenance_passes;
+  double update_s;                      /* scheduler time spent draining and applying update groups */
+  double maintenance_stall_s;           /* scheduler time spent draining and committing passes */
+  double maintenance_prepare_s;         /* passes prepared beside the searches (wall time) */
+} qk_server_stats;
+
+void qk_server_config_default(qk_server_config* cfg);
+/* Starts the scheduler thread on the current device.  Errors: QK_ERR_ARG,
+ * QK_ERR_STATE (empty index), QK_ERR_CUDA / QK_ERR_OOM. */
+qk_status qk_server_create(qk_index* index, const qk_server_config* cfg, qk_server** out);
+/* Finishes every submitted request, stops the scheduler and frees the server. */
+void qk_server_destroy(qk_server* server);
+/* q / x: d FP32 host values, copied at submission.  Tickets count from 0 in
+ * submission order.  QK_ERR_STATE once the server stopped after an error. */
+qk_status qk_server_submit_search(qk_server* server, const float* q, int64_t* ticket);
+qk_status qk_server_submit_insert(qk_server* server, const float* x, int64_t id, int64_t* ticket);
+qk_status qk_server_submit_delete(qk_server* server, int64_t id, int64_t* ticket);
+/* Results of tickets [first, first + count): done flags, search results
+ * (count x k ids and distances, -1 / +inf where not a search or not done) and
+ * latencies in seconds (-1 where not done).  Any output may be NULL. */
+qk_status qk_server_results(qk_server* server, int64_t first, int64_t count, int32_t* done, int64_t* ids,
+                            float* dist, double* latency_s);
+/* Waits until every request submitted so far is done (timeout_s <= 0: no
+ * limit; QK_ERR_TIMEOUT after it).  QK_ERR_STATE if the server stopped after
+ * an error (the message names it). */
+qk_status qk_server_drain(qk_server* server, double timeout_s);
+qk_status qk_server_get_stats(const qk_server* server, qk_server_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

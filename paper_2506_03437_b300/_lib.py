@@ -28,6 +28,9 @@ EXPORTS = [
     "qk_search_nprobe", "qk_batch_create", "qk_batch_destroy", "qk_batch_get_tiles", "qk_batch_set_tiles",
     "qk_batch_search", "qk_batch_capture", "qk_batch_replay", "qk_batch_autotune", "qk_batch_set_timing",
     "qk_batch_stage_times", "qk_maintain_prepare", "qk_maintain_commit",
+    "qk_server_config_default", "qk_server_create", "qk_server_destroy", "qk_server_submit_search",
+    "qk_server_submit_insert", "qk_server_submit_delete", "qk_server_results", "qk_server_drain",
+    "qk_server_get_stats",
 ]
 
 
@@ -56,6 +59,19 @@ class QkMaintAction(C.Structure):
 
 class QkBatchTiles(C.Structure):
     _fields_ = [("queries_per_warp", C.c_int32), ("tile_rows", C.c_int32), ("chunk_rows", C.c_int32)]
+
+
+class QkServerConfig(C.Structure):
+    _fields_ = [("k", C.c_int32), ("recall_target", C.c_float), ("max_batch", C.c_int32), ("streams", C.c_int32),
+                ("min_free_bytes", C.c_int64), ("maintain_every", C.c_int64), ("update_batch", C.c_int32),
+                ("update_wait_s", C.c_double), ("concurrent_maintenance", C.c_int32),
+                ("maint", C.POINTER(QkMaintParams))]
+
+
+class QkServerStats(C.Structure):
+    _fields_ = [("searches", C.c_int64), ("inserts", C.c_int64), ("deletes", C.c_int64), ("batches", C.c_int64),
+                ("update_groups", C.c_int64), ("maintenance_passes", C.c_int64), ("update_s", C.c_double),
+                ("maintenance_stall_s", C.c_double), ("maintenance_prepare_s", C.c_double)]
 
 
 class QkError(RuntimeError):
@@ -94,6 +110,15 @@ def _load():
         "qk_maintain_prepare": (i32, [vp, C.POINTER(QkMaintParams), C.POINTER(QkMaintAction), i32,
                                       C.POINTER(C.c_int32), vp]),
         "qk_maintain_commit": (i32, [vp, vp]),
+        "qk_server_config_default": (None, [C.POINTER(QkServerConfig)]),
+        "qk_server_create": (i32, [vp, C.POINTER(QkServerConfig), C.POINTER(vp)]),
+        "qk_server_destroy": (None, [vp]),
+        "qk_server_submit_search": (i32, [vp, vp, C.POINTER(C.c_int64)]),
+        "qk_server_submit_insert": (i32, [vp, vp, i64, C.POINTER(C.c_int64)]),
+        "qk_server_submit_delete": (i32, [vp, i64, C.POINTER(C.c_int64)]),
+        "qk_server_results": (i32, [vp, i64, i64, vp, vp, vp, vp]),
+        "qk_server_drain": (i32, [vp, f64]),
+        "qk_server_get_stats": (i32, [vp, C.POINTER(QkServerStats)]),
         "qk_batch_create": (i32, [vp, i64, i32, i32, C.POINTER(vp)]),
         "qk_batch_destroy": (None, [vp]),
         "qk_batch_get_tiles": (i32, [vp, C.POINTER(QkBatchTiles)]),

@@ -1,0 +1,575 @@
+// The serving loop in host C++ (continuous batching over one index).
+//
+// Callers submit searches, inserts and deletes from any thread and get a
+// ticket each.  One scheduler thread owns the GPU work:
+//   - searches that are waiting when one of `streams` slots is free launch
+//     together as one batch on that slot's stream (pinned host staging,
+//     device buffers, an event per batch), so batches overlap on the device
+//     and requests that arrive meanwhile join the next free slot; a batch
+//     is held back while free device memory is below min_free_bytes;
+//   - updates wait until update_batch of them are pending or the oldest has
+//     waited update_wait_s; then the searches in flight are drained and the
+//     group is applied as its net effect (one delete call, one insert call:
+//     an id inserted and deleted inside the group never reaches the index, an
+//     id deleted and inserted again is deleted first);
+//   - every maintain_every operations a maintenance pass (Sec. 4) runs.  With
+//     concurrent maintenance a worker thread prepares it on its own stream
+//     (qk_maintain_prepare) while searches go on, updates wait, and the pass
+//     is committed at the next drain; otherwise the scheduler drains and runs
+//     it in place.  A pass also needs min_window queries since the previous
+//     one (its statistics window).
+// A request's latency runs from its submission to the moment its result is in
+// host memory.  Every GPU step is a call of the index's own C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "index.cuh"
+
+using namespace qk;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Op {
+  int64_t ticket;
+  int kind;              // 0 search, 1 insert, 2 delete
+  int64_t id;            // inserted / deleted id
+  Clock::time_point t;   // submission
+};
+
+struct Result {
+  std::atomic<int32_t> done{0};
+  double latency_s = 0.0;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t event = nullptr;
+  float* q_host = nullptr;
+  int64_t* ids_host = nullptr;
+  float* dist_host = nullptr;
+  float* q_dev = nullptr;
+  int64_t* ids_dev = nullptr;
+  float* dist_dev = nullptr;
+  std::vector<int64_t> tickets;   // of the batch in flight
+  std::vector<Clock::time_point> t0;
+  bool busy = false;
+};
+
+}  // namespace
+
+struct qk_server {
+  qk_index* ix = nullptr;
+  qk_server_config cfg{};
+  std::vector<double> lam_s, lam_us;
+  qk_maint_params maint{};
+  int d = 0;
+  int device = 0;
+  // submissions
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Op> searches, updates;
+  std::deque<std::vector<float>> search_q; // queries of the waiting searches (same order as `searches`)
+  std::unordered_map<int64_t, std::vector<float>> insert_vecs;
+  int64_t next_ticket = 0;
+  bool stopping = false;
+  // results (grown under mu; read without it once done is set)
+  std::deque<Result> results;
+  std::vector<int64_t> res_ids;            // k per ticket
+  std::vector<float> res_dist;
+  std::mutex res_mu;
+  // scheduler state
+  std::vector<Slot> slots;
+  std::thread scheduler;
+  std::thread preparer;
+  std::atomic<int> prep_state{0};          // 0 idle, 1 running, 2 ready, 3 failed
+  std::string prep_error;
+  cudaStream_t maint_stream = nullptr;
+  int64_t ops_seen = 0, passes = 0, searched_since = 0;
+  // statistics
+  std::atomic<int64_t> n_search{0}, n_insert{0}, n_delete{0}, batches{0}, drains{0};
+  double update_s = 0.0, maint_stall_s = 0.0, maint_prepare_s = 0.0;
+  std::atomic<int32_t> failed{0};
+  std::string error;
+};
+
+namespace {
+
+double secs(Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); }
+
+void set_done(qk_server* sv, int64_t ticket, Clock::time_point t0, Clock::time_point now) {
+  Result* r;
+  {
+    std::lock_guard<std::mutex> g(sv->res_mu);
+    r = &sv->results[(size_t)ticket];
+  }
+  r->latency_s = secs(t0, now);
+  r->done.store(1, std::memory_order_release);
+}
+
+void finish_slot(qk_server* sv, Slot& s) {
+  const int k = sv->cfg.k;
+  const auto now = Clock::now();
+  {
+    std::lock_guard<std::mutex> g(sv->res_mu);
+    for (size_t j = 0; j < s.tickets.size(); ++j) {
+      std::memcpy(&sv->res_ids[(size_t)s.tickets[j] * k], s.ids_host + j * k, sizeof(int64_t) * k);
+      std::memcpy(&sv->res_dist[(size_t)s.tickets[j] * k], s.dist_host + j * k, sizeof(float) * k);
+    }
+  }
+  for (size_t j = 0; j < s.tickets.size(); ++j) set_done(sv, s.tickets[j], s.t0[j], now);
+  sv->n_search += (int64_t)s.tickets.size();
+  s.tickets.clear();
+  s.t0.clear();
+  s.busy = false;
+}
+
+bool fail(qk_server* sv, qk_status st, const char* what) {
+  if (st == QK_OK) return false;
+  if (!sv->failed.exchange(1)) sv->error = std::string(what) + ": " + qk_last_error();
+  return true;
+}
+
+void drain(qk_server* sv) {
+  for (Slot& s : sv->slots)
+    if (s.busy) {
+      cudaEventSynchronize(s.event);
+      finish_slot(sv, s);
+    }
+}
+
+bool free_ok(qk_server* sv) {
+  if (sv->cfg.min_free_bytes <= 0) return true;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return true;
+  return (int64_t)fr >= sv->cfg.min_free_bytes;
+}
+
+// Applies a group of updates as its net effect (see the file comment).
+void apply_updates(qk_server* sv, std::vector<Op>& group) {
+  const auto c0 = Clock::now();
+  drain(sv);
+  struct St {
+    bool del = false;
+    int64_t ins = -1;   // position in group of the live insert
+  };
+  std::unordered_map<int64_t, St> state;
+  for (size_t j = 0; j < group.size(); ++j) {
+    St& s = state[group[j].id];
+    if (group[j].kind == 1) s.ins = (int64_t)j;
+    else if (s.ins >= 0) s.ins = -1;
+    else s.del = true;
+  }
+  std::vector<int64_t> del_ids, ins_ids;
+  std::vector<float> ins_x;
+  {
+    std::unordered_map<int64_t, bool> seen;
+    for (const Op& o : group)
+      if (o.kind == 2 && state[o.id].del && !seen[o.id]) {
+        seen[o.id] = true;
+        del_ids.push_back(o.id);
+      }
+  }
+  std::vector<int64_t> pos;
+  for (auto& kv : state)
+    if (kv.second.ins >= 0) pos.push_back(kv.second.ins);
+  std::sort(pos.begin(), pos.end());
+  {
+    std::lock_guard<std::mutex> g(sv->mu);
+    for (int64_t p : pos) {
+      const Op& o = group[(size_t)p];
+      auto it = sv->insert_vecs.find(o.ticket);
+      ins_ids.push_back(o.id);
+      ins_x.insert(ins_x.end(), it->second.begin(), it->second.end());
+    }
+    for (const Op& o : group)
+      if (o.kind == 1) sv->insert_vecs.erase(o.ticket);
+  }
+  if (!del_ids.empty()) {
+    int64_t removed = 0;
+    fail(sv, qk_delete(sv->ix, del_ids.data(), (int64_t)del_ids.size(), &removed, nullptr), "delete");
+  }
+  if (!ins_ids.empty())
+    fail(sv, qk_insert(sv->ix, ins_x.data(), ins_ids.data(), (int64_t)ins_ids.size(), nullptr), "insert");
+  const auto now = Clock::now();
+  for (const Op& o : group) {
+    set_done(sv, o.ticket, o.t, now);
+    if (o.kind == 1) ++sv->n_insert;
+    else ++sv->n_delete;
+  }
+  ++sv->drains;
+  sv->update_s += secs(c0, now);
+}
+
+void run_prepare(qk_server* sv) {
+  cudaSetDevice(sv->device);
+  const qk_status st = qk_maintain_prepare(sv->ix, &sv->maint, nullptr, 0, nullptr, sv->maint_stream);
+  if (st != QK_OK) {
+    sv->prep_error = qk_last_error();
+    sv->prep_state.store(3);
+  } else {
+    sv->prep_state.store(2);
+  }
+}
+
+void scheduler_loop(qk_server* sv) {
+  cudaSetDevice(sv->device);
+  const int d = sv->d;
+  const int64_t min_window =
+      sv->cfg.maintain_every > 0 ? std::max<int64_t>(1, std::min<int64_t>(1000, sv->cfg.maintain_every / 10)) : 1;
+  Clock::time_point prep_t0{};
+  for (;;) {
+    // finished batches
+    for (Slot& s : sv->slots)
+      if (s.busy && cudaEventQuery(s.event) == cudaSuccess) finish_slot(sv, s);
+    // a prepared maintenance pass: drain and commit
+    const int ps = sv->prep_state.load();
+    if (ps == 2 || ps == 3) {
+      sv->preparer.join();
+      const auto c0 = Clock::now();
+      drain(sv);
+      if (ps == 2) fail(sv, qk_maintain_commit(sv->ix, sv->maint_stream), "maintain_commit");
+      else if (!sv->failed.exchange(1)) sv->error = "maintain_prepare: " + sv->prep_error;
+      ++sv->passes;
+      sv->searched_since = 0;
+      sv->maint_stall_s += secs(c0, Clock::now());
+      sv->maint_prepare_s += secs(prep_t0, c0);
+      sv->prep_state.store(0);
+    }
+    const bool preparing = sv->prep_state.load() == 1;
+    // take the due updates (not while a pass is being prepared)
+    std::vector<Op> group;
+    bool maint_due = false;
+    {
+      std::unique_lock<std::mutex> g(sv->mu);
+      if (!preparing && !sv->updates.empty()) {
+        const double waited = secs(sv->updates.front().t, Clock::now());
+        if ((int64_t)sv->updates.size() >= sv->cfg.update_batch || waited >= sv->cfg.update_wait_s ||
+            (sv->searches.empty() && sv->stopping)) {
+          group.assign(sv->updates.begin(), sv->updates.end());
+          sv->updates.clear();
+        }
+      }
+      maint_due = sv->cfg.maintain_every > 0 && sv->prep_state.load() == 0 &&
+                  sv->ops_seen / sv->cfg.maintain_every > sv->passes && sv->searched_since >= min_window;
+    }
+    if (!group.empty()) apply_updates(sv, group);
+    if (maint_due) {
+      if (sv->cfg.concurrent_maintenance) {
+        std::vector<Op> pending;
+        {
+          std::lock_guard<std::mutex> g(sv->mu);   // the pass plans from the current index
+          pending.assign(sv->updates.begin(), sv->updates.end());
+          sv->updates.clear();
+        }
+        if (!pending.empty()) apply_updates(sv, pending);
+        prep_t0 = Clock::now();
+        sv->prep_state.store(1);
+        sv->preparer = std::thread(run_prepare, sv);
+      } else {
+        const auto c0 = Clock::now();
+        drain(sv);
+        fail(sv, qk_maintain(sv->ix, &sv->maint, nullptr, 0, nullptr, nullptr), "maintain");
+        ++sv->passes;
+        sv->searched_since = 0;
+        sv->maint_stall_s += secs(c0, Clock::now());
+      }
+    }
+    // launch batches while a slot is free and memory allows
+    bool launched = false;
+    for (;;) {
+      Slot* slot = nullptr;
+      for (Slot& s : sv->slots)
+        if (!s.busy) {
+          slot = &s;
+          break;
+        }
+      if (!slot) break;
+      std::vector<Op> batch;
+      {
+        std::lock_guard<std::mutex> g(sv->mu);
+        if (sv->searches.empty()) break;
+        if (!free_ok(sv)) break;
+        const size_t n = std::min<size_t>(sv->searches.size(), (size_t)sv->cfg.max_batch);
+        for (size_t j = 0; j < n; ++j) {
+          batch.push_back(sv->searches.front());
+          std::memcpy(slot->q_host + j * d, sv->search_q.front().data(), sizeof(float) * d);
+          sv->searches.pop_front();
+          sv->search_q.pop_front();
+        }
+      }
+      const int64_t n = (int64_t)batch.size();
+      for (const Op& o : batch) {
+        slot->tickets.push_back(o.ticket);
+        slot->t0.push_back(o.t);
+      }
+      cudaStream_t st = slot->stream;
+      const int k = sv->cfg.k;
+      cudaMemcpyAsync(slot->q_dev, slot->q_host, sizeof(float) * n * d, cudaMemcpyHostToDevice, st);
+      if (fail(sv, qk_search(sv->ix, slot->q_dev, n, k, sv->cfg.recall_target, 0, slot->ids_dev, slot->dist_dev,
+                             nullptr, nullptr, st),
+               "search")) {
+        slot->tickets.clear();
+        slot->t0.clear();
+        break;
+      }
+      cudaMemcpyAsync(slot->ids_host, slot->ids_dev, sizeof(int64_t) * n * k, cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(slot->dist_host, slot->dist_dev, sizeof(float) * n * k, cudaMemcpyDeviceToHost, st);
+      cudaEventRecord(slot->event, st);
+      slot->busy = true;
+      sv->searched_since += n;
+      ++sv->batches;
+      launched = true;
+    }
+    // leave when stopping with nothing left; otherwise wait a little for work
+    bool any_busy = false;
+    for (Slot& s : sv->slots) any_busy |= s.busy;
+    if (launched) continue;
+    if (any_busy) {   // batches in flight: poll their events soon
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      continue;
+    }
+    std::unique_lock<std::mutex> g(sv->mu);
+    if (sv->stopping && sv->searches.empty() && sv->updates.empty() && sv->prep_state.load() == 0) return;
+    sv->cv.wait_for(g, std::chrono::microseconds(200));
+  }
+}
+
+qk_status submit(qk_server* sv, int kind, const float* x, int64_t id, int64_t* ticket) {
+  if (!sv || !ticket) {
+    set_error("null argument");
+    return QK_ERR_ARG;
+  }
+  if (sv->failed.load()) {
+    set_error("the server stopped after an error: " + sv->error);
+    return QK_ERR_STATE;
+  }
+  const int k = sv->cfg.k;
+  std::lock_guard<std::mutex> g(sv->mu);
+  if (sv->stopping) {
+    set_error("the server is stopping");
+    return QK_ERR_STATE;
+  }
+  const int64_t t = sv->next_ticket++;
+  {
+    std::lock_guard<std::mutex> gr(sv->res_mu);
+    sv->results.emplace_back();
+    sv->res_ids.resize((size_t)(t + 1) * k, -1);
+    sv->res_dist.resize((size_t)(t + 1) * k, INFINITY);
+  }
+  Op o{t, kind, id, Clock::now()};
+  if (kind == 0) {
+    sv->searches.push_back(o);
+    sv->search_q.emplace_back(x, x + sv->d);
+  } else {
+    if (kind == 1) sv->insert_vecs.emplace(t, std::vector<float>(x, x + sv->d));
+    sv->updates.push_back(o);
+  }
+  ++sv->ops_seen;
+  *ticket = t;
+  sv->cv.notify_one();
+  return QK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qk_server_config_default(qk_server_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->k = 10;
+  c->recall_target = 0.9f;
+  c->max_batch = 2048;
+  c->streams = 4;
+  c->min_free_bytes = 1LL << 30;
+  c->maintain_every = 0;
+  c->update_batch = 1024;
+  c->update_wait_s = 0.01;
+  c->concurrent_maintenance = 1;
+  c->maint = nullptr;
+}
+
+qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server** out) {
+  if (!ix || !cfg || !out) {
+    set_error("null argument");
+    return QK_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!ix->ready) {
+    set_error("index is empty: build or load it first");
+    return QK_ERR_STATE;
+  }
+  if (cfg->k < 1 || cfg->k > 1024 || cfg->max_batch < 1 || cfg->streams < 1 || cfg->streams > kWorkSlots ||
+      cfg->update_batch < 1 || !(cfg->update_wait_s >= 0) || cfg->maintain_every < 0 ||
+      (cfg->maintain_every > 0 && !cfg->maint)) {
+    set_error("invalid server configuration");
+    return QK_ERR_ARG;
+  }
+  qk_server* sv = new qk_server();
+  sv->ix = ix;
+  sv->cfg = *cfg;
+  sv->d = ix->cfg.d;
+  cudaGetDevice(&sv->device);
+  if (cfg->maint) {   // the pass parameters are copied, lambda table included
+    sv->maint = *cfg->maint;
+    sv->lam_s.assign(cfg->maint->lambda_sizes, cfg->maint->lambda_sizes + cfg->maint->lambda_points);
+    sv->lam_us.assign(cfg->maint->lambda_us, cfg->maint->lambda_us + cfg->maint->lambda_points);
+    sv->maint.lambda_sizes = sv->lam_s.data();
+    sv->maint.lambda_us = sv->lam_us.data();
+    sv->cfg.maint = &sv->maint;
+  }
+  const int d = sv->d, k = cfg->k, mb = cfg->max_batch;
+  qk_status st = QK_OK;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && st == QK_OK) st = cuda_status(e, "server buffers");
+  };
+  sv->slots.resize(cfg->streams);
+  for (Slot& s : sv->slots) {
+    ck(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+    ck(cudaEventCreateWithFlags(&s.event, cudaEventDisableTiming));
+    ck(cudaMallocHost(&s.q_host, sizeof(float) * mb * d));
+    ck(cudaMallocHost(&s.ids_host, sizeof(int64_t) * mb * k));
+    ck(cudaMallocHost(&s.dist_host, sizeof(float) * mb * k));
+    ck(cudaMalloc(&s.q_dev, sizeof(float) * mb * d));
+    ck(cudaMalloc(&s.ids_dev, sizeof(int64_t) * mb * k));
+    ck(cudaMalloc(&s.dist_dev, sizeof(float) * mb * k));
+  }
+  ck(cudaStreamCreateWithFlags(&sv->maint_stream, cudaStreamNonBlocking));
+  if (st != QK_OK) {
+    qk_server_destroy(sv);
+    return st;
+  }
+  sv->scheduler = std::thread(scheduler_loop, sv);
+  *out = sv;
+  return QK_OK;
+}
+
+qk_status qk_server_submit_search(qk_server* sv, const float* q, int64_t* ticket) {
+  if (!q) {
+    set_error("null query");
+    return QK_ERR_ARG;
+  }
+  return submit(sv, 0, q, -1, ticket);
+}
+
+qk_status qk_server_submit_insert(qk_server* sv, const float* x, int64_t id, int64_t* ticket) {
+  if (!x) {
+    set_error("null vector");
+    return QK_ERR_ARG;
+  }
+  return submit(sv, 1, x, id, ticket);
+}
+
+qk_status qk_server_submit_delete(qk_server* sv, int64_t id, int64_t* ticket) {
+  return submit(sv, 2, nullptr, id, ticket);
+}
+
+qk_status qk_server_results(qk_server* sv, int64_t first, int64_t count, int32_t* done, int64_t* ids,
+                            float* dist, double* latency_s) {
+  if (!sv || count < 0 || first < 0) {
+    set_error("invalid arguments");
+    return QK_ERR_ARG;
+  }
+  const int k = sv->cfg.k;
+  std::lock_guard<std::mutex> g(sv->res_mu);
+  if (first + count > (int64_t)sv->results.size()) {
+    set_error("ticket out of range");
+    return QK_ERR_ARG;
+  }
+  for (int64_t j = 0; j < count; ++j) {
+    const Result& r = sv->results[(size_t)(first + j)];
+    const int32_t dn = r.done.load(std::memory_order_acquire);
+    if (done) done[j] = dn;
+    if (latency_s) latency_s[j] = dn ? r.latency_s : -1.0;
+    if (ids) std::memcpy(ids + j * k, &sv->res_ids[(size_t)(first + j) * k], sizeof(int64_t) * k);
+    if (dist) std::memcpy(dist + j * k, &sv->res_dist[(size_t)(first + j) * k], sizeof(float) * k);
+  }
+  return QK_OK;
+}
+
+qk_status qk_server_drain(qk_server* sv, double timeout_s) {
+  if (!sv) {
+    set_error("null server");
+    return QK_ERR_ARG;
+  }
+  const auto t0 = Clock::now();
+  for (;;) {
+    if (sv->failed.load()) {
+      set_error("the server stopped after an error: " + sv->error);
+      return QK_ERR_STATE;
+    }
+    int64_t n;
+    {
+      std::lock_guard<std::mutex> g(sv->res_mu);
+      n = (int64_t)sv->results.size();
+    }
+    bool all = true;
+    {
+      std::lock_guard<std::mutex> g(sv->res_mu);
+      for (int64_t j = n - 1; j >= 0 && all; --j) all = sv->results[(size_t)j].done.load() != 0;
+    }
+    if (all) return QK_OK;
+    if (timeout_s > 0 && secs(t0, Clock::now()) > timeout_s) {
+      set_error("drain timed out");
+      return QK_ERR_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+}
+
+qk_status qk_server_get_stats(const qk_server* sv, qk_server_stats* out) {
+  if (!sv || !out) {
+    set_error("null argument");
+    return QK_ERR_ARG;
+  }
+  out->searches = sv->n_search.load();
+  out->inserts = sv->n_insert.load();
+  out->deletes = sv->n_delete.load();
+  out->batches = sv->batches.load();
+  out->update_groups = sv->drains.load();
+  out->maintenance_passes = sv->passes;
+  out->update_s = sv->update_s;
+  out->maintenance_stall_s = sv->maint_stall_s;
+  out->maintenance_prepare_s = sv->maint_prepare_s;
+  return QK_OK;
+}
+
+void qk_server_destroy(qk_server* sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> g(sv->mu);
+    sv->stopping = true;
+  }
+  sv->cv.notify_all();
+  if (sv->scheduler.joinable()) sv->scheduler.join();
+  if (sv->preparer.joinable()) sv->preparer.join();
+  for (Slot& s : sv->slots) {
+    if (s.busy && s.event) cudaEventSynchronize(s.event);
+    if (s.event) cudaEventDestroy(s.event);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.q_host) cudaFreeHost(s.q_host);
+    if (s.ids_host) cudaFreeHost(s.ids_host);
+    if (s.dist_host) cudaFreeHost(s.dist_host);
+    if (s.q_dev) cudaFree(s.q_dev);
+    if (s.ids_dev) cudaFree(s.ids_dev);
+    if (s.dist_dev) cudaFree(s.dist_dev);
+  }
+  if (sv->maint_stream) cudaStreamDestroy(sv->maint_stream);
+  delete sv;
+}
+
+}  // extern "C"

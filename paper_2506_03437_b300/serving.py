@@ -321,3 +321,103 @@ def skewed_stream(centers, start_ids, n_ops, sigma, seed, hot=100, zipf=1.2, rot
         else:
             kind[j] = SEARCH
     return Ops(t, kind, vec, ref)
+
+
+class NativeServer:
+    """The same serving loop run by the library's scheduler thread (qk_server_* in
+    include/quake_b300.h): this class only drives the open-loop arrivals and reads the
+    results.  A request's latency counts from its scheduled arrival: the time between the
+    arrival and the submission (if the driver runs late) is added to the server's own."""
+
+    def __init__(self, index, d, k=10, recall_target=0.9, max_batch=2048, streams=4, min_free_bytes=1 << 30,
+                 maintain_every=0, maint_args=None, update_batch=1024, update_wait_s=0.01,
+                 concurrent_maintenance=True):
+        import ctypes as C
+        from . import _lib as L
+        self.C, self.L = C, L
+        self.ix, self.d, self.k = index, d, k
+        cfg = L.QkServerConfig()
+        L.lib.qk_server_config_default(C.byref(cfg))
+        cfg.k, cfg.recall_target, cfg.max_batch, cfg.streams = k, recall_target, max_batch, streams
+        cfg.min_free_bytes, cfg.maintain_every = min_free_bytes, maintain_every
+        cfg.update_batch, cfg.update_wait_s = update_batch, update_wait_s
+        cfg.concurrent_maintenance = int(bool(concurrent_maintenance))
+        self._keep = []
+        if maintain_every:
+            a = dict(tau_us=0.25, alpha=0.9, refine_radius=50, refine_iters=1, split_iters=10, s_min=0,
+                     refine=True, window=0)
+            a.update(maint_args or {})
+            ls = np.ascontiguousarray(a.pop("lam_sizes"), np.float64)
+            lu = np.ascontiguousarray(a.pop("lam_us"), np.float64)
+            p = L.QkMaintParams()
+            p.lambda_sizes = ls.ctypes.data_as(C.POINTER(C.c_double))
+            p.lambda_us = lu.ctypes.data_as(C.POINTER(C.c_double))
+            p.lambda_points = int(ls.shape[0])
+            p.refine_radius, p.refine_iters, p.split_iters = a["refine_radius"], a["refine_iters"], a["split_iters"]
+            p.s_min, p.refine, p.tau_us = a["s_min"], int(bool(a["refine"])), a["tau_us"]
+            p.alpha, p.window = a["alpha"], a["window"]
+            self._keep += [ls, lu, p]
+            cfg.maint = C.pointer(p)
+        self.cfg = cfg
+
+    def run(self, ops, keep_results=False):
+        """Serves the stream (a fresh server per run, so ticket j is op j) and returns the
+        same summary as Server.run."""
+        C, L = self.C, self.L
+        h = C.c_void_p()
+        L.check(L.lib.qk_server_create(self.ix._h, C.byref(self.cfg), C.byref(h)))
+        n = len(ops)
+        lag = np.zeros(n)
+        vec = np.ascontiguousarray(ops.vec, np.float32)
+        base, row = vec.ctypes.data, vec.shape[1] * 4
+        kinds, refs, ts = ops.kind.tolist(), ops.ref.tolist(), ops.t.tolist()
+        tk = C.c_int64()
+        sub_s, sub_i, sub_d = L.lib.qk_server_submit_search, L.lib.qk_server_submit_insert, L.lib.qk_server_submit_delete
+        try:
+            t0 = time.perf_counter()
+            for j in range(n):
+                now = time.perf_counter() - t0
+                if ts[j] > now:
+                    if ts[j] - now > 2e-4:
+                        time.sleep(ts[j] - now - 1e-4)
+                    while time.perf_counter() - t0 < ts[j]:
+                        pass
+                    now = time.perf_counter() - t0
+                lag[j] = now - ts[j]
+                kd = kinds[j]
+                if kd == SEARCH:
+                    st = sub_s(h, base + j * row, C.byref(tk))
+                elif kd == INSERT:
+                    st = sub_i(h, base + j * row, refs[j], C.byref(tk))
+                else:
+                    st = sub_d(h, refs[j], C.byref(tk))
+                L.check(st)
+            L.check(L.lib.qk_server_drain(h, 0.0))
+            wall = time.perf_counter() - t0
+            done = np.zeros(n, np.int32)
+            lat = np.zeros(n)
+            ids = np.empty((n, self.k), np.int64) if keep_results else None
+            dist = np.empty((n, self.k), np.float32) if keep_results else None
+            L.check(L.lib.qk_server_results(h, 0, n, L.ptr(done), L.ptr(ids), L.ptr(dist), L.ptr(lat)))
+            stt = L.QkServerStats()
+            L.check(L.lib.qk_server_get_stats(h, C.byref(stt)))
+        finally:
+            L.lib.qk_server_destroy(h)
+        assert done.all()
+        lat = lat + lag
+        self.out_ids, self.out_dist = ids, dist
+        out = {"wall_s": round(wall, 4), "batches": stt.batches, "maintenance_passes": stt.maintenance_passes,
+               "update_drains": stt.update_groups, "update_s": round(stt.update_s, 4),
+               "maintenance_stall_s": round(stt.maintenance_stall_s, 4),
+               "maintenance_prepare_s": round(stt.maintenance_prepare_s, 4),
+               "driver_lag_p99_ms": round(float(np.percentile(lag, 99)) * 1e3, 4),
+               "concurrent_maintenance": bool(self.cfg.concurrent_maintenance), "native": True}
+        for kind, name in ((SEARCH, "search"), (INSERT, "insert"), (DELETE, "delete")):
+            v = lat[ops.kind == kind]
+            if v.shape[0]:
+                a = v * 1e3
+                out[name] = {"n": int(v.shape[0]), "p50_ms": round(float(np.percentile(a, 50)), 4),
+                             "p99_ms": round(float(np.percentile(a, 99)), 4), "mean_ms": round(float(a.mean()), 4)}
+        n_s = int((ops.kind == SEARCH).sum())
+        out["search_qps"] = round(n_s / wall, 1) if wall > 0 else None
+        return out

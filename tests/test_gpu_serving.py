@@ -57,3 +57,46 @@ def test_stream_with_updates_and_maintenance(concurrent):
         elif kind == 2:
             live.discard(int(ref))
     assert sorted(got.tolist()) == sorted(live)
+
+
+def test_native_server_results_alone_equal_results_in_the_mix():
+    from paper_2506_03437_b300.serving import NativeServer, Ops
+    X, ids, Q = synth.aps_search(seed=43, n=30_000, d=64, n_comp=40, sigma=1.2, nq=3000)
+    levels = kmeans.build_index(X, ids, 150, 8, iters=3, seed=5)
+    from paper_2506_03437_b300 import index as I
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.15, f_M_parent=0.5)
+    alone = [ix.search(Q[j:j + 1], 10, recall_target=0.9) for j in range(0, 3000, 7)]
+    ops = Ops(np.zeros(3000), np.zeros(3000, np.int8), Q, np.full(3000, -1))
+    srv = NativeServer(ix, 64, k=10, recall_target=0.9, max_batch=200, streams=4)
+    st = srv.run(ops, keep_results=True)
+    assert st["batches"] >= 15 and st["search"]["n"] == 3000
+    for n, j in enumerate(range(0, 3000, 7)):
+        assert np.array_equal(srv.out_ids[j], alone[n][0][0])
+        assert np.array_equal(srv.out_dist[j], alone[n][1][0])
+
+
+@pytest.mark.parametrize("concurrent", [False, True])
+def test_native_server_stream_with_updates_and_maintenance(concurrent):
+    from paper_2506_03437_b300.serving import NativeServer, skewed_stream
+    X, ids, Q = synth.aps_search(seed=44, n=20_000, d=64, n_comp=50, sigma=1.2, nq=1)
+    levels = kmeans.build_index(X, ids, 100, 0, iters=3, seed=6)
+    from paper_2506_03437_b300 import index as I
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.2)
+    C = synth.mixture_centers(50, 64, 44)
+    ops = skewed_stream(C, ids, 6000, 1.2, 8, hot=10, rotate=2000, rate=1e5)
+    srv = NativeServer(ix, 64, k=10, recall_target=0.9, max_batch=256, streams=3, maintain_every=3000,
+                       concurrent_maintenance=concurrent,
+                       maint_args=dict(lam_sizes=[0, 1000], lam_us=[2.0, 47.0], tau_us=0.25, alpha=0.9,
+                                       refine_radius=8, s_min=20))
+    st = srv.run(ops)
+    assert ix.info()["n"] == 20_000 + ops.count(1) - ops.count(2)
+    assert (st["maintenance_passes"] == 2 if not concurrent else st["maintenance_passes"] >= 1)
+    assert st["search"]["n"] == ops.count(0) and st["insert"]["n"] == ops.count(1)
+    _, _, got = ix.export_level(0)
+    live = set(ids.tolist())
+    for kind, ref in zip(ops.kind, ops.ref):
+        if kind == 1:
+            live.add(int(ref))
+        elif kind == 2:
+            live.discard(int(ref))
+    assert sorted(got.tolist()) == sorted(live)
