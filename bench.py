@@ -303,7 +303,7 @@ def run_ours(args):
             "e2e": {"value": round(e2e_qps, 1), "unit": "queries/s",
                     "h2d_bytes_per_step": NQ * D * 4,
                     "d2h_bytes_per_step": NQ * K * (8 + 4) + NQ * 8},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": args.steps,   # one aps_search_kernel per step (plus a memset of its work counter)
             "roofline": roofline(achieved, peak, peak_kind, avg_launch_s),
             "clocks": clk.summary(),
         }
