@@ -100,3 +100,35 @@ def test_native_server_stream_with_updates_and_maintenance(concurrent):
         elif kind == 2:
             live.discard(int(ref))
     assert sorted(got.tolist()) == sorted(live)
+
+
+def test_native_server_rejects_bad_config_and_reports_a_failed_update():
+    """An invalid configuration is refused; an insert of an id the index already holds fails
+    its update group, stops the server, and drain reports it."""
+    import ctypes as C
+    from paper_2506_03437_b300 import _lib as L
+    X, ids, Q = synth.aps_search(seed=45, n=5000, d=64, n_comp=10, sigma=1.0, nq=4)
+    levels = kmeans.build_index(X, ids, 20, 0, iters=2, seed=2)
+    from paper_2506_03437_b300 import index as I
+    ix = make_index(I, X, ids, levels)
+    cfg = L.QkServerConfig()
+    L.lib.qk_server_config_default(C.byref(cfg))
+    h = C.c_void_p()
+    bad = L.QkServerConfig.from_buffer_copy(cfg)
+    bad.streams = 0
+    assert L.lib.qk_server_create(ix._h, C.byref(bad), C.byref(h)) == L.ERR_ARG
+    bad = L.QkServerConfig.from_buffer_copy(cfg)
+    bad.maintain_every = 100   # a maintenance cadence needs pass parameters
+    assert L.lib.qk_server_create(ix._h, C.byref(bad), C.byref(h)) == L.ERR_ARG
+    L.check(L.lib.qk_server_create(ix._h, C.byref(cfg), C.byref(h)))
+    try:
+        t = C.c_int64()
+        L.check(L.lib.qk_server_submit_search(h, Q.ctypes.data, C.byref(t)))
+        x = np.ascontiguousarray(X[0] + 0.5)
+        L.check(L.lib.qk_server_submit_insert(h, x.ctypes.data, 7, C.byref(t)))   # id 7 exists
+        assert L.lib.qk_server_drain(h, 30.0) == L.ERR_STATE
+        assert b"insert" in L.lib.qk_last_error()
+        assert L.lib.qk_server_submit_delete(h, 3, C.byref(t)) == L.ERR_STATE   # stopped
+    finally:
+        L.lib.qk_server_destroy(h)
+    assert ix.info()["n"] == 5000   # the failed group inserted nothing
