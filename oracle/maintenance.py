@@ -28,7 +28,12 @@ technical report:
       N_l is updated after every commit.  Insert descends greedily (the
       nearest centroid at each level, ties to the lower index).  Delete swaps
       the last row of the partition into the freed slot.
+  M9  (optional, level_band) Levels are added and removed by a size band on
+      the top level, [sqrt(N0)/4, 4 sqrt(N0)] (see level_band_action): the
+      paper's thresholds are in its technical report, which is not available.
 """
+
+import math
 
 import numpy as np
 
@@ -199,7 +204,7 @@ class MaintParams:
     """Maintenance parameters (Sec. 4 and Sec. 8.1 defaults where the paper gives them)."""
 
     def __init__(self, lam, tau=0.25, alpha=0.9, refine_radius=50, refine_iters=1, split_iters=10,
-                 s_min=0, seed=1234, refine=True):
+                 s_min=0, seed=1234, refine=True, level_band=False, level_iters=10):
         self.lam = lam
         self.tau = tau
         self.alpha = alpha
@@ -209,6 +214,8 @@ class MaintParams:
         self.s_min = s_min
         self.seed = seed
         self.refine = refine
+        self.level_band = level_band
+        self.level_iters = level_iters
 
 
 def split_seed(seed, level, j):
@@ -344,6 +351,47 @@ def maintain_level(level, A, prm, level_no, parent_of=None):
     return log, keep
 
 
+def level_band_action(n_leaf, n_parent):
+    """Reading L1 (the paper adds and removes levels, Sec. 3-4, with thresholds only in its
+    technical report): the top level should hold between sqrt(N0)/4 and 4 sqrt(N0)
+    centroids, N0 = n_leaf.  One level is the top itself, so it needs a parent level once
+    N0 > 4 sqrt(N0), i.e. N0 > 16; two levels with N0 <= 16 drop the parents; parents
+    outside the band are rebuilt.  Returns (action, new parent count) or None, the count
+    being round(sqrt(N0)) (halves up)."""
+    r = math.sqrt(n_leaf)
+    p = max(1, int(math.floor(r + 0.5)))
+    if n_parent == 0:
+        return ("add_level", p) if n_leaf > 16 else None
+    if n_leaf <= 16:
+        return ("remove_level", 0)
+    if n_parent < r / 4 or n_parent > 4 * r:
+        return ("rebuild_level", p)
+    return None
+
+
+def apply_level_band(levels, logs, prm):
+    """Applies level_band_action after a pass: new parents are k-means (seed + 1, like the
+    build) of the leaf centroids, every leaf under its nearest final parent."""
+    n_leaf = levels[0].n_part
+    act = level_band_action(n_leaf, levels[1].n_part if len(levels) > 1 else 0)
+    if act is None:
+        return
+    kind, p = act
+    if kind == "remove_level":
+        levels.pop()
+    else:
+        C0 = levels[0].centroids
+        C1 = km.lloyd(C0, p, prm.level_iters, prm.seed + 1)
+        lv1, _ = km.partition_level(C0, np.arange(n_leaf, dtype=np.int64), C1)
+        if len(levels) == 1:
+            levels.append(lv1)
+        else:
+            levels[1] = lv1
+    while len(logs) < 2:
+        logs.append([])
+    logs[1].append((kind, p, float("nan"), float("nan"), True))
+
+
 def maintain(levels, hits, window, prm):
     """The bottom-up maintenance pass of Sec. 4 over every level; returns the action logs.
 
@@ -356,7 +404,10 @@ def maintain(levels, hits, window, prm):
     logs = []
     if len(levels) == 1:
         log, _ = maintain_level(levels[0], np.asarray(hits[0]) / window, prm, 0)
-        return [log]
+        logs = [log]
+        if prm.level_band:
+            apply_level_band(levels, logs, prm)
+        return logs
     n_leaf = levels[0].n_part
     parent_of = [0] * n_leaf
     for p, leaves in enumerate(levels[1].ids):
@@ -373,4 +424,6 @@ def maintain(levels, hits, window, prm):
                          [np.array(m, dtype=np.int64) for m in members])
     log1, _ = maintain_level(levels[1], np.asarray(hits[1]) / window, prm, 1)
     logs.append(log1)
+    if prm.level_band:
+        apply_level_band(levels, logs, prm)
     return logs

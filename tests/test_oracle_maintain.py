@@ -64,3 +64,39 @@ def test_pass_keeps_every_vector_and_lowers_modelled_cost():
     assert np.array_equal(got, ids)
     assert all(v.shape[0] == i.shape[0] for v, i in zip(levels[0].vectors, levels[0].ids))
     assert before > 0
+
+
+def test_level_band_thresholds():
+    f = maintenance.level_band_action
+    assert f(16, 0) is None                       # 16 = 4 sqrt(16): the leaves are a valid top
+    assert f(17, 0) == ("add_level", 4)           # round(sqrt(17)) = 4
+    assert f(1000, 0) == ("add_level", 32)
+    assert f(16, 4) == ("remove_level", 0)
+    assert f(100, 10) is None
+    assert f(100, 3) is None and f(100, 40) is None       # the band's ends, 2.5 and 40, are inside
+    assert f(100, 2) == ("rebuild_level", 10) and f(100, 41) == ("rebuild_level", 10)
+    assert f(30, 0) == ("add_level", 5) and f(42, 0) == ("add_level", 6)   # 5.48 -> 5, 6.48 -> 6
+    assert f(1, 0) is None
+
+
+def test_maintain_adds_a_parent_level_under_the_band():
+    """One level of 40 leaves: after the pass the index has round(sqrt(40)) = 6 parents, which are
+    the build's parents of the pass's leaf centroids, every leaf under exactly one."""
+    from oracle import kmeans
+    g = np.random.default_rng(0)
+    X = (g.standard_normal((4000, 8)) + 4 * np.repeat(g.standard_normal((40, 8)), 100, axis=0)).astype(np.float32)
+    ids = np.arange(4000, dtype=np.int64)
+    levels = kmeans.build_index(X, ids, 40, 0, iters=3, seed=5)
+    lam = maintenance.Latency([0, 1000], [5.0, 55.0])
+    prm = maintenance.MaintParams(lam, tau=1e9, level_band=True, level_iters=4, seed=5)   # no split or merge
+    logs = maintenance.maintain(levels, [np.ones(40)], 40, prm)
+    assert len(levels) == 2 and levels[1].n_part == 6
+    assert logs[1] == [("add_level", 6, logs[1][0][2], logs[1][0][3], True)]
+    want = kmeans.build_index(levels[0].centroids, np.arange(40, dtype=np.int64), 6, 0, iters=4, seed=6)[0]
+    np.testing.assert_array_equal(levels[1].centroids, want.centroids)
+    members = np.sort(np.concatenate(levels[1].ids))
+    assert np.array_equal(members, np.arange(40))
+    # and with 16 leaves the parent level goes away again
+    small = kmeans.build_index(X, ids, 16, 4, iters=3, seed=5)
+    logs = maintenance.maintain(small, [np.ones(16), np.ones(4)], 16, prm)
+    assert len(small) == 1 and logs[1][-1][0] == "remove_level"
