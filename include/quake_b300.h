@@ -266,6 +266,16 @@ qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, i
  *   s_min             partitions smaller than this are merge candidates.
  *   window            |W| in queries; 0 = the queries searched since the last
  *                     build, load or maintain.
+ *   level_band        1: after the levels' passes, keep the top level within
+ *                     sqrt(N0)/4 .. 4 sqrt(N0) centroids (N0 = leaves; the
+ *                     paper adds and removes levels, Sec. 3 and Sec. 4, with
+ *                     thresholds given only in its technical report): a
+ *                     single-level index with N0 > 16 gets a parent level, a
+ *                     two-level one with N0 <= 16 loses it, and a parent level
+ *                     outside the band is rebuilt.  New parents: k-means
+ *                     (level_iters Lloyd iterations, seed + 1 like the build)
+ *                     of the leaf centroids into round(sqrt(N0)).  0: off.
+ *   level_iters       Lloyd iterations of that k-means.
  */
 typedef struct {
   const double* lambda_sizes;
@@ -279,12 +289,16 @@ typedef struct {
   double tau_us;
   double alpha;
   int64_t window;
+  int32_t level_band;
+  int32_t level_iters;
 } qk_maint_params;
 
 /* One considered action: kind 0 = split, 1 = merge; partition is the index
  * at the start of the level's pass; estimate is Eq. 6 (split) or the uniform
  * redistribution estimate (merge); delta is Eq. 4 or Eq. 5 after the
- * tentative action (NaN if a split left a child empty). */
+ * tentative action (NaN if a split left a child empty).  With level_band,
+ * kind 2 = parent level added, 3 = removed, 4 = rebuilt (level 1, partition =
+ * the new parent count, committed = 1, estimate and delta NaN). */
 typedef struct {
   int32_t level;
   int32_t kind;

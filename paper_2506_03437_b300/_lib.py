@@ -49,6 +49,7 @@ class QkMaintParams(C.Structure):
         ("lambda_points", C.c_int32), ("refine_radius", C.c_int32), ("refine_iters", C.c_int32),
         ("split_iters", C.c_int32), ("s_min", C.c_int32), ("refine", C.c_int32),
         ("tau_us", C.c_double), ("alpha", C.c_double), ("window", C.c_int64),
+        ("level_band", C.c_int32), ("level_iters", C.c_int32),
     ]
 
 

@@ -505,6 +505,44 @@ static qk_status maintain_plan(qk_index* ix, const qk_maint_params* params, qk_m
     QK_CUDA(cudaMemcpyAsync(dpol.p, pol.data(), sizeof(int32_t) * pol.size(), cudaMemcpyHostToDevice, s));
   }
 
+  // the level band (off unless asked): keep the top level within
+  // sqrt(M0)/4 .. 4 sqrt(M0) centroids by adding, removing or rebuilding the
+  // parent level; new parents are the build's k-means (seed + 1) of the leaf
+  // centroids into round(sqrt(M0))
+  if (P.level_band) {
+    const double rt = std::sqrt((double)M0);
+    const int32_t np = std::max<int32_t>(1, (int32_t)std::floor(rt + 0.5));
+    const int32_t top = N1 > 0 ? M1 : 0;
+    int kind = -1;
+    if (top == 0) {
+      if (M0 > 16) kind = 2;
+    } else if (M0 <= 16) {
+      kind = 3;
+    } else if (top < rt / 4.0 || top > 4.0 * rt) {
+      kind = 4;
+    }
+    if (kind == 2 || kind == 4) {
+      QK_TRY(dC1.reserve(sizeof(float) * (size_t)np * d));
+      QK_TRY(dpol.reserve(sizeof(int32_t) * (size_t)M0));
+      QK_TRY(kmeans(dC0.as<float>(), M0, d, np, std::max(0, P.level_iters), ix->cfg.seed + 1, dC1.as<float>(),
+                    dpol.as<int32_t>(), s, nullptr));
+      M1 = np;
+    } else if (kind == 3) {
+      M1 = 0;
+    }
+    if (kind >= 0) {
+      qk_maint_action act;
+      std::memset(&act, 0, sizeof(act));
+      act.level = 1;
+      act.kind = kind;
+      act.partition = M1;
+      act.committed = 1;
+      act.estimate = NAN;
+      act.delta = NAN;
+      acts.push_back(act);
+    }
+  }
+
   tr.mark("parent_level");
   // the new structure, laid out from the labels into a fresh object (the live
   // arena is only read)
@@ -518,7 +556,7 @@ static qk_status maintain_plan(qk_index* ix, const qk_maint_params* params, qk_m
   QK_CUDA(cudaMemsetAsync(nst.p, 0, sizeof(int32_t), s));
   nx->status = nst.as<int32_t>();
   qk_status st = install(nx, ix->vec0, ix->ids0, ix->cap0, dC0.as<float>(), dlab.as<int32_t>(),
-                         N1 > 0 ? dC1.as<float>() : nullptr, N1 > 0 ? dpol.as<int32_t>() : nullptr, s, true);
+                         M1 > 0 ? dC1.as<float>() : nullptr, M1 > 0 ? dpol.as<int32_t>() : nullptr, s, true);
   nx->status = nullptr;
   if (st != QK_OK) {
     release_structure(nx);

@@ -112,7 +112,7 @@ class Index:
         return out
 
     def _maint(self, fn, lam_sizes, lam_us, tau_us, alpha, refine_radius, refine_iters, split_iters, s_min, refine,
-               window, stream):
+               window, stream, level_band=False, level_iters=10):
         ls = np.ascontiguousarray(lam_sizes, np.float64)
         lu = np.ascontiguousarray(lam_us, np.float64)
         p = L.QkMaintParams()
@@ -121,26 +121,29 @@ class Index:
         p.lambda_points = int(ls.shape[0])
         p.refine_radius, p.refine_iters, p.split_iters = refine_radius, refine_iters, split_iters
         p.s_min, p.refine, p.tau_us, p.alpha, p.window = s_min, int(bool(refine)), tau_us, alpha, window
+        p.level_band, p.level_iters = int(bool(level_band)), level_iters
         cap = 1 << 16
         log = (L.QkMaintAction * cap)()
         n = C.c_int32()
         L.check(fn(self._h, C.byref(p), log, cap, C.byref(n), L.stream_ptr(stream)))
-        return [dict(level=a.level, kind=("split", "merge")[a.kind], partition=a.partition,
+        kinds = ("split", "merge", "add_level", "remove_level", "rebuild_level")
+        return [dict(level=a.level, kind=kinds[a.kind], partition=a.partition,
                      committed=bool(a.committed), estimate=a.estimate, delta=a.delta)
                 for a in log[:min(n.value, cap)]]
 
     def maintain(self, lam_sizes, lam_us, tau_us=0.25, alpha=0.9, refine_radius=50, refine_iters=1,
-                 split_iters=10, s_min=0, refine=True, window=0, stream=None):
+                 split_iters=10, s_min=0, refine=True, window=0, stream=None, level_band=False, level_iters=10):
         """Runs the maintenance pass; returns the list of considered actions as dicts."""
         return self._maint(L.lib.qk_maintain, lam_sizes, lam_us, tau_us, alpha, refine_radius, refine_iters,
-                           split_iters, s_min, refine, window, stream)
+                           split_iters, s_min, refine, window, stream, level_band, level_iters)
 
     def maintain_prepare(self, lam_sizes, lam_us, tau_us=0.25, alpha=0.9, refine_radius=50, refine_iters=1,
-                         split_iters=10, s_min=0, refine=True, window=0, stream=None):
+                         split_iters=10, s_min=0, refine=True, window=0, stream=None, level_band=False,
+                         level_iters=10):
         """Plans the pass and builds its partitions aside (searches may run meanwhile);
         returns the action list.  maintain_commit() then installs it."""
         return self._maint(L.lib.qk_maintain_prepare, lam_sizes, lam_us, tau_us, alpha, refine_radius,
-                           refine_iters, split_iters, s_min, refine, window, stream)
+                           refine_iters, split_iters, s_min, refine, window, stream, level_band, level_iters)
 
     def maintain_commit(self, stream=None):
         L.check(L.lib.qk_maintain_commit(self._h, L.stream_ptr(stream)))

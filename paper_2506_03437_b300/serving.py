@@ -345,7 +345,7 @@ class NativeServer:
         self._keep = []
         if maintain_every:
             a = dict(tau_us=0.25, alpha=0.9, refine_radius=50, refine_iters=1, split_iters=10, s_min=0,
-                     refine=True, window=0)
+                     refine=True, window=0, level_band=False, level_iters=10)
             a.update(maint_args or {})
             ls = np.ascontiguousarray(a.pop("lam_sizes"), np.float64)
             lu = np.ascontiguousarray(a.pop("lam_us"), np.float64)
@@ -356,6 +356,7 @@ class NativeServer:
             p.refine_radius, p.refine_iters, p.split_iters = a["refine_radius"], a["refine_iters"], a["split_iters"]
             p.s_min, p.refine, p.tau_us = a["s_min"], int(bool(a["refine"])), a["tau_us"]
             p.alpha, p.window = a["alpha"], a["window"]
+            p.level_band, p.level_iters = int(bool(a["level_band"])), a["level_iters"]
             self._keep += [ls, lu, p]
             cfg.maint = C.pointer(p)
         self.cfg = cfg

@@ -5,7 +5,7 @@ import pytest
 
 from oracle import aps, kmeans, knn, maintenance
 
-from .parity import same_topk
+from .parity import compare_search, same_topk
 from .test_gpu_search import make_index
 from .test_oracle_maintain import example_lambda, example_level
 
@@ -156,3 +156,42 @@ def test_prepare_then_commit_equals_maintain_and_searches_run_meanwhile(I):
     with pytest.raises(L.QkError) as e:
         b.maintain_commit()
     assert e.value.status == L.ERR_STATE and b.info()["n_leaf"] == n_leaf
+
+
+def test_level_band_adds_and_removes_the_parent_level(I):
+    """Reading M9 on the GPU: one level of 40 leaves gains round(sqrt(40)) = 6 parents, the
+    oracle's (the build's k-means of the leaf centroids, seed + 1); 16 leaves lose them; and the
+    new two-level index searches like the oracle's."""
+    g = np.random.default_rng(0)
+    X = (g.standard_normal((4000, 8)) + 4 * np.repeat(g.standard_normal((40, 8)), 100, axis=0)).astype(np.float32)
+    X = np.concatenate([X, np.zeros((4000, 24), np.float32)], axis=1)   # d = 32
+    ids = np.arange(4000, dtype=np.int64)
+    levels = kmeans.build_index(X, ids, 40, 0, iters=3, seed=5)
+    ix = make_index(I, X, ids, levels, seed=5, f_M_leaf=0.5, f_M_parent=1.0)
+    Q = X[::97] + 0.01
+    ix.search(Q, 10, recall_target=0.0, nprobe=2)
+    lam = maintenance.Latency([0, 1000], [5.0, 55.0])
+    prm = maintenance.MaintParams(lam, tau=1e9, level_band=True, level_iters=4, seed=5)
+    want = maintenance.maintain(levels, [ix.hits(0)], Q.shape[0], prm)
+    got = ix.maintain([0, 1000], [5.0, 55.0], tau_us=1e9, level_band=True, level_iters=4, window=Q.shape[0])
+    assert [(a["level"], a["kind"], a["partition"]) for a in got if a["level"] == 1] == [(1, "add_level", 6)]
+    assert want[1][0][:2] == ("add_level", 6) and ix.info()["n_parent"] == 6
+    s1, c1, i1 = ix.export_level(1)
+    np.testing.assert_allclose(c1, levels[1].centroids, rtol=1e-5, atol=1e-5)
+    off = np.concatenate([[0], np.cumsum(s1)])
+    for p in range(6):
+        assert set(i1[off[p]:off[p + 1]].tolist()) == set(levels[1].ids[p].tolist())
+    r = ix.search(Q, 10, recall_target=0.9)
+    orc = aps.search(levels, Q, aps.Params(k=10, recall_target=0.9, f_M=(0.5, 1.0)))
+    n_ok, n_exc = compare_search(r, orc, 10)
+    assert n_exc <= 2
+    # 16 leaves: the parent level goes away again
+    small = kmeans.build_index(X, ids, 16, 4, iters=3, seed=5)
+    ix2 = make_index(I, X, ids, small, seed=5)
+    ix2.search(Q, 10, recall_target=0.0, nprobe=2)
+    got = ix2.maintain([0, 1000], [5.0, 55.0], tau_us=1e9, level_band=True, level_iters=4, window=Q.shape[0])
+    assert got[-1]["kind"] == "remove_level" and ix2.info()["n_parent"] == 0
+    r2 = ix2.search(Q, 10, recall_target=0.0, nprobe=16)
+    D, Ix = knn.knn(X, ids, Q, 10)
+    for j in range(Q.shape[0]):
+        assert same_topk(r2[0][j], r2[1][j], Ix[j], D[j])
