@@ -353,6 +353,31 @@ qk_status qk_maintain_prepare(qk_index* index, const qk_maint_params* params, qk
 qk_status qk_maintain_commit(qk_index* index, void* stream);
 
 /*
+ * Scan-latency profile lambda(s) of the cost model (Sec. 4, "Cost Model":
+ * lambda is measured by offline profiling; Sec. 9 profiles it again for other
+ * devices and for compressed partitions).  For every size sizes[i] (rows,
+ * positive, strictly increasing) a throwaway one-level index of P partitions
+ * of that many rows is made on the current device, in cfg's dimension, metric,
+ * storage format and rerank (n_leaf and n_parent are ignored).  Its rows are
+ * seeded synthetic data (cfg->seed): P = max(4 x SMs, rows of about 1 GiB),
+ * capped at 4096 partitions and 24 GiB of FP32 rows.  Q queries (4 x SMs ..
+ * 4096, fewer for large partitions)
+ * each sit on one partition's centre, and fixed-nprobe searches with k
+ * results are timed with CUDA events on `stream` (median of `reps` after one
+ * untimed search) at nprobe 1 and 9.
+ *   out_us[i] = (T(9) - T(1)) / (8 Q), in microseconds, floored at 0:
+ * the device time one more scanned partition of sizes[i] rows adds per
+ * (query, partition) item of a search batch.  The differences remove the
+ * launch, centroid scoring, result write and re-rank.  The table can be passed
+ * to qk_maintain as lambda_sizes / lambda_us; tau_us is then in the same unit.
+ * Synchronous.  Errors: QK_ERR_ARG for bad arguments or a size whose 9
+ * partitions exceed 24 GiB of FP32 rows; QK_ERR_OOM / QK_ERR_CUDA from the
+ * device.  The index of each size is freed before the next.
+ */
+qk_status qk_profile_scan(const qk_config* cfg, int32_t k, const int64_t* sizes, int32_t n_sizes, int32_t reps,
+                          double* out_us, void* stream);
+
+/*
  * Allocation-free Lloyd step.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory while they run
  * (a serving loop that cannot afford the device-wide synchronisation of

@@ -27,7 +27,7 @@ EXPORTS = [
     "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain", "qk_nearest_centroids",
     "qk_search_nprobe", "qk_batch_create", "qk_batch_destroy", "qk_batch_get_tiles", "qk_batch_set_tiles",
     "qk_batch_search", "qk_batch_capture", "qk_batch_replay", "qk_batch_autotune", "qk_batch_set_timing",
-    "qk_batch_stage_times", "qk_maintain_prepare", "qk_maintain_commit",
+    "qk_batch_stage_times", "qk_maintain_prepare", "qk_maintain_commit", "qk_profile_scan",
     "qk_server_config_default", "qk_server_create", "qk_server_destroy", "qk_server_submit_search",
     "qk_server_submit_insert", "qk_server_submit_delete", "qk_server_results", "qk_server_drain",
     "qk_server_get_stats",
@@ -111,6 +111,7 @@ def _load():
         "qk_maintain_prepare": (i32, [vp, C.POINTER(QkMaintParams), C.POINTER(QkMaintAction), i32,
                                       C.POINTER(C.c_int32), vp]),
         "qk_maintain_commit": (i32, [vp, vp]),
+        "qk_profile_scan": (i32, [vp, i32, vp, i32, i32, vp, vp]),
         "qk_server_config_default": (None, [C.POINTER(QkServerConfig)]),
         "qk_server_create": (i32, [vp, C.POINTER(QkServerConfig), C.POINTER(vp)]),
         "qk_server_destroy": (None, [vp]),

@@ -37,6 +37,21 @@ def config(d, metric=L.METRIC_L2, n_leaf=1000, n_parent=0, kmeans_iters=10, beta
     return c
 
 
+def profile_scan(d, sizes, k=10, reps=3, stream=None, **cfg):
+    """lambda(s) of the cost model measured on the current device (qk_profile_scan): microseconds
+    of device time one more scanned partition of s rows adds per (query, partition) item, for the
+    configuration's dimension, metric and storage.  Returns a float64 array beside `sizes`."""
+    return _profile(config(d, **cfg), sizes, k, reps, stream)
+
+
+def _profile(c, sizes, k, reps, stream):
+    sz = np.ascontiguousarray(sizes, dtype=np.int64)
+    out = np.empty(sz.shape[0], np.float64)
+    L.check(L.lib.qk_profile_scan(C.byref(c), int(k), L.ptr(sz), int(sz.shape[0]), int(reps), L.ptr(out),
+                                  L.stream_ptr(stream)))
+    return out
+
+
 class Index:
     """A Quake index on the current CUDA device (see include/quake_b300.h)."""
 
@@ -144,6 +159,10 @@ class Index:
         returns the action list.  maintain_commit() then installs it."""
         return self._maint(L.lib.qk_maintain_prepare, lam_sizes, lam_us, tau_us, alpha, refine_radius,
                            refine_iters, split_iters, s_min, refine, window, stream, level_band, level_iters)
+
+    def profile_scan(self, sizes, k=10, reps=3, stream=None):
+        """lambda(s) for this index's dimension, metric and storage (see profile_scan)."""
+        return _profile(self.cfg, sizes, k, reps, stream)
 
     def maintain_commit(self, stream=None):
         L.check(L.lib.qk_maintain_commit(self._h, L.stream_ptr(stream)))

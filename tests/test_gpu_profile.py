@@ -1,0 +1,83 @@
+"""lambda(s) measured on the GPU (Sec. 4, "Cost Model": the scan latency comes from offline
+profiling; Sec. 9: profile it again per storage format).  A timing has no oracle value, so the
+tests check what the measurement must satisfy, and that the measured table drives the
+maintenance pass exactly as the oracle's cost model does with the same table."""
+
+import numpy as np
+import pytest
+
+from oracle import kmeans, maintenance
+
+from .test_gpu_maintain import scenario
+from .test_gpu_search import make_index
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [256, 4096, 16384, 65536]
+
+
+@pytest.fixture(scope="module")
+def I():
+    from paper_2506_03437_b300 import index
+    return index
+
+
+@pytest.fixture(scope="module")
+def lam(I):
+    from paper_2506_03437_b300 import _lib as L
+    return {st: I.profile_scan(128, SIZES, k=10, reps=3, storage=code)
+            for st, code in (("f32", L.STORE_F32), ("bf16", L.STORE_BF16), ("fp8", L.STORE_FP8))}
+
+
+def test_lambda_grows_with_the_rows_scanned(lam):
+    f = lam["f32"]
+    print("lambda(s) us, d = 128:", {k: v.round(4).tolist() for k, v in lam.items()})
+    assert np.all(np.isfinite(f)) and np.all(f > 0)
+    assert f[1] > f[0] and f[2] > f[1]
+    # large partitions stream from HBM: four times the rows take about four times as long
+    assert 2.0 < f[3] / f[2] < 8.0
+    # and no faster than HBM allows (measured copy peak about 6.3-6.5 TB/s; 20% margin)
+    bytes_per_item = SIZES[3] * 128 * 4
+    assert bytes_per_item / (f[3] * 1e-6) < 1.2 * 6.5e12
+
+
+def test_low_precision_storage_scans_faster(lam):
+    assert lam["bf16"][3] < lam["f32"][3]
+    assert lam["fp8"][3] < lam["f32"][3]
+
+
+def test_profiled_table_drives_maintenance_like_the_oracle(I):
+    """The measured lambda enters Eq. 1-6 unchanged: the pass on the GPU and the oracle's pass
+    with the same table take the same actions, estimates and deltas."""
+    X, ids, Q = scenario()
+    sizes = np.array([16, 64, 256, 1024, 4096], np.int64)
+    us = I.profile_scan(X.shape[1], sizes, k=10, reps=3)
+    assert np.all(np.isfinite(us)) and us[-1] > us[0]
+    levels = kmeans.build_index(X, ids, 24, 0, iters=5, seed=11)
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.25, seed=1234)
+    ix.search(Q, 10, recall_target=0.0, nprobe=2)
+    tau = 0.01 * float(us[3])
+    prm = maintenance.MaintParams(maintenance.Latency(sizes.astype(np.float64), us), tau=tau, alpha=0.9,
+                                  refine_radius=4, s_min=120, split_iters=8, seed=1234)
+    logs = maintenance.maintain(levels, [ix.hits(0)], Q.shape[0], prm)
+    got = ix.maintain(sizes.astype(np.float64), us, tau_us=tau, alpha=0.9, refine_radius=4, s_min=120,
+                      split_iters=8, window=Q.shape[0])
+    want = [(0, k, j, ok, e, dl) for k, j, e, dl, ok in logs[0]]
+    assert len(want) > 0 and len(got) == len(want)
+    for a, (lv, k, j, ok, e, dl) in zip(got, want):
+        assert (a["level"], a["kind"], a["partition"], a["committed"]) == (lv, k, j, ok)
+        assert abs(a["estimate"] - e) <= 1e-6 * max(abs(e), float(us[-1]))
+        if dl is not None:
+            assert abs(a["delta"] - dl) <= 1e-6 * max(abs(dl), float(us[-1]))
+    assert ix.export_level(0)[0].tolist() == levels[0].sizes().tolist()
+
+
+def test_profile_rejects_bad_arguments(I):
+    from paper_2506_03437_b300 import _lib as L
+    for sizes, k in (([64, 64], 10), ([0, 8], 10), ([64], 0)):
+        with pytest.raises(L.QkError) as e:
+            I.profile_scan(32, sizes, k=k)
+        assert e.value.status == L.ERR_ARG
+    with pytest.raises(L.QkError) as e:    # 9 partitions of this size exceed 24 GiB
+        I.profile_scan(1024, [1 << 21])
+    assert e.value.status == L.ERR_ARG
