@@ -308,7 +308,7 @@ def run_ours(args):
             "clocks": clk.summary(),
         }
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(X, ids, Q, tau, args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline(X, ids, Q, tau, args.cpu_seconds, workers=cpu_workers(args))
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -334,20 +334,38 @@ def oracle_index(X, ids):
     return kmeans.build_index(X, ids, N_LEAF, N_PARENT, iters=ORACLE_BUILD_ITERS, seed=SEED)
 
 
-def cpu_baseline(X, ids, Q, tau, seconds, levels=None):
-    """The oracle's APS search timed on a bounded sample of the same queries (1 host thread)."""
+def cpu_workers(args):
+    if args.cpu_workers >= 0:
+        return args.cpu_workers
+    from oracle import pool
+    return min(64, pool.available_cores())
+
+
+def cpu_baseline(X, ids, Q, tau, seconds, levels=None, workers=0):
+    """The oracle's APS search timed on a bounded sample of the same queries: 1 host thread, and
+    with workers > 1 also over that many processes (the queries split between them)."""
     from oracle import aps
     if levels is None:
         levels = oracle_index(X, ids)
+    from threadpoolctl import threadpool_limits
     prm = aps.Params(k=K, recall_target=tau, f_M=(F_M_LEAF, F_M_PARENT))
-    done, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds and done < Q.shape[0]:
-        aps.search(levels, Q[done:done + 1], prm)
-        done += 1
-    el = time.perf_counter() - t0
-    return {"value": round(done / el, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": (f"first {done} of {Q.shape[0]} queries, FP64 numpy APS search on 1 thread, over an index "
-                       f"the oracle built itself ({ORACLE_BUILD_ITERS} Lloyd iterations)")}
+    done = 0
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < seconds and done < Q.shape[0]:
+            aps.search(levels, Q[done:done + 1], prm)
+            done += 1
+        el = time.perf_counter() - t0
+    out = {"value": round(done / el, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+           "sample": (f"first {done} of {Q.shape[0]} queries, FP64 numpy APS search on 1 thread, over an index "
+                      f"the oracle built itself ({ORACLE_BUILD_ITERS} Lloyd iterations)")}
+    if workers > 1:
+        from oracle import pool
+        rate, n_done = pool.search_rate(levels, Q, prm, seconds, workers)
+        out["parallel"] = {"value": round(rate, 3), "unit": "queries/s", "cores": workers, "kind": "oracle",
+                           "sample": (f"{n_done} of {Q.shape[0]} queries split over {workers} spawned processes "
+                                      f"(one BLAS thread each), at most {seconds:g} s each")}
+    return out
 
 
 def run_reference(args):
@@ -360,13 +378,15 @@ def run_reference(args):
     from oracle import aps
     prm = aps.Params(k=K, recall_target=0.9, f_M=(F_M_LEAF, F_M_PARENT))
     per_step = max(1, args.ref_queries)
-    for w in range(args.warmup):
-        aps.search(levels, Q[:1], prm)
-    t0 = time.perf_counter()
-    for s in range(args.steps):
-        lo = (s * per_step) % NQ
-        aps.search(levels, Q[lo:lo + per_step], prm)
-    el = time.perf_counter() - t0
+    from threadpoolctl import threadpool_limits
+    with threadpool_limits(1):
+        for w in range(args.warmup):
+            aps.search(levels, Q[:1], prm)
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            lo = (s * per_step) % NQ
+            aps.search(levels, Q[lo:lo + per_step], prm)
+        el = time.perf_counter() - t0
     qps = per_step * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": round(qps, 3), "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
@@ -580,11 +600,14 @@ def batch_cpu_baseline(X, ids, lab, sizes, C, Q, nprobe, k, seconds):
     off = np.concatenate([[0], np.cumsum(sizes)])   # rows are grouped by partition already
     level = kmeans.Level(C, [X[off[j]:off[j + 1]] for j in range(len(sizes))],
                          [ids[off[j]:off[j + 1]] for j in range(len(sizes))])
-    done, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds and done < Q.shape[0]:
-        aps.ivf_search(level, Q[done:done + 1], k, nprobe[done:done + 1])
-        done += 1
-    el = time.perf_counter() - t0
+    from threadpoolctl import threadpool_limits
+    done = 0
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < seconds and done < Q.shape[0]:
+            aps.ivf_search(level, Q[done:done + 1], k, nprobe[done:done + 1])
+            done += 1
+        el = time.perf_counter() - t0
     return {"value": round(done / el, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
             "sample": f"first {done} of {Q.shape[0]} queries, FP64 numpy per-query IVF on 1 thread"}
 
@@ -882,6 +905,8 @@ def main():
     ap.add_argument("--tiles", default="", help="queries_per_warp,tile_rows,chunk_rows for the batching "
                                                  "workload instead of the autotuner's choice")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-workers", type=int, default=-1,
+                    help="processes of the parallel oracle leg (-1: the host's cores, at most 64; 0 or 1: skip)")
     ap.add_argument("--ref-queries", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fixed", action="store_true", help="skip the fixed-nprobe comparison of the APS workload")

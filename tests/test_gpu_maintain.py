@@ -195,3 +195,30 @@ def test_level_band_adds_and_removes_the_parent_level(I):
     D, Ix = knn.knn(X, ids, Q, 10)
     for j in range(Q.shape[0]):
         assert same_topk(r2[0][j], r2[1][j], Ix[j], D[j])
+
+
+def test_level_band_rebuilds_parents_outside_the_band(I):
+    """Reading M9: 40 leaves under 1 parent (below sqrt(40)/4) are regrouped under round(sqrt(40)) = 6
+    new parents, the oracle's."""
+    g = np.random.default_rng(1)
+    X = (g.standard_normal((4000, 32)) + 4 * np.repeat(g.standard_normal((40, 32)), 100, axis=0)).astype(np.float32)
+    ids = np.arange(4000, dtype=np.int64)
+    levels = kmeans.build_index(X, ids, 40, 1, iters=3, seed=7)
+    ix = make_index(I, X, ids, levels, seed=7, f_M_leaf=0.5, f_M_parent=1.0)
+    Q = X[::50] + 0.01
+    ix.search(Q, 10, recall_target=0.0, nprobe=2)
+    prm = maintenance.MaintParams(maintenance.Latency([0, 1000], [5.0, 55.0]), tau=1e9, level_band=True,
+                                  level_iters=4, seed=7)
+    want = maintenance.maintain(levels, [ix.hits(0), ix.hits(1)], Q.shape[0], prm)
+    got = ix.maintain([0, 1000], [5.0, 55.0], tau_us=1e9, level_band=True, level_iters=4, window=Q.shape[0])
+    assert [(a["kind"], a["partition"]) for a in got if a["level"] == 1] == [("rebuild_level", 6)]
+    assert want[1][-1][:2] == ("rebuild_level", 6) and ix.info()["n_parent"] == 6
+    s1, c1, i1 = ix.export_level(1)
+    np.testing.assert_allclose(c1, levels[1].centroids, rtol=1e-5, atol=1e-5)
+    off = np.concatenate([[0], np.cumsum(s1)])
+    for p in range(6):
+        assert set(i1[off[p]:off[p + 1]].tolist()) == set(levels[1].ids[p].tolist())
+    r = ix.search(Q, 10, recall_target=0.9)
+    orc = aps.search(levels, Q, aps.Params(k=10, recall_target=0.9, f_M=(0.5, 1.0)))
+    n_ok, n_exc = compare_search(r, orc, 10)
+    assert n_exc <= 2
