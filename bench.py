@@ -27,7 +27,23 @@ import sys
 import threading
 import time
 
-import numpy as np
+
+def _impl_arg(argv):
+    for i, a in enumerate(argv):
+        if a == "--impl" and i + 1 < len(argv):
+            return argv[i + 1]
+        if a.startswith("--impl="):
+            return a.split("=", 1)[1]
+    return None
+
+
+if _impl_arg(sys.argv) == "reference":
+    # the reference arm times the oracle in this process on one BLAS thread ("cores": 1); the
+    # variables must be set before numpy loads its BLAS
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -347,20 +363,13 @@ def cpu_baseline(X, ids, Q, tau, seconds, levels=None, workers=0):
     from oracle import aps
     if levels is None:
         levels = oracle_index(X, ids)
-    from threadpoolctl import threadpool_limits
+    from oracle import pool
     prm = aps.Params(k=K, recall_target=tau, f_M=(F_M_LEAF, F_M_PARENT))
-    done = 0
-    with threadpool_limits(1):
-        t0 = time.perf_counter()
-        while time.perf_counter() - t0 < seconds and done < Q.shape[0]:
-            aps.search(levels, Q[done:done + 1], prm)
-            done += 1
-        el = time.perf_counter() - t0
-    out = {"value": round(done / el, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
-           "sample": (f"first {done} of {Q.shape[0]} queries, FP64 numpy APS search on 1 thread, over an index "
-                      f"the oracle built itself ({ORACLE_BUILD_ITERS} Lloyd iterations)")}
+    rate1, done = pool.search_rate(levels, Q, prm, seconds, 1)
+    out = {"value": round(rate1, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+           "sample": (f"first {done} of {Q.shape[0]} queries, FP64 numpy APS search in one spawned process on one "
+                      f"BLAS thread, over an index the oracle built itself ({ORACLE_BUILD_ITERS} Lloyd iterations)")}
     if workers > 1:
-        from oracle import pool
         rate, n_done = pool.search_rate(levels, Q, prm, seconds, workers)
         out["parallel"] = {"value": round(rate, 3), "unit": "queries/s", "cores": workers, "kind": "oracle",
                            "sample": (f"{n_done} of {Q.shape[0]} queries split over {workers} spawned processes "
@@ -378,15 +387,13 @@ def run_reference(args):
     from oracle import aps
     prm = aps.Params(k=K, recall_target=0.9, f_M=(F_M_LEAF, F_M_PARENT))
     per_step = max(1, args.ref_queries)
-    from threadpoolctl import threadpool_limits
-    with threadpool_limits(1):
-        for w in range(args.warmup):
-            aps.search(levels, Q[:1], prm)
-        t0 = time.perf_counter()
-        for s in range(args.steps):
-            lo = (s * per_step) % NQ
-            aps.search(levels, Q[lo:lo + per_step], prm)
-        el = time.perf_counter() - t0
+    for w in range(args.warmup):
+        aps.search(levels, Q[:1], prm)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        lo = (s * per_step) % NQ
+        aps.search(levels, Q[lo:lo + per_step], prm)
+    el = time.perf_counter() - t0
     qps = per_step * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": round(qps, 3), "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
@@ -600,16 +607,11 @@ def batch_cpu_baseline(X, ids, lab, sizes, C, Q, nprobe, k, seconds):
     off = np.concatenate([[0], np.cumsum(sizes)])   # rows are grouped by partition already
     level = kmeans.Level(C, [X[off[j]:off[j + 1]] for j in range(len(sizes))],
                          [ids[off[j]:off[j + 1]] for j in range(len(sizes))])
-    from threadpoolctl import threadpool_limits
-    done = 0
-    with threadpool_limits(1):
-        t0 = time.perf_counter()
-        while time.perf_counter() - t0 < seconds and done < Q.shape[0]:
-            aps.ivf_search(level, Q[done:done + 1], k, nprobe[done:done + 1])
-            done += 1
-        el = time.perf_counter() - t0
-    return {"value": round(done / el, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of {Q.shape[0]} queries, FP64 numpy per-query IVF on 1 thread"}
+    from oracle import pool
+    rate, done = pool.ivf_rate(level, Q, k, nprobe, seconds, 1)
+    return {"value": round(rate, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": (f"first {done} of {Q.shape[0]} queries, FP64 numpy per-query IVF in one spawned process on "
+                       "one BLAS thread")}
 
 
 def run_precision(args):
