@@ -146,7 +146,11 @@ qk_status qk_load(qk_index* index, const float* x, const int64_t* ids, int64_t n
  * Outputs (nq x k, row-major): out_ids, out_dist.  Optional (NULL to skip):
  * out_nprobe[nq] leaf partitions scanned, out_recall[nq] the final estimate r
  * (NaN in fixed-nprobe mode).  Per-partition access counts are accumulated in
- * the index (see qk_get_hits).  NaN in q -> QK_ERR_ARG.  With low-precision
+ * the index (see qk_get_hits).  A query with a NaN or infinite element (or a
+ * squared norm beyond FP32) is refused by the kernel: its ids are -1, its
+ * distances and recall NaN, its nprobe 0, the other queries are answered, and
+ * the call (or, with device buffers, the next qk_check) returns QK_ERR_ARG.
+ * With low-precision
  * storage the leaf scan keeps rerank * k candidates by their approximate
  * distance (rho is the k-th of them) and the k returned are re-ranked with
  * exact FP32 distances.  Inner product: rho is ||q - x_k|| of the k-th result.

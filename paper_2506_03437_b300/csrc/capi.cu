@@ -763,13 +763,6 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   const bool np_dev = !out_nprobe || is_device_ptr(out_nprobe);
   const bool rc_dev = !out_recall || is_device_ptr(out_recall);
   const bool all_dev = q_dev && ids_dev && dist_dev && np_dev && rc_dev;
-  if (!q_dev) {
-    for (int64_t i = 0; i < nq * d; ++i)
-      if (std::isnan(q[i])) {
-        set_error("NaN in queries");
-        return QK_ERR_ARG;
-      }
-  }
   // staging for host buffers
   const size_t bq = sizeof(float) * (size_t)nq * d;
   const size_t bi = sizeof(int64_t) * (size_t)nq * k, bd = sizeof(float) * (size_t)nq * k;

@@ -819,6 +819,22 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
       for (int j = b.lane; j < B::D; j += 32) qn = fmaf(b.sq[j], b.sq[j], qn);
       b.qn = warp_sum_f(qn);
     }
+    // A query with a NaN or infinite element, or whose squared norm exceeds
+    // FP32, is refused before any comparison sees it: ids -1, distances NaN,
+    // and the status records a bad argument (the other queries are answered).
+    if (__syncthreads_or(!(b.qn < INFINITY))) {
+      if (threadIdx.x == 0) b.report(DEV_BAD_ARG, 1, 0, 0);
+      for (int i = threadIdx.x; i < args.kq; i += kThreads) {
+        args.out_dist[qi * args.kq + i] = NAN;
+        args.out_ids[qi * args.kq + i] = -1;
+      }
+      if (threadIdx.x == 0) {
+        if (args.out_nprobe) args.out_nprobe[qi] = 0;
+        if (args.out_recall) args.out_recall[qi] = NAN;
+      }
+      __syncthreads();
+      continue;
+    }
     // The tree is searched in the Euclidean geometry it was built in: the top
     // partition and the upper levels rank centroids by squared L2; only the
     // base rows use the index's metric (for inner product, -<q, x>).

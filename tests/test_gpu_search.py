@@ -188,6 +188,17 @@ def test_invalid_arguments_are_rejected(I):
     with pytest.raises(L.QkError) as e:
         ix.search(q, 5)
     assert e.value.status == L.ERR_ARG
+    # device buffers: the kernel refuses the bad query, answers the other, and qk_check reports it
+    import torch
+    qd = torch.from_numpy(X[:2].copy()).cuda()
+    qd[1, 5] = float("inf")
+    gi, gd, gn, gr = ix.search(qd, 5, recall_target=0.0, nprobe=4)
+    with pytest.raises(L.QkError) as e:
+        ix.check()
+    assert e.value.status == L.ERR_ARG
+    assert int(gi[0, 0]) == 0 and float(gd[0, 0]) == 0.0 and int(gn[0]) == 4
+    assert bool((gi[1] == -1).all()) and bool(torch.isnan(gd[1]).all()) and int(gn[1]) == 0
+    ix.check()   # the status was cleared
     with pytest.raises(L.QkError):
         ix.search(np.zeros((2, 64), np.float32), 0)
     with pytest.raises(L.QkError) as e:
