@@ -435,8 +435,10 @@ qk_status qk_kmeans_step_noalloc(const float* x, int64_t n, int32_t d, const flo
  *
  * Conventions: every buffer is 16-byte aligned device memory; calls are
  * stream-ordered and return before the GPU finishes; device-side errors
- * (an nprobe outside [1, max_nprobe], a bounded wait that expired) are
- * recorded in the index's status word and reported by qk_check.  A plan
+ * (an nprobe outside [1, max_nprobe], a query with a NaN or infinite
+ * element, a bounded wait that expired) are recorded in the index's status
+ * word and reported by qk_check; a refused query gets (id -1, +inf) rows and
+ * the others are answered.  A plan
  * follows the index's inserts, deletes and maintenance by itself on the next
  * qk_batch_search; a captured graph does not (qk_batch_replay then returns
  * QK_ERR_STATE: capture again).  Calls on one plan must not overlap.  L2

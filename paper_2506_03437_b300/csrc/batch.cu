@@ -554,9 +554,18 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(SelArgs a) {
       const float qnorm = sqrtf(qn), cmax = sqrtf(__uint_as_float(*a.cmax2));
       const float s = qnorm + cmax;
       s_f[0] = 0.0078125f * qnorm * cmax + 6.103515625e-05f * s * s;   // 2^-7 and 2^-14
+      s_int[3] = !(qn < INFINITY);
     }
   }
   __syncthreads();
+  if (s_int[3]) {   // a NaN or infinite element, or a norm beyond FP32: refused like a bad nprobe
+    if (tid == 0) {
+      a.nsel[q] = 0;
+      a.qslots[q] = 0;
+      report_once(a.status, a.diag, DEV_BAD_ARG, -5, q, 0);
+    }
+    return;
+  }
   const float E = s_f[0];
   // with every centroid wanted, or when the bound lets too many through, the
   // exact distances of all centroids replace the approximate row

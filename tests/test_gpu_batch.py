@@ -199,6 +199,21 @@ def test_invalid_arguments(I, small):
         ix.check()
     assert e.value.status == L.ERR_ARG
     assert int(gi[1, 0]) == -1 and int(gi[3, 0]) == -1 and int(gi[0, 0]) >= 0
+    # a query with a NaN or infinite element is refused the same way; the others are unchanged
+    four = torch.full((8,), 4, dtype=torch.int32, device="cuda")
+    ref_i, ref_d = plan.search(q, four)
+    ix.check()
+    ref_i, ref_d = ref_i.clone(), ref_d.clone()
+    qb = q.clone()
+    qb[2, 7] = float("nan")
+    qb[5, 0] = float("inf")
+    gi, gd = plan.search(qb, four)
+    with pytest.raises(L.QkError) as e:
+        ix.check()
+    assert e.value.status == L.ERR_ARG
+    assert bool((gi[2] == -1).all()) and bool((gi[5] == -1).all())
+    for j in (0, 1, 3, 4, 6, 7):
+        assert torch.equal(gi[j], ref_i[j]) and torch.equal(gd[j], ref_d[j])
     ixi = I.Index(64, n_leaf=8, metric=L.METRIC_IP)
     ixi.build(X[:2000], ids[:2000])
     with pytest.raises(L.QkError):
