@@ -46,7 +46,8 @@ typedef enum {
   QK_ERR_DUP_ID = 5,      /* insert of an id that is already present; nothing applied */
   QK_ERR_STATE = 6,       /* call not valid in the index's current state (e.g. search before build) */
   QK_ERR_UNSUPPORTED = 7, /* configuration not supported by this build */
-  QK_ERR_INTERNAL = 8     /* a kernel's own consistency check failed; results are not valid */
+  QK_ERR_INTERNAL = 8,    /* a kernel's own consistency check failed; results are not valid */
+  QK_ERR_IO = 9           /* a checkpoint file could not be written or read, or is not valid */
 } qk_status;
 
 enum { QK_METRIC_L2 = 0, QK_METRIC_IP = 1 };
@@ -216,6 +217,27 @@ qk_status qk_export_quantized(const qk_index* index, uint8_t* codes, float* scal
 /* Copies the access counts of `level` (one int64 per partition, summed over
  * searches since the last reset) to a host array; reset != 0 zeroes them. */
 qk_status qk_get_hits(qk_index* index, int32_t level, int64_t* hits, int32_t reset);
+
+/*
+ * Checkpoint and resume.  The paper has no counterpart (its indexes live in
+ * memory).  qk_save writes one file (host byte order) with everything a
+ * search or maintenance pass reads: the configuration with the current
+ * partition counts, the partitions of both levels (sizes, centroids, ids and
+ * FP32 rows grouped by partition; with BF16 / FP8 storage also the
+ * low-precision rows and FP8 scales as they are, since rows inserted after the
+ * build keep the scale they were quantized with), the access counters of both
+ * levels and the statistics window, and a 64-bit FNV-1a checksum.  The index
+ * is only read; it must not be modified meanwhile.
+ * qk_restore creates an index on the current device from such a file: it
+ * searches, updates and maintains exactly as the saved one.  Partition
+ * numbers and contents are kept; the arena layout is fresh.  cfg_out
+ * (optional) receives the configuration.  Errors: QK_ERR_ARG (null
+ * arguments), QK_ERR_STATE (qk_save of an empty index), QK_ERR_IO (the file
+ * cannot be opened, written or read, is not a checkpoint, is truncated, fails
+ * the checksum or is inconsistent), QK_ERR_OOM / QK_ERR_CUDA.  Synchronous.
+ */
+qk_status qk_save(qk_index* index, const char* path);
+qk_status qk_restore(const char* path, qk_config* cfg_out, qk_index** out);
 
 /*
  * Exact cap volume fraction u = 1/2 I_x((d+1)/2, 1/2), x = 1 - (t/rho)^2 for

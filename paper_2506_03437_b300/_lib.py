@@ -12,13 +12,13 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("QK_LIBRARY") or os.path.join(HERE, "libquake_b300.so")
 
-OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DUP_ID, ERR_STATE, ERR_UNSUPPORTED, ERR_INTERNAL = range(9)
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DUP_ID, ERR_STATE, ERR_UNSUPPORTED, ERR_INTERNAL, ERR_IO = range(10)
 METRIC_L2, METRIC_IP = 0, 1
 BETA_TABLE, BETA_EXACT = 0, 1
 STORE_F32, STORE_BF16, STORE_FP8 = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT",
-                5: "ERR_DUP_ID", 6: "ERR_STATE", 7: "ERR_UNSUPPORTED", 8: "ERR_INTERNAL"}
+                5: "ERR_DUP_ID", 6: "ERR_STATE", 7: "ERR_UNSUPPORTED", 8: "ERR_INTERNAL", 9: "ERR_IO"}
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = [
@@ -27,7 +27,7 @@ EXPORTS = [
     "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain", "qk_nearest_centroids",
     "qk_search_nprobe", "qk_batch_create", "qk_batch_destroy", "qk_batch_get_tiles", "qk_batch_set_tiles",
     "qk_batch_search", "qk_batch_capture", "qk_batch_replay", "qk_batch_autotune", "qk_batch_set_timing",
-    "qk_batch_stage_times", "qk_maintain_prepare", "qk_maintain_commit", "qk_profile_scan",
+    "qk_batch_stage_times", "qk_maintain_prepare", "qk_maintain_commit", "qk_profile_scan", "qk_save", "qk_restore",
     "qk_server_config_default", "qk_server_create", "qk_server_destroy", "qk_server_submit_search",
     "qk_server_submit_insert", "qk_server_submit_delete", "qk_server_results", "qk_server_drain",
     "qk_server_get_stats",
@@ -112,6 +112,8 @@ def _load():
                                       C.POINTER(C.c_int32), vp]),
         "qk_maintain_commit": (i32, [vp, vp]),
         "qk_profile_scan": (i32, [vp, i32, vp, i32, i32, vp, vp]),
+        "qk_save": (i32, [vp, C.c_char_p]),
+        "qk_restore": (i32, [C.c_char_p, vp, vp]),
         "qk_server_config_default": (None, [C.POINTER(QkServerConfig)]),
         "qk_server_create": (i32, [vp, C.POINTER(QkServerConfig), C.POINTER(vp)]),
         "qk_server_destroy": (None, [vp]),

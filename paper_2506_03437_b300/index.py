@@ -7,6 +7,7 @@ arrays for host inputs.
 """
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -159,6 +160,20 @@ class Index:
         returns the action list.  maintain_commit() then installs it."""
         return self._maint(L.lib.qk_maintain_prepare, lam_sizes, lam_us, tau_us, alpha, refine_radius,
                            refine_iters, split_iters, s_min, refine, window, stream, level_band, level_iters)
+
+    def save(self, path):
+        """Writes a checkpoint of the index to `path` (qk_save)."""
+        L.check(L.lib.qk_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def restore(cls, path):
+        """An index on the current device from a checkpoint written by save() (qk_restore)."""
+        cfg = L.QkConfig()
+        h = C.c_void_p()
+        L.check(L.lib.qk_restore(os.fsencode(path), C.byref(cfg), C.byref(h)))
+        ix = cls.__new__(cls)
+        ix.cfg, ix._h = cfg, h
+        return ix
 
     def profile_scan(self, sizes, k=10, reps=3, stream=None):
         """lambda(s) for this index's dimension, metric and storage (see profile_scan)."""
