@@ -42,6 +42,7 @@
 
 #include "common.cuh"
 #include "index.cuh"
+#include "trace.h"
 
 namespace qk {
 
@@ -1057,7 +1058,10 @@ qk_status enqueue(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe
   if (capturing && !(b->scan_tiles.queries_per_warp == t.queries_per_warp && b->scan_tiles.tile_rows == t.tile_rows))
     b->scan_blocks = 0;
   const bool timing = b->timing && !capturing;
+  static const char* const kStage[6] = {"start", "scoring", "selection", "grouping", "scan", "merge"};
+  Trace tr("batch");
   auto mark = [&](int i) -> qk_status {
+    if (i > 0) tr.mark(kStage[i]);
     if (timing) QK_CUDA(cudaEventRecord(b->ev[i], s));
     return QK_OK;
   };

@@ -756,6 +756,7 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
     return QK_ERR_ARG;
   }
   if (nq == 0) return QK_OK;
+  Trace tr("search");
   cudaStream_t s = (cudaStream_t)stream;
   const int d = ix->cfg.d;
   const bool q_dev = is_device_ptr(q);
@@ -833,13 +834,16 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   a.kcap = std::max({a.k0, a.k1, a.M_root});
   a.mcap = std::max({a.M_root, a.k1, 1});
   QK_TRY(launch_search(a, s));
+  tr.mark("launch");
   ix->queries_seen += nq;
   if (!all_dev) {
     if (!ids_dev) QK_CUDA(cudaMemcpyAsync(out_ids, dids, bi, cudaMemcpyDeviceToHost, s));
     if (!dist_dev) QK_CUDA(cudaMemcpyAsync(out_dist, ddist, bd, cudaMemcpyDeviceToHost, s));
     if (!np_dev) QK_CUDA(cudaMemcpyAsync(out_nprobe, dnp, bn, cudaMemcpyDeviceToHost, s));
     if (!rc_dev) QK_CUDA(cudaMemcpyAsync(out_recall, drc, br, cudaMemcpyDeviceToHost, s));
-    return read_device_status(ix, s);
+    const qk_status st = read_device_status(ix, s);
+    tr.mark("results");
+    return st;
   }
   return QK_OK;
 }
