@@ -45,7 +45,7 @@ typedef enum {
   QK_ERR_TIMEOUT = 4,     /* a bounded device wait expired; results are not valid */
   QK_ERR_DUP_ID = 5,      /* insert of an id that is already present; nothing applied */
   QK_ERR_STATE = 6,       /* call not valid in the index's current state (e.g. search before build) */
-  QK_ERR_UNSUPPORTED = 7, /* configuration not supported by this build */
+  QK_ERR_UNSUPPORTED = 7, /* configuration not supported by this library */
   QK_ERR_INTERNAL = 8,    /* a kernel's own consistency check failed; results are not valid */
   QK_ERR_IO = 9           /* a checkpoint file could not be written or read, or is not valid */
 } qk_status;

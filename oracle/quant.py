@@ -1,7 +1,8 @@
 """Low-precision storage formats (oracle; test infrastructure only).
 
-The benchmark spec stores base vectors in BF16, or in FP8 E4M3 with a scale per
-partition, scans them with FP32 accumulation and re-ranks an oversized
+The index can store base vectors in BF16, or in FP8 E4M3 with a scale per
+partition (a compressed form of the partitions the paper names as future
+work, Sec. 9), scan them with FP32 accumulation and re-rank an oversized
 candidate list exactly in FP32.  This module restates the two formats from
 their definitions, by brute force:
 
