@@ -20,6 +20,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <unordered_map>
 #include <vector>
 
@@ -92,7 +93,7 @@ qk_status io_error(const std::string& what) {
 
 using namespace qk;
 
-extern "C" qk_status qk_save(qk_index* ix, const char* path) {
+static qk_status save_impl(qk_index* ix, const char* path) {
   if (!ix || !path) {
     set_error("qk_save: null argument");
     return QK_ERR_ARG;
@@ -155,7 +156,7 @@ extern "C" qk_status qk_save(qk_index* ix, const char* path) {
   return QK_OK;
 }
 
-extern "C" qk_status qk_restore(const char* path, qk_config* cfg_out, qk_index** out) {
+static qk_status restore_impl(const char* path, qk_config* cfg_out, qk_index** out) {
   if (!path || !out) {
     set_error("qk_restore: null argument");
     return QK_ERR_ARG;
@@ -181,6 +182,15 @@ extern "C" qk_status qk_restore(const char* path, qk_config* cfg_out, qk_index**
       cfg.n_parent != N1 || n > (int64_t(1) << 40) / d)
     return io_error("qk_restore: invalid header");
   const int lpb = row_bytes_lp(cfg.storage);
+  // the file must be exactly as long as its header says, before anything is allocated
+  const long here = std::ftell(g.f);
+  const double need = (double)here + 4.0 * N0 + 4.0 * N0 * d + 8.0 * n + 4.0 * n * d +
+                      (lpb ? (double)n * d * lpb + 4.0 * N0 : 0.0) +
+                      (N1 > 0 ? 4.0 * N1 + 4.0 * N1 * d + 8.0 * N0 : 0.0) + 8.0 * N0 + 8.0 * N1 + 8.0;
+  if (here < 0 || std::fseek(g.f, 0, SEEK_END) != 0) return io_error("qk_restore: cannot seek");
+  const long size = std::ftell(g.f);
+  if (size < 0 || (double)size != need || std::fseek(g.f, here, SEEK_SET) != 0)
+    return io_error("qk_restore: file size does not match its header (truncated or corrupt)");
   std::vector<int32_t> s0(N0), s1(N1);
   std::vector<float> c0((size_t)N0 * d), c1((size_t)N1 * d), x((size_t)n * d), sc(N0);
   std::vector<int64_t> id0(n), mem1(N1 > 0 ? N0 : 0);
@@ -276,4 +286,22 @@ extern "C" qk_status qk_restore(const char* path, qk_config* cfg_out, qk_index**
   if (cfg_out) *cfg_out = cfg;
   *out = ix;
   return QK_OK;
+}
+
+extern "C" qk_status qk_save(qk_index* ix, const char* path) {
+  try {
+    return save_impl(ix, path);
+  } catch (const std::bad_alloc&) {
+    set_error("qk_save: out of host memory");
+    return QK_ERR_OOM;
+  }
+}
+
+extern "C" qk_status qk_restore(const char* path, qk_config* cfg_out, qk_index** out) {
+  try {
+    return restore_impl(path, cfg_out, out);
+  } catch (const std::bad_alloc&) {
+    set_error("qk_restore: out of host memory");
+    return QK_ERR_OOM;
+  }
 }
