@@ -1193,6 +1193,7 @@ qk_status check_call(qk_batch* b, const float* q, int64_t nq, const int32_t* npr
 extern "C" {
 
 qk_status qk_batch_create(qk_index* ix, int64_t max_nq, int32_t k, int32_t max_nprobe, qk_batch** out) {
+  QK_GUARD_BEGIN
   if (!ix || !out) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -1248,6 +1249,7 @@ qk_status qk_batch_create(qk_index* ix, int64_t max_nq, int32_t k, int32_t max_n
   }
   *out = b;
   return QK_OK;
+  QK_GUARD_END
 }
 
 void qk_batch_destroy(qk_batch* b) {
@@ -1259,6 +1261,7 @@ void qk_batch_destroy(qk_batch* b) {
 }
 
 qk_status qk_batch_set_timing(qk_batch* b, int32_t on) {
+  QK_GUARD_BEGIN
   if (!b) {
     set_error("null plan");
     return QK_ERR_ARG;
@@ -1268,9 +1271,11 @@ qk_status qk_batch_set_timing(qk_batch* b, int32_t on) {
   b->timing = on != 0;
   b->timed = false;
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_batch_stage_times(qk_batch* b, float* ms) {
+  QK_GUARD_BEGIN
   if (!b || !ms) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -1282,18 +1287,22 @@ qk_status qk_batch_stage_times(qk_batch* b, float* ms) {
   QK_CUDA(cudaEventSynchronize(b->ev[5]));
   for (int i = 0; i < 5; ++i) QK_CUDA(cudaEventElapsedTime(&ms[i], b->ev[i], b->ev[i + 1]));
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_batch_get_tiles(const qk_batch* b, qk_batch_tiles* out) {
+  QK_GUARD_BEGIN
   if (!b || !out) {
     set_error("null argument");
     return QK_ERR_ARG;
   }
   *out = b->tiles;
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_batch_set_tiles(qk_batch* b, const qk_batch_tiles* t) {
+  QK_GUARD_BEGIN
   if (!b || !t) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -1305,19 +1314,23 @@ qk_status qk_batch_set_tiles(qk_batch* b, const qk_batch_tiles* t) {
   }
   b->tiles = *t;
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_batch_search(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
                           float* out_dist, void* stream) {
+  QK_GUARD_BEGIN
   QK_TRY(check_call(b, q, nq, nprobe, out_ids, out_dist));
   if (nq == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   QK_TRY(refresh(b, s));
   return enqueue(b, q, nq, nprobe, out_ids, out_dist, s);
+  QK_GUARD_END
 }
 
 qk_status qk_batch_capture(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
                            float* out_dist, void* stream) {
+  QK_GUARD_BEGIN
   QK_TRY(check_call(b, q, nq, nprobe, out_ids, out_dist));
   if (nq == 0) {
     set_error("nothing to capture");
@@ -1353,9 +1366,11 @@ qk_status qk_batch_capture(qk_batch* b, const float* q, int64_t nq, const int32_
   }
   b->graph_version = b->ix->version;
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_batch_replay(qk_batch* b, void* stream) {
+  QK_GUARD_BEGIN
   if (!b || !b->graph) {
     set_error("no captured batch");
     return QK_ERR_STATE;
@@ -1366,10 +1381,12 @@ qk_status qk_batch_replay(qk_batch* b, void* stream) {
   }
   QK_CUDA(cudaGraphLaunch(b->graph, (cudaStream_t)stream));
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_batch_autotune(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
                             float* out_dist, int32_t reps, qk_batch_tiles* chosen, void* stream) {
+  QK_GUARD_BEGIN
   QK_TRY(check_call(b, q, nq, nprobe, out_ids, out_dist));
   if (nq == 0) {
     set_error("nothing to tune on");
@@ -1418,6 +1435,7 @@ qk_status qk_batch_autotune(qk_batch* b, const float* q, int64_t nq, const int32
   b->tiles = st == QK_OK ? best_t : keep;
   if (chosen) *chosen = b->tiles;
   return st;
+  QK_GUARD_END
 }
 
 }  // extern "C"

@@ -616,6 +616,7 @@ static void keep_pool_memory(int dev) {
 }
 
 qk_status qk_create(const qk_config* cfg, qk_index** out) {
+  QK_GUARD_BEGIN
   if (!cfg || !out) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -661,6 +662,7 @@ qk_status qk_create(const qk_config* cfg, qk_index** out) {
   }
   *out = ix;
   return QK_OK;
+  QK_GUARD_END
 }
 
 void qk_destroy(qk_index* ix) {
@@ -681,6 +683,7 @@ void qk_destroy(qk_index* ix) {
 }
 
 qk_status qk_build(qk_index* ix, const float* x, const int64_t* ids, int64_t n, void* stream) {
+  QK_GUARD_BEGIN
   if (!ix || !x || !ids || n < 1) {
     set_error("null argument or empty input");
     return QK_ERR_ARG;
@@ -710,11 +713,13 @@ qk_status qk_build(qk_index* ix, const float* x, const int64_t* ids, int64_t n, 
     QK_TRY(kmeans(C0, N0, d, N1, ix->cfg.kmeans_iters, ix->cfg.seed + 1, C1, a1, s, nullptr));
   }
   return install(ix, X, I, n, C0, a0, C1, a1, s, false);
+  QK_GUARD_END
 }
 
 qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, const float* leaf_centroids,
                   const int32_t* leaf_of_row, const float* parent_centroids, const int32_t* parent_of_leaf,
                   void* stream) {
+  QK_GUARD_BEGIN
   if (!ix || !x || !ids || n < 0 || !leaf_centroids || !leaf_of_row) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -739,6 +744,7 @@ qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, c
     QK_TRY(in_device(parent_of_leaf, (size_t)N0, ta1, &a1, s));
   }
   return install(ix, X, I, n, C0, a0, C1, a1, s, false);
+  QK_GUARD_END
 }
 
 // The search of qk_search; nprobe_q (device, optional) gives fixed-nprobe
@@ -850,11 +856,14 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
 
 qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
                     int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall, void* stream) {
+  QK_GUARD_BEGIN
   return search_impl(ix, q, nq, k, recall_target, nprobe, nullptr, out_ids, out_dist, out_nprobe, out_recall, stream);
+  QK_GUARD_END
 }
 
 qk_status qk_search_nprobe(qk_index* ix, const float* q, int64_t nq, int32_t k, const int32_t* nprobe,
                            int64_t* out_ids, float* out_dist, void* stream) {
+  QK_GUARD_BEGIN
   QK_TRY(check_ready(ix));
   if (nq < 0 || (nq > 0 && !nprobe)) {
     set_error("invalid search arguments");
@@ -876,9 +885,11 @@ qk_status qk_search_nprobe(qk_index* ix, const float* q, int64_t nq, int32_t k, 
   const int32_t* dn = nullptr;
   QK_TRY(in_device(nprobe, (size_t)nq, tn, &dn, s));
   return search_impl(ix, q, nq, k, 0.0f, std::min(mx, ix->n_leaf), dn, out_ids, out_dist, nullptr, nullptr, stream);
+  QK_GUARD_END
 }
 
 qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n, void* stream) {
+  QK_GUARD_BEGIN
   QK_TRY(check_ready(ix));
   if (n < 0 || (n > 0 && (!x || !ids))) {
     set_error("invalid insert arguments");
@@ -969,9 +980,11 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   ++ix->version;
   tr.mark("place");
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_removed, void* stream) {
+  QK_GUARD_BEGIN
   QK_TRY(check_ready(ix));
   if (n < 0 || (n > 0 && !ids)) {
     set_error("invalid delete arguments");
@@ -1042,17 +1055,21 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
   tr.mark("moves");
   if (n_removed) *n_removed = removed;
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_check(qk_index* ix, void* stream) {
+  QK_GUARD_BEGIN
   if (!ix) {
     set_error("null index");
     return QK_ERR_ARG;
   }
   return read_device_status(ix, (cudaStream_t)stream);
+  QK_GUARD_END
 }
 
 qk_status qk_info(const qk_index* ix, int64_t* n_vectors, int32_t* n_leaf, int32_t* n_parent, int32_t* d) {
+  QK_GUARD_BEGIN
   if (!ix) {
     set_error("null index");
     return QK_ERR_ARG;
@@ -1062,10 +1079,12 @@ qk_status qk_info(const qk_index* ix, int64_t* n_vectors, int32_t* n_leaf, int32
   if (n_parent) *n_parent = ix->ready ? ix->n_parent : ix->cfg.n_parent;
   if (d) *d = ix->cfg.d;
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_export_level(const qk_index* ix, int32_t level, int32_t* sizes, float* centroids, int64_t* ids,
                           float* vectors) {
+  QK_GUARD_BEGIN
   QK_TRY(check_ready(ix));
   const int d = ix->cfg.d;
   if (level == 0) {
@@ -1106,9 +1125,11 @@ qk_status qk_export_level(const qk_index* ix, int32_t level, int32_t* sizes, flo
   }
   set_error("no such level");
   return QK_ERR_ARG;
+  QK_GUARD_END
 }
 
 qk_status qk_export_quantized(const qk_index* ix, uint8_t* codes, float* scales) {
+  QK_GUARD_BEGIN
   QK_TRY(check_ready(ix));
   if (!ix->lp0) {
     set_error("the index stores FP32 only");
@@ -1127,9 +1148,11 @@ qk_status qk_export_quantized(const qk_index* ix, uint8_t* codes, float* scales)
   if (scales && ix->cfg.storage == QK_STORE_BF16)
     for (int32_t j = 0; j < ix->n_leaf; ++j) scales[j] = 1.0f;
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_get_hits(qk_index* ix, int32_t level, int64_t* hits, int32_t reset) {
+  QK_GUARD_BEGIN
   QK_TRY(check_ready(ix));
   unsigned long long* src = level == 0 ? ix->hits0 : (level == 1 ? ix->hits1 : nullptr);
   int32_t n = level == 0 ? ix->n_leaf : ix->n_parent;
@@ -1140,10 +1163,12 @@ qk_status qk_get_hits(qk_index* ix, int32_t level, int64_t* hits, int32_t reset)
   if (hits) QK_CUDA(cudaMemcpy(hits, src, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
   if (reset) QK_CUDA(cudaMemset(src, 0, sizeof(unsigned long long) * n));
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_cap_fraction(int32_t d, int32_t mode, const double* t, const double* rho, int64_t n, double* out_u,
                           void* stream) {
+  QK_GUARD_BEGIN
   if (d < 1 || n < 0 || (n > 0 && (!t || !rho || !out_u)) || (mode != QK_BETA_EXACT && mode != QK_BETA_TABLE)) {
     set_error("invalid arguments");
     return QK_ERR_ARG;
@@ -1166,10 +1191,12 @@ qk_status qk_cap_fraction(int32_t d, int32_t mode, const double* t, const double
   if (!out_dev) QK_CUDA(cudaMemcpyAsync(out_u, dout, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   QK_CUDA(cudaStreamSynchronize(s));
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_nearest_centroids(const float* x, int64_t n, int32_t d, const float* c, int32_t K, int32_t metric,
                                int32_t k, int32_t* out_idx, float* out_dist, void* stream) {
+  QK_GUARD_BEGIN
   if (!x || !c || !out_idx || n < 0 || K < 1 || d < 32 || d % 32 != 0 || k < 1 || k > 8 || k > K ||
       (metric != QK_METRIC_L2 && metric != QK_METRIC_IP)) {
     set_error("qk_nearest_centroids: invalid arguments (d a multiple of 32, 1 <= k <= min(8, K))");
@@ -1204,10 +1231,12 @@ qk_status qk_nearest_centroids(const float* x, int64_t n, int32_t d, const float
     return QK_ERR_TIMEOUT;
   }
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, int32_t K, float* c_new,
                          int32_t* assign, int32_t* counts, void* stream) {
+  QK_GUARD_BEGIN
   if (!x || !c || n < 1 || d < 1 || K < 1) {
     set_error("invalid arguments");
     return QK_ERR_ARG;
@@ -1232,6 +1261,7 @@ qk_status qk_kmeans_step(const float* x, int64_t n, int32_t d, const float* c, i
   if (counts) QK_CUDA(cudaMemcpyAsync(counts, cnt, sizeof(int32_t) * (size_t)K, cudaMemcpyDefault, s));
   QK_CUDA(cudaStreamSynchronize(s));
   return QK_OK;
+  QK_GUARD_END
 }
 
 }  // extern "C"

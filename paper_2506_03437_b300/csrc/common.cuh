@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
+#include <new>
 #include <string>
 
 #include "../../include/quake_b300.h"
@@ -21,6 +23,21 @@ qk_status cuda_status(cudaError_t e, const char* what);
     cudaError_t e__ = (call);                                      \
     if (e__ != cudaSuccess) return ::qk::cuda_status(e__, #call);  \
   } while (0)
+
+// Host exceptions (std::bad_alloc from a container, above all) must not cross
+// the C interface: the body of every qk_status entry point runs inside
+// QK_GUARD_BEGIN ... QK_GUARD_END.
+#define QK_GUARD_BEGIN try {
+#define QK_GUARD_END                                                     \
+  }                                                                      \
+  catch (const std::bad_alloc&) {                                        \
+    ::qk::set_error("out of host memory");                               \
+    return QK_ERR_OOM;                                                   \
+  }                                                                      \
+  catch (const std::exception& e__) {                                    \
+    ::qk::set_error(std::string("unexpected host exception: ") + e__.what()); \
+    return QK_ERR_INTERNAL;                                              \
+  }
 
 #define QK_TRY(call)                         \
   do {                                       \

@@ -593,14 +593,17 @@ static void discard_pending(qk_index* ix) {
 
 extern "C" qk_status qk_maintain(qk_index* ix, const qk_maint_params* params, qk_maint_action* log, int32_t log_cap,
                                  int32_t* n_log, void* stream) {
+  QK_GUARD_BEGIN
   qk_index* nx = nullptr;
   QK_TRY(maintain_plan(ix, params, log, log_cap, n_log, stream, &nx));
   discard_pending(ix);
   return commit_structure(ix, nx, (cudaStream_t)stream);
+  QK_GUARD_END
 }
 
 extern "C" qk_status qk_maintain_prepare(qk_index* ix, const qk_maint_params* params, qk_maint_action* log,
                                          int32_t log_cap, int32_t* n_log, void* stream) {
+  QK_GUARD_BEGIN
   if (!ix) {
     set_error("null index");
     return QK_ERR_ARG;
@@ -613,9 +616,11 @@ extern "C" qk_status qk_maintain_prepare(qk_index* ix, const qk_maint_params* pa
   ix->pending = nx;
   ix->pending_version = v;
   return QK_OK;
+  QK_GUARD_END
 }
 
 extern "C" qk_status qk_maintain_commit(qk_index* ix, void* stream) {
+  QK_GUARD_BEGIN
   if (!ix || !ix->pending) {
     set_error("no prepared maintenance pass");
     return QK_ERR_STATE;
@@ -628,4 +633,5 @@ extern "C" qk_status qk_maintain_commit(qk_index* ix, void* stream) {
   qk_index* nx = ix->pending;
   ix->pending = nullptr;
   return commit_structure(ix, nx, (cudaStream_t)stream);
+  QK_GUARD_END
 }

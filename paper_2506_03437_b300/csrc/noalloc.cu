@@ -64,6 +64,7 @@ using namespace qk;
 
 extern "C" qk_status qk_kmeans_step_noalloc(const float* x, int64_t n, int32_t d, const float* c, int32_t K,
                                             float* c_new, int32_t* assign, int32_t* counts, void* stream) {
+  QK_GUARD_BEGIN
   if (!x || !c || !c_new || !assign || !counts || n < 1 || d < 1 || K < 1) {
     set_error("qk_kmeans_step_noalloc: null buffer or empty size");
     return QK_ERR_ARG;
@@ -86,4 +87,5 @@ extern "C" qk_status qk_kmeans_step_noalloc(const float* x, int64_t n, int32_t d
   QK_TRY(launch_kmeans_assign(x, n, d, c, K, assign, nullptr, s));
   QK_TRY(launch_kmeans_update(x, n, d, assign, c, K, c_new, sums, counts, s));
   return QK_OK;
+  QK_GUARD_END
 }

@@ -194,6 +194,7 @@ using namespace qk;
 
 extern "C" qk_status qk_profile_scan(const qk_config* cfg, int32_t k, const int64_t* sizes, int32_t n_sizes,
                                      int32_t reps, double* out_us, void* stream) {
+  QK_GUARD_BEGIN
   if (!cfg || !sizes || !out_us || n_sizes < 1 || k < 1 || k > 1024 || reps < 1) {
     set_error("qk_profile_scan: invalid arguments");
     return QK_ERR_ARG;
@@ -216,4 +217,5 @@ extern "C" qk_status qk_profile_scan(const qk_config* cfg, int32_t k, const int6
   QK_CUDA(cudaEventCreate(&ev.b));
   for (int32_t i = 0; i < n_sizes; ++i) QK_TRY(profile_one(*cfg, k, sizes[i], reps, n_sm, s, ev, &out_us[i]));
   return QK_OK;
+  QK_GUARD_END
 }

@@ -404,6 +404,7 @@ void qk_server_config_default(qk_server_config* c) {
 }
 
 qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server** out) {
+  QK_GUARD_BEGIN
   if (!ix || !cfg || !out) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -456,30 +457,38 @@ qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server*
   sv->scheduler = std::thread(scheduler_loop, sv);
   *out = sv;
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_server_submit_search(qk_server* sv, const float* q, int64_t* ticket) {
+  QK_GUARD_BEGIN
   if (!q) {
     set_error("null query");
     return QK_ERR_ARG;
   }
   return submit(sv, 0, q, -1, ticket);
+  QK_GUARD_END
 }
 
 qk_status qk_server_submit_insert(qk_server* sv, const float* x, int64_t id, int64_t* ticket) {
+  QK_GUARD_BEGIN
   if (!x) {
     set_error("null vector");
     return QK_ERR_ARG;
   }
   return submit(sv, 1, x, id, ticket);
+  QK_GUARD_END
 }
 
 qk_status qk_server_submit_delete(qk_server* sv, int64_t id, int64_t* ticket) {
+  QK_GUARD_BEGIN
   return submit(sv, 2, nullptr, id, ticket);
+  QK_GUARD_END
 }
 
 qk_status qk_server_results(qk_server* sv, int64_t first, int64_t count, int32_t* done, int64_t* ids,
                             float* dist, double* latency_s) {
+  QK_GUARD_BEGIN
   if (!sv || count < 0 || first < 0) {
     set_error("invalid arguments");
     return QK_ERR_ARG;
@@ -499,9 +508,11 @@ qk_status qk_server_results(qk_server* sv, int64_t first, int64_t count, int32_t
     if (dist) std::memcpy(dist + j * k, &sv->res_dist[(size_t)(first + j) * k], sizeof(float) * k);
   }
   return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_server_drain(qk_server* sv, double timeout_s) {
+  QK_GUARD_BEGIN
   if (!sv) {
     set_error("null server");
     return QK_ERR_ARG;
@@ -529,9 +540,11 @@ qk_status qk_server_drain(qk_server* sv, double timeout_s) {
     }
     std::this_thread::sleep_for(std::chrono::microseconds(200));
   }
+  QK_GUARD_END
 }
 
 qk_status qk_server_get_stats(const qk_server* sv, qk_server_stats* out) {
+  QK_GUARD_BEGIN
   if (!sv || !out) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -546,6 +559,7 @@ qk_status qk_server_get_stats(const qk_server* sv, qk_server_stats* out) {
   out->maintenance_stall_s = sv->maint_stall_s;
   out->maintenance_prepare_s = sv->maint_prepare_s;
   return QK_OK;
+  QK_GUARD_END
 }
 
 void qk_server_destroy(qk_server* sv) {
