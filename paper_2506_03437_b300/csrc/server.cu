@@ -225,7 +225,7 @@ void run_prepare(qk_server* sv) {
   }
 }
 
-void scheduler_loop(qk_server* sv) {
+void scheduler_body(qk_server* sv) {
   cudaSetDevice(sv->device);
   const int d = sv->d;
   const int64_t min_window =
@@ -345,6 +345,17 @@ void scheduler_loop(qk_server* sv) {
     std::unique_lock<std::mutex> g(sv->mu);
     if (sv->stopping && sv->searches.empty() && sv->updates.empty() && sv->prep_state.load() == 0) return;
     sv->cv.wait_for(g, std::chrono::microseconds(200));
+  }
+}
+
+// A host exception in the scheduler (a failed allocation) stops the server as
+// a failed call does: the error is kept and returned by drain and submissions.
+void scheduler_loop(qk_server* sv) {
+  try {
+    scheduler_body(sv);
+  } catch (const std::exception& e) {
+    set_error(std::string("scheduler: ") + e.what());
+    fail(sv, QK_ERR_INTERNAL, "scheduler");
   }
 }
 
