@@ -480,15 +480,25 @@ __device__ float exact_l2(const float* q, const float* c, int d, int lane) {
 
 // Key of the rank-th smallest (1-based) of row[0..K): four 8-bit radix passes
 // over a shared histogram.
+// The row is read as float4: its stride is a multiple of 4 floats (16-byte
+// aligned), and the padding after K is skipped.
 __device__ uint32_t radix_select(const float* row, int K, int rank, uint32_t* hist, int* s_b, int* s_rank) {
+  const float4* row4 = reinterpret_cast<const float4*>(row);
+  const int K4 = (K + 3) >> 2;
   uint32_t prefix = 0, mask = 0;
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 24 - 8 * pass;
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
     __syncthreads();
-    for (int c = threadIdx.x; c < K; c += blockDim.x) {
-      const uint32_t key = fkey(row[c]);
-      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    for (int c4 = threadIdx.x; c4 < K4; c4 += blockDim.x) {
+      const float4 v = row4[c4];
+      const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (4 * c4 + t >= K) break;
+        const uint32_t key = fkey(e[t]);
+        if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -583,10 +593,17 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(SelArgs a) {
     const float lim = exact_row ? theta : __fadd_ru(theta, 2.f * E);
     if (tid == 0) s_int[0] = 0;
     __syncthreads();
-    for (int c = tid; c < K; c += blockDim.x) {
-      if (row[c] <= lim) {
-        const int pos = atomicAdd(&s_int[0], 1);
-        if (pos < kSelCap) cidx[pos] = c;
+    const float4* row4 = reinterpret_cast<const float4*>(row);
+    for (int c4 = tid; c4 < ((K + 3) >> 2); c4 += blockDim.x) {
+      const float4 v = row4[c4];
+      const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int c = 4 * c4 + t;
+        if (c < K && e[t] <= lim) {
+          const int pos = atomicAdd(&s_int[0], 1);
+          if (pos < kSelCap) cidx[pos] = c;
+        }
       }
     }
     __syncthreads();
