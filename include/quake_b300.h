@@ -576,7 +576,10 @@ qk_status qk_server_create(qk_index* index, const qk_server_config* cfg, qk_serv
 /* Finishes every submitted request, stops the scheduler and frees the server. */
 void qk_server_destroy(qk_server* server);
 /* q / x: d FP32 host values, copied at submission.  Tickets count from 0 in
- * submission order.  QK_ERR_STATE once the server stopped after an error. */
+ * submission order.  QK_ERR_ARG (no ticket; the server keeps running) for a
+ * vector with a NaN or infinite element or a squared norm beyond FP32, which
+ * the kernels would refuse.  QK_ERR_STATE once the server stopped after an
+ * error. */
 qk_status qk_server_submit_search(qk_server* server, const float* q, int64_t* ticket);
 qk_status qk_server_submit_insert(qk_server* server, const float* x, int64_t id, int64_t* ticket);
 qk_status qk_server_submit_delete(qk_server* server, int64_t id, int64_t* ticket);

@@ -368,6 +368,21 @@ qk_status submit(qk_server* sv, int kind, const float* x, int64_t id, int64_t* t
     set_error("the server stopped after an error: " + sv->error);
     return QK_ERR_STATE;
   }
+  if (kind != 2) {
+    // a vector the kernels would refuse is refused here, so that one bad
+    // request cannot stop the server: every element finite, squared norm
+    // within FP32
+    if (!x) {
+      set_error("null vector");
+      return QK_ERR_ARG;
+    }
+    double n2 = 0.0;
+    for (int j = 0; j < sv->d; ++j) n2 += (double)x[j] * (double)x[j];
+    if (!(n2 < 1e38)) {
+      set_error("vector with a NaN or infinite element, or a squared norm beyond FP32");
+      return QK_ERR_ARG;
+    }
+  }
   const int k = sv->cfg.k;
   std::lock_guard<std::mutex> g(sv->mu);
   if (sv->stopping) {

@@ -123,7 +123,15 @@ def test_native_server_rejects_bad_config_and_reports_a_failed_update():
     L.check(L.lib.qk_server_create(ix._h, C.byref(cfg), C.byref(h)))
     try:
         t = C.c_int64()
+        # a non-finite vector is refused at submission; the server keeps running
+        nanq = np.ascontiguousarray(Q[0].copy())
+        nanq[3] = np.nan
+        assert L.lib.qk_server_submit_search(h, nanq.ctypes.data, C.byref(t)) == L.ERR_ARG
+        infx = np.ascontiguousarray(X[0].copy())
+        infx[0] = np.inf
+        assert L.lib.qk_server_submit_insert(h, infx.ctypes.data, 10 ** 9, C.byref(t)) == L.ERR_ARG
         L.check(L.lib.qk_server_submit_search(h, Q.ctypes.data, C.byref(t)))
+        assert L.lib.qk_server_drain(h, 30.0) == L.OK
         x = np.ascontiguousarray(X[0] + 0.5)
         L.check(L.lib.qk_server_submit_insert(h, x.ctypes.data, 7, C.byref(t)))   # id 7 exists
         assert L.lib.qk_server_drain(h, 30.0) == L.ERR_STATE
