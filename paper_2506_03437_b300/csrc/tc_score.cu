@@ -196,15 +196,17 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
       // stride 1024 B, so every address the descriptors can form stays
       // inside the slice.
       const uint32_t a_base = smem_u32(smem + b * kSliceA), b_base = smem_u32(smem + 2 * kSliceA + b * kSliceB);
+      // consecutive threads take consecutive 16-byte chunks of one row, so a
+      // warp reads whole 128-byte row segments from global memory
       for (int e = tid; e < kM * (kKS / 4); e += kThreads) {
-        int r = e % kM, c = e / kM;
+        int c = e % (kKS / 4), r = e / (kKS / 4);
         int64_t gr = row0 + r;
         bool v = gr < n;
         const float* src = X + (v ? gr : 0) * d + ks * kKS + c * 4;
         cp_async16(a_base + ((r >> 3) * (kKS / 4) + c) * 128 + (r & 7) * 16, src, v);
       }
       for (int e = tid; e < kN * (kKS / 4); e += kThreads) {
-        int r = e % kN, c = e / kN;
+        int c = e % (kKS / 4), r = e / (kKS / 4);
         int gc = n0 + r;
         bool v = gc < K;
         const float* src = C + (int64_t)(v ? gc : 0) * d + ks * kKS + c * 4;
