@@ -71,6 +71,11 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool v
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
@@ -178,48 +183,61 @@ __global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float
   uint32_t issued[2] = {0u, 0u};   // commits outstanding per buffer (0 or 1)
   bool ok = true;
 
+  // a buffer is free once the MMAs that read it have completed
+  auto free_buffer = [&](int b) {
+    if (!issued[b]) return;
+    if (!mbar_wait_bounded(&bars[b], phase[b])) {
+      ok = false;
+      atomicExch(status, DEV_TIMEOUT);
+    }
+    phase[b] ^= 1u;
+    issued[b] = 0;
+  };
+  // slice ks into buffer b: 8-row groups, each holding its 8 K-chunks of 16
+  // bytes as consecutive core matrices: (row r, chunk c) at
+  // ((r / 8) * 8 + c) * 128 + (r % 8) * 16.  K stride 128 B, row-group stride
+  // 1024 B, so every address the descriptors can form stays inside the slice.
+  // Consecutive threads take consecutive 16-byte chunks of one row, so a warp
+  // reads whole 128-byte row segments from global memory.
+  auto stage = [&](int n0, int ks, int b) {
+    const uint32_t a_base = smem_u32(smem + b * kSliceA), b_base = smem_u32(smem + 2 * kSliceA + b * kSliceB);
+    for (int e = tid; e < kM * (kKS / 4); e += kThreads) {
+      int c = e % (kKS / 4), r = e / (kKS / 4);
+      int64_t gr = row0 + r;
+      bool v = gr < n;
+      const float* src = X + (v ? gr : 0) * d + ks * kKS + c * 4;
+      cp_async16(a_base + ((r >> 3) * (kKS / 4) + c) * 128 + (r & 7) * 16, src, v);
+    }
+    for (int e = tid; e < kN * (kKS / 4); e += kThreads) {
+      int c = e % (kKS / 4), r = e / (kKS / 4);
+      int gc = n0 + r;
+      bool v = gc < K;
+      const float* src = C + (int64_t)(v ? gc : 0) * d + ks * kKS + c * 4;
+      cp_async16(b_base + ((r >> 3) * (kKS / 4) + c) * 128 + (r & 7) * 16, src, v);
+    }
+    cp_async_commit();
+  };
+
   for (int n0 = n_begin; n0 < n_end && ok; n0 += kN) {
+    // two slices in flight: slice ks + 1 is copied while slice ks is waited for
+    free_buffer(0);
+    stage(n0, 0, 0);
+    for (int j = tid; j < kN; j += kThreads) scn[j] = n0 + j < K ? cnorm[n0 + j] : INFINITY;
     for (int ks = 0; ks < nslices; ++ks) {
       const int b = ks & 1;
-      // the buffer is free once the MMAs that read it have completed
-      if (issued[b]) {
-        if (!mbar_wait_bounded(&bars[b], phase[b])) {
-          ok = false;
-          atomicExch(status, DEV_TIMEOUT);
-        }
-        phase[b] ^= 1u;
-        issued[b] = 0;
+      if (ks + 1 < nslices) {
+        free_buffer(b ^ 1);
+        stage(n0, ks + 1, b ^ 1);
+        cp_async_wait_group<1>();   // this thread's copies of slice ks have landed
+      } else {
+        cp_async_wait_group<0>();
       }
-      // stage slice ks: 8-row groups, each holding its 8 K-chunks of 16 bytes
-      // as consecutive core matrices: (row r, chunk c) at
-      // ((r / 8) * 8 + c) * 128 + (r % 8) * 16.  K stride 128 B, row-group
-      // stride 1024 B, so every address the descriptors can form stays
-      // inside the slice.
-      const uint32_t a_base = smem_u32(smem + b * kSliceA), b_base = smem_u32(smem + 2 * kSliceA + b * kSliceB);
-      // consecutive threads take consecutive 16-byte chunks of one row, so a
-      // warp reads whole 128-byte row segments from global memory
-      for (int e = tid; e < kM * (kKS / 4); e += kThreads) {
-        int c = e % (kKS / 4), r = e / (kKS / 4);
-        int64_t gr = row0 + r;
-        bool v = gr < n;
-        const float* src = X + (v ? gr : 0) * d + ks * kKS + c * 4;
-        cp_async16(a_base + ((r >> 3) * (kKS / 4) + c) * 128 + (r & 7) * 16, src, v);
-      }
-      for (int e = tid; e < kN * (kKS / 4); e += kThreads) {
-        int c = e % (kKS / 4), r = e / (kKS / 4);
-        int gc = n0 + r;
-        bool v = gc < K;
-        const float* src = C + (int64_t)(v ? gc : 0) * d + ks * kKS + c * 4;
-        cp_async16(b_base + ((r >> 3) * (kKS / 4) + c) * 128 + (r & 7) * 16, src, v);
-      }
-      if (ks == 0)
-        for (int j = tid; j < kN; j += kThreads) scn[j] = n0 + j < K ? cnorm[n0 + j] : INFINITY;
-      cp_async_wait_all();
       fence_proxy_async();        // generic-proxy writes -> tensor-core (async proxy) reads
       fence_before_sync();
       __syncthreads();
       fence_after_sync();
       if (tid == 0) {
+        const uint32_t a_base = smem_u32(smem + b * kSliceA), b_base = smem_u32(smem + 2 * kSliceA + b * kSliceB);
 #pragma unroll
         for (int i = 0; i < kKS / 8; ++i) {   // K = 8 per tf32 MMA: two 16-byte chunks
           uint64_t ad = smem_desc(a_base + (2 * i) * 128, 128, (kKS / 4) * 128);
