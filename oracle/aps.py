@@ -16,6 +16,10 @@ library):
   R3  p_0 = prod_j (1 - u_j) over the raw cap fractions u_j; the remaining
       mass 1 - p_0 is spread in proportion to the normalised v_i = u_i / sum u
       (Eq. 8-9).  With sum u = 0, p_0 = 1 and every p_i = 0.
+      Params(p0_reading="normalised") takes the text of Eq. 8 literally
+      instead: the caps are normalised first and p_0 = prod_j (1 - v_j) over
+      the normalised v_j.  It exists to compare the two readings; the search
+      defaults to R3.
   R4  Until R holds k results the estimator is not used: partitions are
       scanned in centroid-distance order.  When R first holds k results, rho is
       set and every p is computed.
@@ -55,7 +59,7 @@ class Params:
     """Search parameters (defaults from Sec. 5 and Sec. 8.1)."""
 
     def __init__(self, k=10, recall_target=0.9, nprobe=0, f_M=(0.1, 0.25),
-                 tau_rho=0.01, upper_recall=0.99, beta_mode="table"):
+                 tau_rho=0.01, upper_recall=0.99, beta_mode="table", p0_reading="raw"):
         self.k = k
         self.recall_target = recall_target
         self.nprobe = nprobe
@@ -63,6 +67,9 @@ class Params:
         self.tau_rho = tau_rho
         self.upper_recall = upper_recall
         self.beta_mode = beta_mode
+        if p0_reading not in ("raw", "normalised"):
+            raise ValueError("p0_reading is 'raw' (R3) or 'normalised' (Eq. 8 read literally)")
+        self.p0_reading = p0_reading
 
 
 def n_candidates(f, n):
@@ -85,8 +92,9 @@ def bisector_distances(D, C):
     return np.maximum(t, 0.0)
 
 
-def probabilities(t, rho, d, mode="table", table=None):
-    """p_0..p_{M-1} from Eq. 8-9 with raw caps for p_0 (R3).  t[0] is unused."""
+def probabilities(t, rho, d, mode="table", table=None, p0_reading="raw"):
+    """p_0..p_{M-1} from Eq. 8-9 with raw caps for p_0 (R3), or with the
+    normalised caps for p_0 when p0_reading is "normalised".  t[0] is unused."""
     t = np.asarray(t, dtype=np.float64)
     M = t.shape[0]
     p = np.zeros(M)
@@ -97,8 +105,13 @@ def probabilities(t, rho, d, mode="table", table=None):
         u = cap_fraction(t[1:], rho, d)
     else:
         u = cap_fraction_table(t[1:], rho, table)
-    p0 = float(np.prod(1.0 - u))
     U = float(u.sum())
+    if p0_reading == "raw":
+        p0 = float(np.prod(1.0 - u))
+    elif U > 0.0:
+        p0 = float(np.prod(1.0 - u / U))
+    else:
+        p0 = 1.0
     p[0] = p0
     if U > 0.0:
         p[1:] = (1.0 - p0) * (u / U)
@@ -147,7 +160,11 @@ def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
     cand_D   their squared Euclidean centroid distances D_i (R11)
     metric   ranks the level's rows (L2 for upper levels, R11)
     Returns a dict: dist, ids (R sorted), scanned (positions in scan order),
-    r (final estimate), trace (decision margins for parity checks).
+    r (final estimate), trace (decision margins for parity checks) and steps:
+    one record per estimator step, the first taken when R first holds k
+    results, then one after every later scan, each with the position just
+    scanned ("pos", None for the first), "rho" and "p" as they stand after
+    the recompute decision, "recomputed" and "r".
     """
     q = np.asarray(q, dtype=np.float64)
     M = len(cand)
@@ -155,6 +172,7 @@ def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
     scanned = np.zeros(M, dtype=bool)
     order = []
     trace = []
+    steps = []
 
     def scan(pos):
         j = cand[pos]
@@ -166,7 +184,7 @@ def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
     if fixed_nprobe > 0:
         for pos in range(min(fixed_nprobe, M)):
             scan(pos)
-        return dict(dist=R.dist, ids=R.ids, scanned=order, r=float("nan"), trace=trace)
+        return dict(dist=R.dist, ids=R.ids, scanned=order, r=float("nan"), trace=trace, steps=steps)
 
     t = bisector_distances(cand_D, level.centroids[np.asarray(cand)])
 
@@ -174,11 +192,12 @@ def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
     while not R.full() and not scanned.all():                       # R4
         scan(int(np.argmin(scanned)))
     if not R.full():
-        return dict(dist=R.dist, ids=R.ids, scanned=order, r=1.0, trace=trace)
+        return dict(dist=R.dist, ids=R.ids, scanned=order, r=1.0, trace=trace, steps=steps)
 
     rho = kth_radius(R, q, metric)
-    p = probabilities(t, rho, d, params.beta_mode, table)
+    p = probabilities(t, rho, d, params.beta_mode, table, params.p0_reading)
     r = p[0] + p[1:][scanned[1:]].sum()                                # R5
+    steps.append(dict(pos=None, rho=rho, recomputed=True, p=p.copy(), r=float(r)))
     while True:
         trace.append(("stop", len(order), r - tau_R))
         if not (r < tau_R) or scanned.all():                          # R8
@@ -196,11 +215,13 @@ def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
         rho_new = kth_radius(R, q, metric)
         dev = abs(rho_new - rho) - params.tau_rho * rho
         trace.append(("recompute", len(order), dev / max(rho, 1e-300)))
-        if abs(rho_new - rho) > params.tau_rho * rho:                 # R7
+        recomputed = abs(rho_new - rho) > params.tau_rho * rho
+        if recomputed:                                                 # R7
             rho = rho_new
-            p = probabilities(t, rho, d, params.beta_mode, table)
+            p = probabilities(t, rho, d, params.beta_mode, table, params.p0_reading)
         r = p[0] + p[1:][scanned[1:]].sum()
-    return dict(dist=R.dist, ids=R.ids, scanned=order, r=float(r), trace=trace)
+        steps.append(dict(pos=int(best), rho=rho, recomputed=bool(recomputed), p=p.copy(), r=float(r)))
+    return dict(dist=R.dist, ids=R.ids, scanned=order, r=float(r), trace=trace, steps=steps)
 
 
 def root_candidates(q, top_level, f):

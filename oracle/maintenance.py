@@ -234,13 +234,17 @@ def nearest(C, live, x, count, exclude=None):
     return [int(cand[i]) for i in order[:count]]
 
 
-def maintain_level(level, A, prm, level_no, parent_of=None):
+def maintain_level(level, A, prm, level_no, parent_of=None, detail=None):
     """One estimate / verify / commit pass over one level (Sec. 4 "Decision Workflow").
 
     level      kmeans.Level (centroids, vectors, ids), modified in place
     A          access frequency per partition (hits / |W|)
     parent_of  for level 0 of a two-level index: the parent of every leaf,
                extended and compacted together with the leaves
+    detail     optional list; every verify appends a dict with the action's
+               kind, partition, estimate, exact delta and decision, plus the
+               children's sizes (split) or, per receiver m, (Delta s_m,
+               Delta A_m) (merge, M5)
     Returns (log, keep): the actions taken and the old index of every
     surviving partition, in the new order.
 
@@ -293,6 +297,8 @@ def maintain_level(level, A, prm, level_no, parent_of=None):
             d = delta_split_exact(lam(n_live + 1) - lam(n_live), a, lam(s), alpha * a, lam(sL), alpha * a, lam(sR))
             ok = decide(d, tau)
             log.append(("split", j, e, d, ok))
+            if detail is not None:
+                detail.append(dict(kind="split", j=j, estimate=e, delta=d, ok=ok, sizes=(sL, sR)))
             if not ok:
                 continue
             jn = len(C)
@@ -330,6 +336,9 @@ def maintain_level(level, A, prm, level_no, parent_of=None):
             d = delta_merge_exact(lam(n_live - 1) - lam(n_live), a, lam(s), rec)
             ok = decide(d, tau)
             log.append(("merge", j, e, d, ok))
+            if detail is not None:
+                detail.append(dict(kind="merge", j=j, estimate=e, delta=d, ok=ok,
+                                   receivers={m: (len(rs), a * len(rs) / s) for m, rs in sorted(recv.items())}))
             if not ok:
                 continue
             for m, rs in sorted(recv.items()):
