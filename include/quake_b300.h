@@ -20,6 +20,7 @@
  *  - Supported dimensions: 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024.
  *  - No C++ exception crosses the ABI.  A failing call returns a non-zero
  *    qk_status and leaves a message for qk_last_error() (thread-local).
+ *  - Device buffers must be memory of the current GPU (or managed memory).
  *  - Calls on one index are not thread-safe; use one index per host thread or
  *    serialise the calls.  Searches with device buffers may be in flight on up
  *    to 16 streams at once; insert, delete, maintain and build must not overlap
@@ -408,19 +409,28 @@ qk_status qk_profile_scan(const qk_config* cfg, int32_t k, const int64_t* sizes,
  * exists for callers that must not allocate device memory while they run
  * (a serving loop that cannot afford the device-wide synchronisation of
  * cudaMalloc/cudaFree, a process whose custom allocator owns all free
- * memory, an embedder with a fixed device footprint).  It computes exactly
- * what qk_kmeans_step computes, but allocates nothing: no cudaMalloc, no
- * cudaFree, no allocating library routine.
+ * memory, an embedder with a fixed device footprint).  It allocates nothing:
+ * no cudaMalloc, no cudaFree, no allocating library routine.
  *
- *  - Every buffer must be device memory (host pointers -> QK_ERR_ARG):
- *    x (n x d), c (K x d) in; c_new (K x d), assign[n], counts[K] out, all
- *    required.  c_new may be the same buffer as c.
+ *  - What it computes: one Lloyd step with the exact FP32 assignment (every
+ *    point to its nearest centroid by direct differences, ties to the lower
+ *    index) and FP64 member sums.  qk_kmeans_step assigns through tensor-core
+ *    scoring when K >= 32 and d % 32 == 0, keeping a short candidate list that
+ *    it re-checks exactly in FP32; the two agree whenever that list contains
+ *    the nearest centroid.  Centroids then agree to within the summation
+ *    order of the FP64 sums (a few FP32 ulp at most).
+ *  - Every buffer must be device memory of the current GPU, or managed
+ *    memory: x (n x d), c (K x d) in; c_new (K x d), assign[n], counts[K] out,
+ *    all required.  Host memory and another GPU's memory are refused
+ *    (QK_ERR_ARG).  c_new may be the same buffer as c.
  *  - Its only scratch, the FP64 per-cluster sums, lives in a fixed 8 MiB
- *    array inside the library that every GPU loading the library keeps until
- *    the process exits.  K * d may not exceed 1,048,576 (QK_ERR_ARG otherwise).
- *  - The first call on a device looks up the array's device address (once per
- *    device, with that device current); make that first call before any
- *    stream capture.
+ *    array inside the library.  K * d may not exceed 1,048,576 (QK_ERR_ARG
+ *    otherwise).  CUDA loads the array's module lazily: the first call on a
+ *    GPU loads it and looks up its device address, and the GPU then keeps the
+ *    8 MiB until the process exits.  Make that first call at start-up: before
+ *    handing the GPU's free memory to another allocator, and before any
+ *    stream capture.  After a cudaDeviceReset the next call looks the address
+ *    up again.
  *  - All calls share the one array and each call clears the sums it uses
  *    before accumulating.  Calls that overlap on the GPU (different streams,
  *    or different host threads, at the same time) race on it: serialise them.

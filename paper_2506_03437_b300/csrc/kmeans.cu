@@ -126,8 +126,10 @@ __global__ void kmeans_accumulate_kernel(const float* __restrict__ X, int64_t n,
   }
 }
 
+// C_new may be the same buffer as C_prev (each element is read, then written,
+// by one thread), so those two are not marked __restrict__.
 __global__ void kmeans_finalize_kernel(const double* __restrict__ sums, const int32_t* __restrict__ counts,
-                                       const float* __restrict__ C_prev, float* __restrict__ C_new, int K, int d) {
+                                       const float* C_prev, float* C_new, int K, int d) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)K * d) return;
   int c = (int)(e / d);

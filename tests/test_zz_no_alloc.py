@@ -58,6 +58,25 @@ def test_noalloc_step_matches_regular_step_twice():
         np.testing.assert_array_max_ulp(cn1, cn0, maxulp=2)
 
 
+def test_noalloc_step_in_place_matches_regular_step():
+    """c_new may be the same buffer as c: the step then updates c in place."""
+    import torch
+    from paper_2506_03437_b300 import _lib as L
+    d, K, n = 64, 100, 20_000
+    X, _, _ = synth.plain_ivf(seed=503, n=n, d=d, n_comp=K // 2, sigma=0.5, nq=1)
+    C = X[np.random.default_rng(3).choice(n, K, replace=False)].copy()
+    cn0, a0, cnt0 = regular_step(L, X, C)
+    xd, cd = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+    a = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(K, dtype=torch.int32, device="cuda")
+    L.check(L.lib.qk_kmeans_step_noalloc(xd.data_ptr(), n, d, cd.data_ptr(), K, cd.data_ptr(), a.data_ptr(),
+                                         cnt.data_ptr(), None))
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy(), a0)
+    assert np.array_equal(cnt.cpu().numpy(), cnt0)
+    np.testing.assert_array_max_ulp(cd.cpu().numpy(), cn0, maxulp=2)
+
+
 def test_noalloc_step_rejects_oversize_and_host_buffers():
     import torch
     from paper_2506_03437_b300 import _lib as L
