@@ -162,6 +162,22 @@ qk_status qk_search(qk_index* index, const float* q, int64_t nq, int32_t k, floa
                     float* out_recall, void* stream);
 
 /*
+ * qk_search that also reports each query's partition selection: the
+ * partitions Algorithm 1 (Sec. 5) scanned, in the order it scanned them.
+ * out_scanned0 (nq x cap0 int32, optional) receives the leaf partitions
+ * scanned by query j in row j; out_scanned1 (nq x cap1, optional) the parent
+ * partitions scanned by the upper-level APS (all -1 for a one-level index).
+ * Entries past the number scanned, or a whole row of a refused query, are -1;
+ * a query that scanned more than cap partitions keeps the first cap.
+ * Either record may be NULL; a non-NULL record needs cap >= 1 (QK_ERR_ARG
+ * otherwise).  Host or device buffers, like every other output.
+ */
+qk_status qk_search_scanned(qk_index* index, const float* q, int64_t nq, int32_t k, float recall_target,
+                            int32_t nprobe, int64_t* out_ids, float* out_dist, int32_t* out_nprobe,
+                            float* out_recall, int32_t* out_scanned0, int32_t cap0, int32_t* out_scanned1,
+                            int32_t cap1, void* stream);
+
+/*
  * Waits for the index's work on `stream` and reports what its kernels found:
  * QK_ERR_TIMEOUT if a bounded device wait expired, QK_ERR_INTERNAL if a
  * kernel's consistency check failed (details in qk_last_error), QK_OK
@@ -174,6 +190,31 @@ qk_status qk_check(qk_index* index, void* stream);
 /* Index shape.  Any output pointer may be NULL. */
 qk_status qk_info(const qk_index* index, int64_t* n_vectors, int32_t* n_leaf, int32_t* n_parent,
                   int32_t* d);
+
+/*
+ * Index statistics: what the maintenance planner (Sec. 4) and an operator
+ * read.  Partition sizes and the access counts A_l,j of the cost model (Eq. 1)
+ * accumulate per partition (qk_get_hits returns them one by one); this call
+ * sums them, together with the arena's occupancy.  Reads the hit counters
+ * from the device (synchronous).  QK_ERR_STATE before the index is built.
+ */
+typedef struct {
+  int64_t n_vectors;          /* live vectors */
+  int32_t levels;             /* 1, or 2 with a parent level */
+  int32_t n_partitions[2];    /* leaf partitions; parent partitions (0 without) */
+  int32_t d, metric, storage;
+  int32_t min_size, max_size; /* smallest and largest leaf partition */
+  double mean_size;           /* live vectors per leaf partition */
+  int64_t arena_rows;         /* rows reserved in the leaf arena */
+  int64_t arena_used;         /* rows below the free tail: partitions' rooms and holes */
+  int64_t arena_holes;        /* rows left behind by partitions that moved to the tail */
+  int64_t arena_free;         /* rows of the free tail */
+  int64_t arena_bytes;        /* device bytes of the arena (FP32 rows, ids, low-precision copy) */
+  int64_t hits[2];            /* scanned (query, partition) pairs since the last reset, per level */
+  int64_t queries_seen;       /* queries searched since the last build or maintenance (|W|) */
+  uint64_t version;           /* changes with every build, insert, delete and maintenance commit */
+} qk_index_stats;
+qk_status qk_stats(const qk_index* index, qk_index_stats* out);
 
 /*
  * Inserts n vectors x (n x d) with new ids (Sec. 3, "Adaptive Incremental

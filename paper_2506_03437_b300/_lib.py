@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIME
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = [
     "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load",
-    "qk_search", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_export_quantized", "qk_get_hits", "qk_cap_fraction",
+    "qk_search", "qk_search_scanned", "qk_stats", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_export_quantized", "qk_get_hits", "qk_cap_fraction",
     "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain", "qk_nearest_centroids",
     "qk_search_nprobe", "qk_batch_create", "qk_batch_destroy", "qk_batch_get_tiles", "qk_batch_set_tiles",
     "qk_batch_search", "qk_batch_capture", "qk_batch_replay", "qk_batch_autotune", "qk_batch_set_timing",
@@ -69,6 +69,15 @@ class QkServerConfig(C.Structure):
                 ("maint", C.POINTER(QkMaintParams))]
 
 
+class QkIndexStats(C.Structure):
+    _fields_ = [("n_vectors", C.c_int64), ("levels", C.c_int32), ("n_partitions", C.c_int32 * 2),
+                ("d", C.c_int32), ("metric", C.c_int32), ("storage", C.c_int32),
+                ("min_size", C.c_int32), ("max_size", C.c_int32), ("mean_size", C.c_double),
+                ("arena_rows", C.c_int64), ("arena_used", C.c_int64), ("arena_holes", C.c_int64),
+                ("arena_free", C.c_int64), ("arena_bytes", C.c_int64), ("hits", C.c_int64 * 2),
+                ("queries_seen", C.c_int64), ("version", C.c_uint64)]
+
+
 class QkServerStats(C.Structure):
     _fields_ = [("searches", C.c_int64), ("inserts", C.c_int64), ("deletes", C.c_int64), ("batches", C.c_int64),
                 ("update_groups", C.c_int64), ("maintenance_passes", C.c_int64), ("update_s", C.c_double),
@@ -94,6 +103,8 @@ def _load():
         "qk_build": (i32, [vp, vp, vp, i64, vp]),
         "qk_load": (i32, [vp, vp, vp, i64, vp, vp, vp, vp, vp]),
         "qk_search": (i32, [vp, vp, i64, i32, f32, i32, vp, vp, vp, vp, vp]),
+        "qk_search_scanned": (i32, [vp, vp, i64, i32, f32, i32, vp, vp, vp, vp, vp, i32, vp, i32, vp]),
+        "qk_stats": (i32, [vp, C.POINTER(QkIndexStats)]),
         "qk_check": (i32, [vp, vp]),
         "qk_info": (i32, [vp, vp, vp, vp, vp]),
         "qk_insert": (i32, [vp, vp, vp, i64, vp]),

@@ -751,12 +751,19 @@ qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, c
 // mode one nprobe per query, nprobe then being their maximum.
 static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
                              const int32_t* nprobe_q, int64_t* out_ids, float* out_dist, int32_t* out_nprobe,
-                             float* out_recall, void* stream) {
+                             float* out_recall, void* stream, int32_t* scan0 = nullptr, int32_t cap0 = 0,
+                             int32_t* scan1 = nullptr, int32_t cap1 = 0) {
   QK_TRY(check_ready(ix));
   if (nq < 0 || k < 1 || k > 1024 || (nq > 0 && (!q || !out_ids || !out_dist))) {
     set_error("invalid search arguments");
     return QK_ERR_ARG;
   }
+  if ((scan0 && cap0 < 1) || (scan1 && cap1 < 1)) {
+    set_error("a scanned-partition record needs a capacity >= 1");
+    return QK_ERR_ARG;
+  }
+  if (!scan0) cap0 = 0;
+  if (!scan1) cap1 = 0;
   if (!(recall_target > 0.f) && nprobe < 1) {
     set_error("fixed-nprobe search needs nprobe >= 1");
     return QK_ERR_ARG;
@@ -769,15 +776,18 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   const bool ids_dev = is_device_ptr(out_ids), dist_dev = is_device_ptr(out_dist);
   const bool np_dev = !out_nprobe || is_device_ptr(out_nprobe);
   const bool rc_dev = !out_recall || is_device_ptr(out_recall);
-  const bool all_dev = q_dev && ids_dev && dist_dev && np_dev && rc_dev;
+  const bool s0_dev = !scan0 || is_device_ptr(scan0);
+  const bool s1_dev = !scan1 || is_device_ptr(scan1);
+  const bool all_dev = q_dev && ids_dev && dist_dev && np_dev && rc_dev && s0_dev && s1_dev;
   // staging for host buffers
   const size_t bq = sizeof(float) * (size_t)nq * d;
   const size_t bi = sizeof(int64_t) * (size_t)nq * k, bd = sizeof(float) * (size_t)nq * k;
   const size_t bn = sizeof(int32_t) * (size_t)nq, br = sizeof(float) * (size_t)nq;
+  const size_t bs0 = sizeof(int32_t) * (size_t)nq * cap0, bs1 = sizeof(int32_t) * (size_t)nq * cap1;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   if (!all_dev) {
     QK_TRY(ensure(ix->stage_in, al(bq)));
-    QK_TRY(ensure(ix->stage_out, al(bi) + al(bd) + al(bn) + al(br)));
+    QK_TRY(ensure(ix->stage_out, al(bi) + al(bd) + al(bn) + al(br) + al(bs0) + al(bs1)));
   }
   unsigned char* so = static_cast<unsigned char*>(ix->stage_out.p);
   const float* dq = q;
@@ -789,6 +799,9 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   float* ddist = dist_dev ? out_dist : reinterpret_cast<float*>(so + al(bi));
   int32_t* dnp = np_dev ? out_nprobe : reinterpret_cast<int32_t*>(so + al(bi) + al(bd));
   float* drc = rc_dev ? out_recall : reinterpret_cast<float*>(so + al(bi) + al(bd) + al(bn));
+  const size_t o_s0 = al(bi) + al(bd) + al(bn) + al(br);
+  int32_t* ds0 = s0_dev ? scan0 : reinterpret_cast<int32_t*>(so + o_s0);
+  int32_t* ds1 = s1_dev ? scan1 : reinterpret_cast<int32_t*>(so + o_s0 + al(bs0));
 
   SearchArgs a;
   a.Q = dq;
@@ -831,6 +844,10 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   a.out_recall = out_recall ? drc : nullptr;
   a.hits0 = ix->hits0;
   a.hits1 = ix->hits1;
+  a.scan0 = scan0 ? ds0 : nullptr;
+  a.scan_cap0 = cap0;
+  a.scan1 = scan1 ? ds1 : nullptr;
+  a.scan_cap1 = cap1;
   // every launch takes its own work-stealing counter, so searches on different
   // streams may be in flight together (up to kWorkSlots of them)
   a.work = ix->work + (ix->search_seq++ % kWorkSlots);
@@ -847,6 +864,8 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
     if (!dist_dev) QK_CUDA(cudaMemcpyAsync(out_dist, ddist, bd, cudaMemcpyDeviceToHost, s));
     if (!np_dev) QK_CUDA(cudaMemcpyAsync(out_nprobe, dnp, bn, cudaMemcpyDeviceToHost, s));
     if (!rc_dev) QK_CUDA(cudaMemcpyAsync(out_recall, drc, br, cudaMemcpyDeviceToHost, s));
+    if (!s0_dev) QK_CUDA(cudaMemcpyAsync(scan0, ds0, bs0, cudaMemcpyDeviceToHost, s));
+    if (!s1_dev) QK_CUDA(cudaMemcpyAsync(scan1, ds1, bs1, cudaMemcpyDeviceToHost, s));
     const qk_status st = read_device_status(ix, s);
     tr.mark("results");
     return st;
@@ -858,6 +877,15 @@ qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float r
                     int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall, void* stream) {
   QK_GUARD_BEGIN
   return search_impl(ix, q, nq, k, recall_target, nprobe, nullptr, out_ids, out_dist, out_nprobe, out_recall, stream);
+  QK_GUARD_END
+}
+
+qk_status qk_search_scanned(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
+                            int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall,
+                            int32_t* out_scanned0, int32_t cap0, int32_t* out_scanned1, int32_t cap1, void* stream) {
+  QK_GUARD_BEGIN
+  return search_impl(ix, q, nq, k, recall_target, nprobe, nullptr, out_ids, out_dist, out_nprobe, out_recall, stream,
+                     out_scanned0, cap0, out_scanned1, cap1);
   QK_GUARD_END
 }
 
@@ -1078,6 +1106,47 @@ qk_status qk_info(const qk_index* ix, int64_t* n_vectors, int32_t* n_leaf, int32
   if (n_leaf) *n_leaf = ix->ready ? ix->n_leaf : ix->cfg.n_leaf;
   if (n_parent) *n_parent = ix->ready ? ix->n_parent : ix->cfg.n_parent;
   if (d) *d = ix->cfg.d;
+  return QK_OK;
+  QK_GUARD_END
+}
+
+qk_status qk_stats(const qk_index* ix, qk_index_stats* out) {
+  QK_GUARD_BEGIN
+  QK_TRY(check_ready(ix));
+  if (!out) {
+    set_error("null output");
+    return QK_ERR_ARG;
+  }
+  qk_index_stats st{};
+  st.n_vectors = ix->n;
+  st.levels = ix->n_parent > 0 ? 2 : 1;
+  st.n_partitions[0] = ix->n_leaf;
+  st.n_partitions[1] = ix->n_parent;
+  st.d = ix->cfg.d;
+  st.metric = ix->cfg.metric;
+  st.storage = ix->cfg.storage;
+  if (!ix->h_size0.empty()) {
+    st.min_size = *std::min_element(ix->h_size0.begin(), ix->h_size0.end());
+    st.max_size = *std::max_element(ix->h_size0.begin(), ix->h_size0.end());
+  }
+  st.mean_size = ix->n_leaf > 0 ? (double)ix->n / ix->n_leaf : 0.0;
+  st.arena_rows = ix->cap0;
+  st.arena_used = ix->used0;
+  st.arena_holes = ix->holes0;
+  st.arena_free = ix->cap0 - ix->used0;
+  const int64_t lp = ix->cfg.storage == QK_STORE_BF16 ? 2 : ix->cfg.storage == QK_STORE_FP8 ? 1 : 0;
+  st.arena_bytes = ix->cap0 * ((int64_t)ix->cfg.d * (4 + lp) + 8);
+  for (int l = 0; l < 2; ++l) {
+    const unsigned long long* src = l == 0 ? ix->hits0 : ix->hits1;
+    const int32_t n = l == 0 ? ix->n_leaf : ix->n_parent;
+    if (!src || n <= 0) continue;
+    std::vector<unsigned long long> h((size_t)n);
+    QK_CUDA(cudaMemcpy(h.data(), src, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost));
+    for (unsigned long long v : h) st.hits[l] += (int64_t)v;
+  }
+  st.queries_seen = ix->queries_seen.load();
+  st.version = ix->version;
+  *out = st;
   return QK_OK;
   QK_GUARD_END
 }

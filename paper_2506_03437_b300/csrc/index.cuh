@@ -71,6 +71,10 @@ struct SearchArgs {
   int32_t* status = nullptr;     // device status word
   int64_t* diag = nullptr;       // first failure: code, query, details
   int64_t* wait_stats = nullptr; // longest bulk-copy wait of the launch (cycles), optional
+  int32_t* scan0 = nullptr;      // optional: level-0 partitions scanned per query, nq x scan_cap0, -1 padded
+  int32_t scan_cap0 = 0;
+  int32_t* scan1 = nullptr;      // optional: level-1 partitions scanned per query, nq x scan_cap1, -1 padded
+  int32_t scan_cap1 = 0;
   int32_t kcap = 16;             // capacity of the result set (>= every k used)
   int32_t mcap = 16;             // capacity of the candidate list
 };

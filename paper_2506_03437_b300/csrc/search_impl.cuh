@@ -150,6 +150,8 @@ struct Block {
   float qn;                      // ||q||^2 (inner product radius)
   long long max_wait;   // longest tile wait of this thread, in SM cycles
   bool aborted;         // a tile wait expired (uniform across the CTA)
+  int32_t* rec;         // scanned-partition record of the current query and level, or NULL
+  int rec_cap, rec_n;   // its length; partitions scanned so far (thread 0)
 
   // Records the first failure of the launch (code, query, details) and keeps going.
   __device__ void report(int code, int64_t a0, int64_t a1, int64_t a2) {
@@ -510,7 +512,25 @@ struct Block {
     if (tid == 0) {
       csc[pos] = 1;
       if (hits) atomicAdd(&hits[part], 1ull);
+      if (rec && rec_n < rec_cap) rec[rec_n] = part;
+      ++rec_n;
     }
+    __syncthreads();
+  }
+
+  // Optional record of the scanned partitions (in scan order) of the current
+  // query at one level; rec_n is kept by thread 0.
+  __device__ void record_start(int32_t* row, int cap) {
+    rec = row;
+    rec_cap = cap;
+    rec_n = 0;
+  }
+  __device__ void record_finish() {
+    __syncthreads();
+    const int n = __shfl_sync(0xffffffffu, rec_n, 0);   // warp 0 learns thread 0's count
+    if (warp == 0 && rec)
+      for (int i = n + lane; i < rec_cap; i += 32) rec[i] = -1;
+    rec = nullptr;
     __syncthreads();
   }
 
@@ -779,6 +799,9 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
   b.qi = -1;
   b.max_wait = 0;
   b.aborted = false;
+  b.rec = nullptr;
+  b.rec_cap = 0;
+  b.rec_n = 0;
   b.stages = reinterpret_cast<float*>(smem + L.stages);
   b.bars = reinterpret_cast<uint64_t*>(smem + L.bars);
   b.sq = reinterpret_cast<float*>(smem + L.q);
@@ -832,6 +855,8 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
         if (args.out_nprobe) args.out_nprobe[qi] = 0;
         if (args.out_recall) args.out_recall[qi] = NAN;
       }
+      for (int i = threadIdx.x; i < args.scan_cap0 && args.scan0; i += kThreads) args.scan0[qi * args.scan_cap0 + i] = -1;
+      for (int i = threadIdx.x; i < args.scan_cap1 && args.scan1; i += kThreads) args.scan1[qi * args.scan_cap1 + i] = -1;
       __syncthreads();
       continue;
     }
@@ -847,12 +872,18 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
     int np = 0;
     if (args.L == 2) {
       // level-1 rows are leaf centroids whose id is the leaf index: x_k = cent0[id]
+      if (args.scan1) b.record_start(args.scan1 + qi * args.scan_cap1, args.scan_cap1);
       b.aps(args.lv[1], M, args.k1, args.k1, args.tau1, 0, args.hits1, 0, args.lv[0].cent, r, np);
+      if (args.scan1) b.record_finish();
       M = b.take_candidates();
+    } else if (args.scan1) {
+      for (int i = threadIdx.x; i < args.scan_cap1; i += kThreads) args.scan1[qi * args.scan_cap1 + i] = -1;
     }
     const int fixed = args.nprobe_q ? args.nprobe_q[qi] : args.fixed_nprobe;
     b.metric = args.metric;
+    if (args.scan0) b.record_start(args.scan0 + qi * args.scan_cap0, args.scan_cap0);
     b.aps(args.lv[0], M, args.k0, args.kq, args.tau0, fixed, args.hits0, args.mode0, args.lv[0].vec, r, np);
+    if (args.scan0) b.record_finish();
     if (b.aborted) break;
     if (args.mode0 != 0) b.rerank(args.lv[0].vec, args.lv[0].ids);
     int rc = sc.r_count;

@@ -110,6 +110,40 @@ class Index:
                                 L.ptr(oi), L.ptr(od), L.ptr(on), L.ptr(orr), L.stream_ptr(stream)))
         return out
 
+    def search_scanned(self, q, k, recall_target=0.9, nprobe=0, cap0=64, cap1=64, stream=None):
+        """search() plus each query's scanned partitions in scan order: returns
+        (ids, dist, nprobe, recall_estimate, scanned0 (nq x cap0), scanned1
+        (nq x cap1)), -1 padded, on the device of `q`."""
+        q = _as(q, np.float32)
+        nq = int(q.shape[0])
+        if hasattr(q, "data_ptr"):
+            import torch
+            dev = q.device
+            out = (torch.empty((nq, k), dtype=torch.int64, device=dev),
+                   torch.empty((nq, k), dtype=torch.float32, device=dev),
+                   torch.empty(nq, dtype=torch.int32, device=dev),
+                   torch.empty(nq, dtype=torch.float32, device=dev),
+                   torch.empty((nq, cap0), dtype=torch.int32, device=dev),
+                   torch.empty((nq, cap1), dtype=torch.int32, device=dev))
+        else:
+            out = (np.empty((nq, k), np.int64), np.empty((nq, k), np.float32),
+                   np.empty(nq, np.int32), np.empty(nq, np.float32),
+                   np.empty((nq, cap0), np.int32), np.empty((nq, cap1), np.int32))
+        oi, od, on, orr, s0, s1 = out
+        L.check(L.lib.qk_search_scanned(self._h, L.ptr(q), nq, int(k), float(recall_target), int(nprobe),
+                                        L.ptr(oi), L.ptr(od), L.ptr(on), L.ptr(orr), L.ptr(s0), int(cap0),
+                                        L.ptr(s1), int(cap1), L.stream_ptr(stream)))
+        return out
+
+    def stats(self):
+        """Index statistics (qk_stats) as a dict."""
+        st = L.QkIndexStats()
+        L.check(L.lib.qk_stats(self._h, C.byref(st)))
+        out = {name: getattr(st, name) for name, _ in L.QkIndexStats._fields_}
+        out["n_partitions"] = list(st.n_partitions)
+        out["hits"] = list(st.hits)
+        return out
+
     def search_nprobe(self, q, k, nprobe, out=None, stream=None):
         """Fixed-nprobe search, one nprobe per query, through the per-query kernel.
         Returns (ids, dist) on the device of `q`."""

@@ -124,6 +124,28 @@ def zipf_partitions(seed=1238, n=5_000_000, d=256, n_part=20_000, a=1.0, lo=10, 
     return X, np.arange(n, dtype=np.int64), lab, Q, nprobe
 
 
+def unit_mixture(seed=1237, n=200_000, d=768, n_comp=100, s=2.0, nq=64, chunk=1 << 16):
+    """The precision workload's recipe on the host (numpy PCG64), for sizes the
+    oracle can search: n unit-norm rows x = normalize(mu_c + (s / sqrt(d)) g)
+    around n_comp directions mu uniform on the sphere, component uniform per
+    row, and nq queries from the same mixture.  Returns FP32 (X, ids, Q)."""
+    g = rng(seed)
+    mu = g.standard_normal((n_comp, d))
+    mu /= np.linalg.norm(mu, axis=1, keepdims=True)
+    scale = s / d ** 0.5
+
+    def draw(m):
+        out = np.empty((m, d), dtype=np.float32)
+        for a in range(0, m, chunk):
+            b = min(m, a + chunk)
+            lab = g.integers(0, n_comp, size=b - a)
+            x = mu[lab] + scale * g.standard_normal((b - a, d))
+            out[a:b] = x / np.linalg.norm(x, axis=1, keepdims=True)
+        return out
+    X = draw(n)
+    return X, np.arange(n, dtype=np.int64), draw(nq)
+
+
 def unit_mixture_cuda(seed=1237, n=10_000_000, d=768, n_comp=5000, s=1.0, nq=1024, chunk=1 << 20):
     """Precision workload, generated on the GPU (torch Philox, seeded): n unit-norm rows
     x = normalize(mu_c + (s / sqrt(d)) g) around n_comp directions mu uniform on the sphere,

@@ -31,14 +31,14 @@ def test_full_size_aps_sampled_parity(storage):
     a1 = kmeans.assign(C0, C1)
     levels = kmeans.index_from_assignment(X, ids, C0, a0, C1, a1)
     ix = make_index(I, X, ids, levels, f_M_leaf=0.1, f_M_parent=0.25)
-    gi, gd, gn, gr = ix.search(torch.from_numpy(Q).cuda(), 10, recall_target=0.9)
+    out = ix.search_scanned(torch.from_numpy(Q).cuda(), 10, recall_target=0.9, cap0=100, cap1=8)
     ix.check()
-    gi, gd, gn, gr = gi.cpu().numpy(), gd.cpu().numpy(), gn.cpu().numpy(), gr.cpu().numpy()
+    out = tuple(a.cpu().numpy() for a in out)
+    gi, gd, gn, gr = out[:4]
     assert ((gi >= 0) & (gi < n)).all() and (np.diff(gd, axis=1) >= 0).all()
     sel = np.random.default_rng(0).choice(nq, 40, replace=False)
     orc = aps.search(levels, Q[sel], aps.Params(k=10, recall_target=0.9, f_M=(0.1, 0.25)))
-    n_ok, n_exc = compare_search((gi[sel], gd[sel], gn[sel], gr[sel]), orc, 10)
-    assert n_exc <= 2
+    compare_search(tuple(a[sel] for a in out), orc, 10, label="APS 1M x 128, 40 sampled queries")
     # recall of the sample against FP64 brute force
     gtD, _ = knn.knn(X, ids, Q[sel], 10, bulk=True)
     rec = knn.recall_at_k(gi[sel], exact_dist(X, Q[sel], gi[sel]), gtD, 10).mean()
