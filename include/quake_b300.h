@@ -564,6 +564,66 @@ qk_status qk_batch_autotune(qk_batch* plan, const float* q, int64_t nq, const in
 qk_status qk_batch_set_timing(qk_batch* plan, int32_t on);
 qk_status qk_batch_stage_times(qk_batch* plan, float* ms);
 
+/* ------------------------------------------------------------------------
+ * Batched Adaptive Partition Scanning: Algorithm 1 (Sec. 5) for every query
+ * of a batch, with the leaf scans of all queries grouped by partition
+ * (multi-query processing, Sec. 8), so that a partition several queries need
+ * is read from HBM once per round for all of them.
+ *
+ * Steps (all on the GPU, no host synchronisation):
+ *   1. per query: the top partition is scored and the upper level searched by
+ *      APS exactly as qk_search does; the leaf candidates S, nearest first,
+ *      and their bisector distances t_i are kept;
+ *   2. rounds: every unfinished query has asked for some of its candidates;
+ *      the (query, partition) items are grouped by partition and one
+ *      persistent scan computes every item's own exact top-k;
+ *   3. after each round one warp per query walks Algorithm 1 over what was
+ *      scanned, in the order Algorithm 1 takes the partitions (centroid order
+ *      until R holds k results, then decreasing p, with rho, the recompute
+ *      rule and r as in qk_search).  When the partition it takes next was not
+ *      scanned, the query asks for it and for those Algorithm 1 would take
+ *      after it if p stayed as it is, until r would reach the target.  Items
+ *      scanned beyond a query's stop are discarded.
+ * The results, nprobe, r and the partitions scanned therefore equal
+ * qk_search's with the same recall target.  The last of the plan's rounds
+ * (4 unless set) asks for every candidate not yet scanned, so every query
+ * finishes; unused rounds cost only their launches.
+ *
+ * Conventions: L2 metric and FP32 storage; k <= 32; q, out_ids and out_dist
+ * are 16-byte aligned device buffers, out_nprobe[nq], out_recall[nq] and
+ * out_scanned0 (nq x cap0, as qk_search_scanned) optional device buffers.
+ * Calls are stream-ordered and return before the GPU finishes; device-side
+ * errors land in the index's status word (qk_check).  A query with a NaN or
+ * infinite element is refused as in qk_search.  Access counts accumulate as
+ * in qk_search.  A plan follows inserts, deletes and maintenance by itself on
+ * the next qk_aps_batch_search; a captured graph does not (replay then returns
+ * QK_ERR_STATE).  Calls on one plan must not overlap.
+ * ------------------------------------------------------------------------ */
+typedef struct qk_aps_batch qk_aps_batch;
+
+/* A plan for batches of up to max_nq queries with k results (device workspace:
+ * per query the candidate list, its p values and R, plus one round's candidate
+ * buffer of k per item chunk). */
+qk_status qk_aps_batch_create(qk_index* index, int64_t max_nq, int32_t k, qk_aps_batch** out);
+void qk_aps_batch_destroy(qk_aps_batch* plan);
+/* Number of rounds, 1 to 16 (default 4). */
+qk_status qk_aps_batch_set_rounds(qk_aps_batch* plan, int32_t rounds);
+/* Tiles of the grouped scan (as qk_batch_set_tiles; default 2 queries per
+ * warp, tile_rows 8192 / d capped to [8, 64], chunk_rows 4096). */
+qk_status qk_aps_batch_set_tiles(qk_aps_batch* plan, const qk_batch_tiles* tiles);
+qk_status qk_aps_batch_search(qk_aps_batch* plan, const float* q, int64_t nq, float recall_target,
+                              int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall,
+                              int32_t* out_scanned0, int32_t cap0, void* stream);
+/* Runs the batch once, then records it as one CUDA graph (buffers fixed). */
+qk_status qk_aps_batch_capture(qk_aps_batch* plan, const float* q, int64_t nq, float recall_target,
+                               int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall,
+                               void* stream);
+qk_status qk_aps_batch_replay(qk_aps_batch* plan, void* stream);
+/* For the last batch (synchronous): per round, the items asked for and the
+ * items Algorithm 1 took in (the rest were scanned beyond a query's stop);
+ * arrays of the plan's round count. */
+qk_status qk_aps_batch_round_stats(qk_aps_batch* plan, int64_t* asked, int64_t* taken);
+
 /* Fixed-nprobe search with one nprobe per query through the per-query search
  * kernel (one CTA per query; the comparison point of the batched path and of
  * the per-query "oracle nprobe"): like qk_search with recall_target <= 0, but

@@ -30,7 +30,9 @@ EXPORTS = [
     "qk_batch_stage_times", "qk_maintain_prepare", "qk_maintain_commit", "qk_profile_scan", "qk_save", "qk_restore",
     "qk_server_config_default", "qk_server_create", "qk_server_destroy", "qk_server_submit_search",
     "qk_server_submit_insert", "qk_server_submit_delete", "qk_server_results", "qk_server_drain",
-    "qk_server_get_stats",
+    "qk_server_get_stats", "qk_aps_batch_create", "qk_aps_batch_destroy", "qk_aps_batch_set_rounds",
+    "qk_aps_batch_set_tiles", "qk_aps_batch_search", "qk_aps_batch_capture", "qk_aps_batch_replay",
+    "qk_aps_batch_round_stats",
 ]
 
 
@@ -144,6 +146,14 @@ def _load():
         "qk_batch_set_timing": (i32, [vp, i32]),
         "qk_batch_stage_times": (i32, [vp, vp]),
         "qk_batch_autotune": (i32, [vp, vp, i64, vp, vp, vp, i32, C.POINTER(QkBatchTiles), vp]),
+        "qk_aps_batch_create": (i32, [vp, i64, i32, C.POINTER(vp)]),
+        "qk_aps_batch_destroy": (None, [vp]),
+        "qk_aps_batch_set_rounds": (i32, [vp, i32]),
+        "qk_aps_batch_set_tiles": (i32, [vp, C.POINTER(QkBatchTiles)]),
+        "qk_aps_batch_search": (i32, [vp, vp, i64, f32, vp, vp, vp, vp, vp, i32, vp]),
+        "qk_aps_batch_capture": (i32, [vp, vp, i64, f32, vp, vp, vp, vp, vp]),
+        "qk_aps_batch_replay": (i32, [vp, vp]),
+        "qk_aps_batch_round_stats": (i32, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

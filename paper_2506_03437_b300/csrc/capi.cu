@@ -158,12 +158,6 @@ static qk_status ensure(Buffer& b, size_t bytes) {
   return QK_OK;
 }
 
-static int32_t n_candidates(double f, int32_t n) {
-  double m = std::ceil(f * (double)n);
-  if (m < 1) m = 1;
-  if (m > n) m = n;
-  return (int32_t)m;
-}
 
 // Rows reserved per partition: its size plus room for inserts.
 static int64_t capacity_for(int64_t size) { return size + std::max<int64_t>(16, size / 4); }
@@ -578,6 +572,57 @@ static qk_status read_device_status(qk_index* ix, cudaStream_t s) {
   return QK_ERR_INTERNAL;
 }
 
+
+int32_t n_candidates(double f, int32_t n) {
+  double m = std::ceil(f * (double)n);
+  if (m < 1) m = 1;
+  if (m > n) m = n;
+  return (int32_t)m;
+}
+
+void base_search_args(qk_index* ix, int32_t k, float recall_target, int32_t nprobe, SearchArgs& a) {
+  a.d = ix->cfg.d;
+  a.metric = ix->cfg.metric;
+  a.L = ix->n_parent > 0 ? 2 : 1;
+  a.lv[0] = DevLevel{ix->vec0, ix->ids0, ix->off0, ix->size0, ix->cent0, ix->n_leaf};
+  a.lv[1] = DevLevel{ix->vec1, ix->ids1, ix->off1, ix->size1, ix->cent1, ix->n_parent};
+  const bool fixed = !(recall_target > 0.f);
+  a.fixed_nprobe = fixed ? nprobe : 0;
+  if (a.L == 1) {
+    a.root = ix->cent0;
+    a.n_root = ix->n_leaf;
+    a.M_root = fixed ? std::min(nprobe, ix->n_leaf) : n_candidates(ix->cfg.f_M_leaf, ix->n_leaf);
+    a.k1 = 0;
+  } else {
+    a.root = ix->cent1;
+    a.n_root = ix->n_parent;
+    a.M_root = n_candidates(ix->cfg.f_M_parent, ix->n_parent);
+    a.k1 = n_candidates(ix->cfg.f_M_leaf, ix->n_leaf);
+  }
+  const int storage = ix->cfg.storage;
+  a.kq = k;
+  a.k0 = storage == QK_STORE_F32 ? k : std::min(1024, k * std::max(1, ix->cfg.rerank));
+  a.mode0 = storage == QK_STORE_BF16 ? 2 : storage == QK_STORE_FP8 ? 3 : (ix->cfg.metric == QK_METRIC_IP ? 1 : 0);
+  a.lp_vec = ix->lp0;
+  a.lp_scale = ix->lp_scale0;
+  a.tau0 = recall_target;
+  a.tau1 = ix->cfg.upper_recall;
+  a.tau_rho = ix->cfg.tau_rho;
+  a.beta_mode = ix->cfg.beta_mode;
+  a.beta_table = ix->beta_table;
+  a.beta_a = ix->beta_a;
+  a.beta_lnB = ix->beta_lnB;
+  a.hits0 = ix->hits0;
+  a.hits1 = ix->hits1;
+  // every launch takes its own work-stealing counter, so searches on different
+  // streams may be in flight together (up to kWorkSlots of them)
+  a.work = ix->work + (ix->search_seq++ % kWorkSlots);
+  a.status = ix->status;
+  a.diag = ix->diag;
+  a.wait_stats = ix->diag + 8;
+  a.kcap = std::max({a.k0, a.k1, a.M_root});
+  a.mcap = std::max({a.M_root, a.k1, 1});
+}
 }  // namespace qk
 
 using namespace qk;
@@ -747,6 +792,7 @@ qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, c
   QK_GUARD_END
 }
 
+
 // The search of qk_search; nprobe_q (device, optional) gives fixed-nprobe
 // mode one nprobe per query, nprobe then being their maximum.
 static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
@@ -804,58 +850,18 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   int32_t* ds1 = s1_dev ? scan1 : reinterpret_cast<int32_t*>(so + o_s0 + al(bs0));
 
   SearchArgs a;
+  base_search_args(ix, k, recall_target, nprobe, a);
   a.Q = dq;
   a.nq = nq;
-  a.d = d;
-  a.metric = ix->cfg.metric;
-  a.L = ix->n_parent > 0 ? 2 : 1;
-  a.lv[0] = DevLevel{ix->vec0, ix->ids0, ix->off0, ix->size0, ix->cent0, ix->n_leaf};
-  a.lv[1] = DevLevel{ix->vec1, ix->ids1, ix->off1, ix->size1, ix->cent1, ix->n_parent};
-  const bool fixed = !(recall_target > 0.f);
-  a.fixed_nprobe = fixed ? nprobe : 0;
-  a.nprobe_q = fixed ? nprobe_q : nullptr;
-  if (a.L == 1) {
-    a.root = ix->cent0;
-    a.n_root = ix->n_leaf;
-    a.M_root = fixed ? std::min(nprobe, ix->n_leaf) : n_candidates(ix->cfg.f_M_leaf, ix->n_leaf);
-    a.k1 = 0;
-  } else {
-    a.root = ix->cent1;
-    a.n_root = ix->n_parent;
-    a.M_root = n_candidates(ix->cfg.f_M_parent, ix->n_parent);
-    a.k1 = n_candidates(ix->cfg.f_M_leaf, ix->n_leaf);
-  }
-  const int storage = ix->cfg.storage;
-  a.kq = k;
-  a.k0 = storage == QK_STORE_F32 ? k : std::min(1024, k * std::max(1, ix->cfg.rerank));
-  a.mode0 = storage == QK_STORE_BF16 ? 2 : storage == QK_STORE_FP8 ? 3 : (ix->cfg.metric == QK_METRIC_IP ? 1 : 0);
-  a.lp_vec = ix->lp0;
-  a.lp_scale = ix->lp_scale0;
-  a.tau0 = recall_target;
-  a.tau1 = ix->cfg.upper_recall;
-  a.tau_rho = ix->cfg.tau_rho;
-  a.beta_mode = ix->cfg.beta_mode;
-  a.beta_table = ix->beta_table;
-  a.beta_a = ix->beta_a;
-  a.beta_lnB = ix->beta_lnB;
+  a.nprobe_q = a.fixed_nprobe > 0 ? nprobe_q : nullptr;
   a.out_ids = dids;
   a.out_dist = ddist;
   a.out_nprobe = out_nprobe ? dnp : nullptr;
   a.out_recall = out_recall ? drc : nullptr;
-  a.hits0 = ix->hits0;
-  a.hits1 = ix->hits1;
   a.scan0 = scan0 ? ds0 : nullptr;
   a.scan_cap0 = cap0;
   a.scan1 = scan1 ? ds1 : nullptr;
   a.scan_cap1 = cap1;
-  // every launch takes its own work-stealing counter, so searches on different
-  // streams may be in flight together (up to kWorkSlots of them)
-  a.work = ix->work + (ix->search_seq++ % kWorkSlots);
-  a.status = ix->status;
-  a.diag = ix->diag;
-  a.wait_stats = ix->diag + 8;
-  a.kcap = std::max({a.k0, a.k1, a.M_root});
-  a.mcap = std::max({a.M_root, a.k1, 1});
   QK_TRY(launch_search(a, s));
   tr.mark("launch");
   ix->queries_seen += nq;

@@ -75,4 +75,21 @@ __host__ __device__ inline double cap_fraction_table(double t, double rho, const
   return 0.5 * (lo + w * (hi - lo));
 }
 
+// The cap fraction as the search kernels evaluate it during Algorithm 1:
+// inv = 1 / rho computed once per recompute by the caller; exact selects the
+// continued fraction, else the table.  Every kernel that estimates p uses
+// this one function, so they take identical decisions.
+__device__ inline double cap_u(double t, double rho, double inv, bool exact, const double* table, double a,
+                               double lnB) {
+  if (!(rho > 0.0 && t < rho)) return 0.0;
+  if (exact) return cap_fraction_exact(t, rho, a, lnB);
+  const double sc = t * inv;
+  const double x = 1.0 - sc * sc;
+  const double f = x * (kBetaTablePoints - 1);
+  int j = (int)f;
+  if (j > kBetaTablePoints - 2) j = kBetaTablePoints - 2;
+  const double lo = table[j], hi = table[j + 1];
+  return 0.5 * (lo + (f - j) * (hi - lo));
+}
+
 }  // namespace qk

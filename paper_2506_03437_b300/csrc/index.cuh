@@ -75,6 +75,10 @@ struct SearchArgs {
   int32_t scan_cap0 = 0;
   int32_t* scan1 = nullptr;      // optional: level-1 partitions scanned per query, nq x scan_cap1, -1 padded
   int32_t scan_cap1 = 0;
+  int32_t* xs_M = nullptr;       // batched APS: per query, leaf candidates exported (-1: refused query)
+  int32_t* xs_cand = nullptr;    // nq x xs_mcap leaf candidate partitions, nearest first
+  double* xs_t = nullptr;        // nq x xs_mcap their bisector distances t_i
+  int32_t xs_mcap = 0;
   int32_t kcap = 16;             // capacity of the result set (>= every k used)
   int32_t mcap = 16;             // capacity of the candidate list
 };
@@ -154,4 +158,10 @@ bool is_device_ptr(const void* p);
 void swap_structure(qk_index* a, qk_index* b);
 void release_structure(qk_index* ix);
 qk_status assign_nearest(const float* X, int64_t n, int d, const float* C, int K, int32_t* assign, cudaStream_t s);
+// M = ceil(f n) in double precision, clamped to [1, n] (the candidate count of a level).
+int32_t n_candidates(double f, int32_t n);
+// The search kernel's arguments that follow from the index and the call's k,
+// recall target and fixed nprobe (queries, outputs and records not set).
+void base_search_args(qk_index* ix, int32_t k, float recall_target, int32_t nprobe, SearchArgs& a);
+qk_status launch_search(const SearchArgs& a, cudaStream_t stream);
 }  // namespace qk

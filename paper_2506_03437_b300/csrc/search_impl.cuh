@@ -568,21 +568,7 @@ struct Block {
     double su = 0.0, pr = 1.0;
     const double inv = rho > 0.0 ? 1.0 / rho : 0.0;
     for (int i = 1 + lane; i < M; i += 32) {
-      double u = 0.0;
-      double t = ct[i];
-      if (rho > 0.0 && t < rho) {
-        if (beta_mode == QK_BETA_EXACT) {
-          u = cap_fraction_exact(t, rho, beta_a, beta_lnB);
-        } else {
-          double sc = t * inv;
-          double x = 1.0 - sc * sc;
-          double f = x * (kBetaTablePoints - 1);
-          int j = (int)f;
-          if (j > kBetaTablePoints - 2) j = kBetaTablePoints - 2;
-          double lo = beta_table[j], hi = beta_table[j + 1];
-          u = 0.5 * (lo + (f - j) * (hi - lo));
-        }
-      }
+      const double u = cap_u(ct[i], rho, inv, beta_mode == QK_BETA_EXACT, beta_table, beta_a, beta_lnB);
       cp[i] = u;
       su += u;
       pr *= 1.0 - u;
@@ -857,6 +843,7 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
       }
       for (int i = threadIdx.x; i < args.scan_cap0 && args.scan0; i += kThreads) args.scan0[qi * args.scan_cap0 + i] = -1;
       for (int i = threadIdx.x; i < args.scan_cap1 && args.scan1; i += kThreads) args.scan1[qi * args.scan_cap1 + i] = -1;
+      if (threadIdx.x == 0 && args.xs_M) args.xs_M[qi] = -1;
       __syncthreads();
       continue;
     }
@@ -878,6 +865,19 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
       M = b.take_candidates();
     } else if (args.scan1) {
       for (int i = threadIdx.x; i < args.scan_cap1; i += kThreads) args.scan1[qi * args.scan_cap1 + i] = -1;
+    }
+    if (args.xs_M) {
+      // batched APS: export S_0 with its t_i; the leaf level is scanned in
+      // rounds by the grouped scan and replayed per query elsewhere
+      if (b.aborted) break;
+      b.bisector(args.lv[0], M);
+      for (int i = threadIdx.x; i < M; i += kThreads) {
+        args.xs_cand[qi * args.xs_mcap + i] = b.cpart[i];
+        args.xs_t[qi * args.xs_mcap + i] = b.ct[i];
+      }
+      if (threadIdx.x == 0) args.xs_M[qi] = M;
+      __syncthreads();
+      continue;
     }
     const int fixed = args.nprobe_q ? args.nprobe_q[qi] : args.fixed_nprobe;
     b.metric = args.metric;

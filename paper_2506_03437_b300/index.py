@@ -376,3 +376,76 @@ class BatchPlan:
         L.check(L.lib.qk_batch_autotune(self._h, L.ptr(q), int(q.shape[0]), L.ptr(nprobe), L.ptr(out[0]),
                                         L.ptr(out[1]), int(reps), C.byref(t), L.stream_ptr(stream)))
         return (t.queries_per_warp, t.tile_rows, t.chunk_rows)
+
+
+class ApsBatchPlan:
+    """Workspace of the batched APS search of one index (qk_aps_batch_* in
+    include/quake_b300.h): Algorithm 1 for every query of a batch, with the
+    leaf scans grouped by partition.  Every array is a CUDA tensor."""
+
+    def __init__(self, index, max_nq, k, rounds=None):
+        h = C.c_void_p()
+        L.check(L.lib.qk_aps_batch_create(index._h, int(max_nq), int(k), C.byref(h)))
+        self._h, self.index, self.k = h, index, int(k)
+        self.rounds = 4
+        if rounds is not None:
+            self.set_rounds(rounds)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib.qk_aps_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_rounds(self, rounds):
+        L.check(L.lib.qk_aps_batch_set_rounds(self._h, int(rounds)))
+        self.rounds = int(rounds)
+
+    def set_tiles(self, queries_per_warp, tile_rows, chunk_rows):
+        t = L.QkBatchTiles(int(queries_per_warp), int(tile_rows), int(chunk_rows))
+        L.check(L.lib.qk_aps_batch_set_tiles(self._h, C.byref(t)))
+
+    def outputs(self, q, cap0=0):
+        """(ids, dist, nprobe, recall_estimate[, scanned0]) CUDA tensors for q's batch."""
+        import torch
+        nq, dev = int(q.shape[0]), q.device
+        out = (torch.empty((nq, self.k), dtype=torch.int64, device=dev),
+               torch.empty((nq, self.k), dtype=torch.float32, device=dev),
+               torch.empty(nq, dtype=torch.int32, device=dev),
+               torch.empty(nq, dtype=torch.float32, device=dev))
+        if cap0:
+            out = out + (torch.empty((nq, cap0), dtype=torch.int32, device=dev),)
+        return out
+
+    def search(self, q, recall_target=0.9, out=None, cap0=0, stream=None):
+        """Returns (ids, dist, nprobe, recall_estimate[, scanned0]) of the batch."""
+        q = _as(q, np.float32)
+        out = self.outputs(q, cap0) if out is None else out
+        s0 = out[4] if len(out) > 4 else None
+        L.check(L.lib.qk_aps_batch_search(self._h, L.ptr(q), int(q.shape[0]), float(recall_target),
+                                          L.ptr(out[0]), L.ptr(out[1]), L.ptr(out[2]), L.ptr(out[3]),
+                                          L.ptr(s0), int(s0.shape[1]) if s0 is not None else 0,
+                                          L.stream_ptr(stream)))
+        return out
+
+    def capture(self, q, recall_target, out, stream):
+        """Records one batch over these buffers as a CUDA graph on `stream`."""
+        q = _as(q, np.float32)
+        L.check(L.lib.qk_aps_batch_capture(self._h, L.ptr(q), int(q.shape[0]), float(recall_target),
+                                           L.ptr(out[0]), L.ptr(out[1]), L.ptr(out[2]), L.ptr(out[3]),
+                                           L.stream_ptr(stream)))
+
+    def replay(self, stream):
+        L.check(L.lib.qk_aps_batch_replay(self._h, L.stream_ptr(stream)))
+
+    def round_stats(self):
+        """Per round of the last batch: (items asked for, items Algorithm 1 took in)."""
+        a = np.zeros(self.rounds, np.int64)
+        t = np.zeros(self.rounds, np.int64)
+        L.check(L.lib.qk_aps_batch_round_stats(self._h, L.ptr(a), L.ptr(t)))
+        return a, t

@@ -69,7 +69,8 @@ def compare_search(gpu, orc, k, check_r=True, label="", bound=True):
 
     gpu is (ids, dist, nprobe, r) or, from Index.search_scanned, (ids, dist,
     nprobe, r, scanned0, scanned1): then the partitions scanned at each level,
-    in order, are compared with the oracle's as well.  With bound=True the
+    in order, are compared with the oracle's as well (a level given as None
+    is not compared).  With bound=True the
     excused queries may be at most max_excused(nq)."""
     gi, gd, gn, gr = gpu[:4]
     scanned = gpu[4:6] if len(gpu) >= 6 else None
@@ -84,6 +85,8 @@ def compare_search(gpu, orc, k, check_r=True, label="", bound=True):
         sel_ok = True
         if scanned is not None:
             for lv, rec in enumerate(scanned):
+                if rec is None:
+                    continue
                 row = np.asarray(rec[j])
                 got = [int(x) for x in row if x >= 0]
                 want = orc["scanned"][lv][j] if lv < len(orc["scanned"]) else None
