@@ -249,14 +249,49 @@ def run_ours(args):
 
     sizes0, _, _ = ix.export_level(0)
     sizes1, _, _ = ix.export_level(1)
+    # the per-query kernel (one CTA per query runs Algorithm 1 alone), for comparison
     out = (oi, od, on, orr)
     for _ in range(args.warmup):
         ix.search(Qd, K, recall_target=tau, out=out, stream=stream)
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for a_, b_ in pev:
+        a_.record(stream)
+        ix.search(Qd, K, recall_target=tau, out=out, stream=stream)
+        b_.record(stream)
+    torch.cuda.synchronize()
+    pq_s = sum(a_.elapsed_time(b_) for a_, b_ in pev) / 1e3 / args.steps
+    per_query = {"value": round(NQ / pq_s, 1), "unit": "queries/s", "ms_per_step": round(1e3 * pq_s, 4),
+                 "kernel": "aps_search_kernel, one CTA per query"}
+
+    # the hot path: batched APS (the same decisions and results, the leaf scans
+    # of all queries grouped by partition)
+    batched = args.storage == "f32"
+    if batched:
+        plan = I.ApsBatchPlan(ix, NQ, K, rounds=args.rounds)
+        bout = plan.outputs(Qd)
+
+        def step(q_):
+            plan.search(q_, tau, out=bout, stream=stream)
+    else:   # low-precision storage: the per-query kernel is the path
+        plan, bout = None, out
+
+        def step(q_):
+            ix.search(q_, K, recall_target=tau, out=bout, stream=stream)
+    step(Qd)
+    torch.cuda.synchronize()
+    same = {"ids": float((bout[0] == oi).all(dim=1).float().mean().item()),
+            "nprobe": float((bout[2] == on).float().mean().item())}
+    for _ in range(args.warmup):
+        step(Qd)
     torch.cuda.synchronize()
     ix.hits(0, reset=True)
     ix.hits(1, reset=True)
+    if plan:
+        plan.set_timing(True)
     peak, peak_kind = peaks()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    scan_ms, asked = [], []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -264,10 +299,19 @@ def run_ours(args):
         t0 = time.perf_counter()
         for i in range(args.steps):
             ev[i][0].record(stream)
-            ix.search(Qd, K, recall_target=tau, out=out, stream=stream)
+            step(Qd)
             ev[i][1].record(stream)
+            if plan:
+                st = plan.stage_times()          # waits for this step's last event
+                scan_ms.append(st["scan"])
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+    if plan:
+        plan.set_timing(False)
+        stages = st
+        a_items, t_items = plan.round_stats()
+    else:
+        stages, a_items, t_items = {}, np.zeros(0, np.int64), np.zeros(0, np.int64)
     ix.check(stream)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(launch_ms) / 1e3
@@ -275,27 +319,35 @@ def run_ours(args):
         dist.barrier()
     h0 = ix.hits(0)
     h1 = ix.hits(1)
-    # algorithmic bytes: every (query, partition) item reads the partition's rows once,
-    # plus the top partition (32 parent centroids) per query
     eb = {"f32": 4, "bf16": 2, "fp8": 1}[args.storage]
-    bytes_total = (float((h0 * sizes0).sum()) * D * eb + float((h1 * sizes1).sum()) * D * 4
-                   + args.steps * NQ * N_PARENT * D * 4)
-    if args.storage != "f32":   # the re-rank reads rerank * k FP32 rows per query
-        bytes_total += args.steps * NQ * min(1024, args.rerank * K) * D * 4
-    bytes_per_launch = bytes_total / args.steps
-    avg_launch_s = dev_s / args.steps
-    achieved = bytes_per_launch / avg_launch_s / 1e9
+    bytes_unique, bytes_items = algorithmic_bytes(h0, h1, sizes0, sizes1, eb, args.steps, 0)
+    avg_step_s = dev_s / args.steps
+    # the grouped scan, the dominant kernel: 2 FP32 instructions (subtract, fused
+    # multiply-add) per element of every (query, row) pair of the items Algorithm 1 took in
+    pairs = float((h0 * sizes0).sum()) / args.steps
+    scan_s = sum(scan_ms) / 1e3 / args.steps if plan else None
+    clock_mhz = clk.summary().get("sm_max_mhz") or 2032.0
+    peak_ops = 148 * 128 * clock_mhz * 1e6 / 1e12
 
-    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    # end to end: pinned host queries copied in, the batch, results copied out, every step
     Qh = torch.from_numpy(Q).pin_memory()
     oh = (torch.empty((NQ, K), dtype=torch.int64).pin_memory(), torch.empty((NQ, K), dtype=torch.float32).pin_memory(),
           torch.empty(NQ, dtype=torch.int32).pin_memory(), torch.empty(NQ, dtype=torch.float32).pin_memory())
-    ix.search(Qh, K, recall_target=tau, out=oh, stream=stream)
+    qd2 = torch.empty_like(Qd)
+
+    def e2e_step():
+        qd2.copy_(Qh, non_blocking=True)
+        step(qd2)
+        for h_, d_ in zip(oh, bout):
+            h_.copy_(d_, non_blocking=True)
+    e2e_step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ix.search(Qh, K, recall_target=tau, out=oh, stream=stream)
+        e2e_step()
+    torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    e2e_same = bool((oh[0] == bout[0].cpu()).all().item())
 
     dev_s, e2e_s = max_over_ranks([dev_s, e2e_s], world, dev)
     qps = whole_job_rate(NQ * args.steps, world, dev_s)
@@ -310,7 +362,13 @@ def run_ours(args):
             "data": "synthetic (seeded Gaussian mixture; stands in for Sift1M-shaped data)",
             "config": {"workload": WORKLOAD, "n": N, "d": D, "n_leaf": N_LEAF, "n_parent": N_PARENT,
                        "queries_per_step": NQ, "k": K, "recall_target": tau, "recall_at_10": round(rec, 4),
-                       "fixed_nprobe_path": fixed,
+                       "fixed_nprobe_path": fixed, "per_query_kernel": per_query,
+                       "path": (f"batched APS, {args.rounds} rounds (qk_aps_batch_search)" if plan else
+                                "per-query kernel (qk_search)"),
+                       "same_as_per_query_kernel": same,
+                       "stage_ms": {k_: (round(v_, 4) if isinstance(v_, float) else [round(x, 4) for x in v_])
+                                    for k_, v_ in stages.items()},
+                       "items_asked_per_round": a_items.tolist(), "items_taken_per_round": t_items.tolist(),
                        "mean_nprobe": round(mean_nprobe, 2), "f_M": [F_M_LEAF, F_M_PARENT],
                        "tau_rho": 0.01, "upper_recall": 0.99, "beta": "table", "build_s": round(build_s, 2),
                        "storage": args.storage, "rerank": args.rerank if args.storage != "f32" else None,
@@ -318,11 +376,26 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": round(e2e_qps, 1), "unit": "queries/s",
                     "h2d_bytes_per_step": NQ * D * 4,
-                    "d2h_bytes_per_step": NQ * K * (8 + 4) + NQ * 8},
-            "gpu_launches": args.steps,   # one aps_search_kernel per step (plus a memset of its work counter)
-            "roofline": roofline(achieved, peak, peak_kind, avg_launch_s),
+                    "d2h_bytes_per_step": NQ * K * (8 + 4) + NQ * 8, "results_equal_device_run": e2e_same},
+            # per step: the prepare kernel, the first replay, then per round the grouping,
+            # the fill, the grouped scan and the replay
+            "gpu_launches": args.steps * (2 + 4 * args.rounds) if plan else args.steps,
+            "roofline": (scan_roofline(pairs, scan_s, peak_ops, bytes_unique, bytes_items, avg_step_s, peak,
+                                       peak_kind) if plan else
+                         roofline(bytes_unique, bytes_items, peak, peak_kind, avg_step_s)),
             "clocks": clk.summary(),
         }
+        if args.serve_ops > 0 and world == 1:
+            st, scfg, sclk = serve_stream(args.serve_ops, args.serve_load, args.server, args.update_wait,
+                                          args.start, maintain_every=args.serve_ops)
+            line["p50_ms"] = st["search"]["p50_ms"]
+            line["p99_ms"] = st["search"]["p99_ms"]
+            line["serving"] = {"config": scfg, "search_qps": st["search_qps"], "search": st["search"],
+                               "insert": st.get("insert"), "delete": st.get("delete"),
+                               "maintenance_passes": st["maintenance_passes"],
+                               "driver_lag_p99_ms": st["driver_lag_p99_ms"], "clocks": sclk,
+                               "note": ("latency from each request's scheduled arrival to its completion, "
+                                        "through the library's serving loop (qk_server_*)")}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(X, ids, Q, tau, args.cpu_seconds, workers=cpu_workers(args))
         print(json.dumps(line), flush=True)
@@ -330,18 +403,71 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def roofline(achieved, peak, peak_kind, launch_s):
-    """Roofline of aps_search_kernel: algorithmic bytes = every scanned (query,
-    partition) item's rows (s_p * d * 4 bytes) plus the top partition per query."""
+def algorithmic_bytes(h0, h1, sizes0, sizes1, eb, steps, rerank):
+    """Per-launch algorithmic bytes of the search (per item: s_p (d b + 8), rows and int64 ids).
+
+    unique: every partition the launch touches, read once: the level-0 partitions with
+      a hit (rows + ids), the touched parents' rows (leaf centroids + their int64 leaf
+      ids), the top partition, the queries and the results.  The minimum traffic.
+    items: every scanned (query, partition) item's rows + ids (the paper's effective
+      scan rate, Sec. 8 "Scalability"), plus the same top partition, queries and results.
+    Both add the FP32 re-rank rows of low-precision storage (rerank * k per query).
+    h0/h1 are hit counts summed over `steps` identical launches."""
+    row0 = D * eb + 8
+    row1 = D * 4 + 8
+    fixed = NQ * N_PARENT * D * 4 + NQ * D * 4 + NQ * K * 12 + NQ * min(1024, rerank * K) * D * 4
+    unique = float(sizes0[h0 > 0].sum()) * row0 + float(sizes1[h1 > 0].sum()) * row1 + fixed
+    items = (float((h0 * sizes0).sum()) * row0 + float((h1 * sizes1).sum()) * row1) / steps + fixed
+    return unique, items
+
+
+def scan_roofline(pairs, scan_s, peak_ops, bytes_unique, bytes_items, step_s, hbm_peak, hbm_kind):
+    """Roofline of the grouped scan (grouped_scan_kernel), the dominant kernel of a
+    batched APS step.  It is bound by FP32 issue: every (query, row) pair costs d
+    subtractions and d fused multiply-adds on the FP32 lanes (148 SMs x 128 lanes
+    x clock).  achieved = those instructions for the items Algorithm 1 took in,
+    over the grouped scans' device time in the step (CUDA events around each
+    scan launch, summed over the rounds).  The HBM figures of the whole step sit
+    beside it: unique bytes (each touched partition once) and the per-item bytes
+    of the paper's effective scan rate."""
+    ops = 2.0 * pairs * D
+    achieved = ops / scan_s / 1e12
+    return {"bound": "alu", "kernel": "grouped_scan_kernel", "achieved": round(achieved, 2),
+            "peak": round(peak_ops, 2), "unit": "Tops/s", "frac": round(achieved / peak_ops, 4),
+            "traffic": None, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x max SM clock",
+            "scan_ms_per_step": round(1e3 * scan_s, 4), "pairs_per_step": round(pairs),
+            "hbm": {"unique_gbs": round(bytes_unique / step_s / 1e9, 1),
+                    "unique_frac": round(bytes_unique / step_s / 1e9 / hbm_peak, 4),
+                    "effective_scan_gbs": round(bytes_items / step_s / 1e9, 1),
+                    "effective_frac": round(bytes_items / step_s / 1e9 / hbm_peak, 4),
+                    "peak": hbm_peak, "peak_kind": hbm_kind, "unique_bytes": round(bytes_unique),
+                    "item_bytes": round(bytes_items)},
+            "note": ("achieved counts 2 FP32 instructions per element of every scanned (query, row) pair; "
+                     "hbm.unique counts every touched partition's rows and ids once per step, "
+                     "hbm.effective every (query, partition) item's")}
+
+
+def roofline(bytes_unique, bytes_items, peak, peak_kind, launch_s):
+    """Roofline of aps_search_kernel.  achieved = the launch's unique algorithmic bytes
+    (every touched partition once) over its duration, so frac <= 1 is a fraction of HBM;
+    effective_scan_gbs counts every (query, partition) item's bytes, re-reads included;
+    traffic is the ncu DRAM bytes of one launch when a capture of these kernel sources
+    exists."""
     full = (N, NQ, N_LEAF, N_PARENT) == (1_000_000, 10_000, 1000, 32) and STORAGE == "f32"
     traffic = TRAFFIC_BYTES if (full and kernel_hash() == TRAFFIC_KERNEL_HASH) else None
+    achieved = bytes_unique / launch_s / 1e9
+    eff = bytes_items / launch_s / 1e9
     out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-           "note": ("achieved counts every item's partition bytes; hot partitions are re-read from L2, so "
-                    "it can exceed the HBM copy peak. traffic is the ncu DRAM bytes of one launch.")}
+           "unique_bytes": round(bytes_unique), "item_bytes": round(bytes_items),
+           "effective_scan_gbs": round(eff, 1), "effective_frac": round(eff / peak, 4),
+           "note": ("achieved = unique algorithmic bytes (each touched partition's rows and ids once) per "
+                    "launch / launch time; effective_scan_gbs counts every scanned (query, partition) item, "
+                    "so reads served from L2 count too; traffic = ncu DRAM bytes per launch")}
     if traffic is not None:
         out["dram_gbs"] = round(traffic / launch_s / 1e9, 1)
         out["dram_frac"] = round(traffic / launch_s / 1e9 / peak, 4)
+        out["reread_factor"] = round(traffic / bytes_unique, 2)
     return out
 
 
@@ -831,17 +957,17 @@ def run_sweep(args):
         "clocks": clk.summary()}), flush=True)
 
 
-def run_serve(args):
-    """Dynamic skewed stream (start 2M x 128 from 2,000 components; 90% queries, 5% inserts,
-    5% deletes; Zipf(1.2) over a hot set of 100 components rotating every 100,000 operations;
-    maintenance every 100,000 operations), open-loop Poisson arrivals at a fraction of the
-    measured saturation rate.  Reports p50/p99 latency and QPS."""
+def serve_stream(n_ops, load, server="native", update_wait=0.01, start=2_000_000, maintain_every=100_000):
+    """The dynamic skewed stream of the serving workload (start 2M x 128 from 2,000
+    components; 90% queries, 5% inserts, 5% deletes; Zipf(1.2) over a hot set of 100
+    components rotating every 100,000 operations; maintenance every 100,000 operations),
+    open-loop Poisson arrivals at `load` x the saturation rate measured by a closed burst.
+    Returns (latency summary, config, clocks)."""
     import torch
     from paper_2506_03437_b300 import index as I
     from paper_2506_03437_b300.serving import NativeServer, Server, skewed_stream
-    Srv = NativeServer if args.server == "native" else Server
-    torch.cuda.set_device(0)
-    n0, n_comp = args.start, 2000
+    Srv = NativeServer if server == "native" else Server
+    n0, n_comp = start, 2000
     C = synth.mixture_centers(n_comp, D, 1240)
     X, _ = synth.mixture_samples(C, n0, SIGMA, 1241)
     ids = np.arange(n0, dtype=np.int64)
@@ -859,21 +985,31 @@ def run_serve(args):
     srv = Srv(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4)
     sat = srv.run(burst)["search_qps"]
     sat = max(sat, srv.run(burst)["search_qps"])
-    rate = args.serve_load * sat / 0.9          # ops/s so that queries arrive at serve_load x saturation
-    ops = skewed_stream(C, ids, args.ops, SIGMA, 1243, rate=rate)
-    srv = Srv(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4, maintain_every=100_000,
-              maint_args=maint, update_wait_s=args.update_wait)
+    rate = load * sat / 0.9          # ops/s so that queries arrive at load x saturation
+    ops = skewed_stream(C, ids, n_ops, SIGMA, 1243, rate=rate)
+    srv = Srv(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4, maintain_every=maintain_every,
+              maint_args=maint, update_wait_s=update_wait)
     with Clocks(0) as clk:
         st = srv.run(ops)
+    cfg = {"workload": f"serve_{n0}x{D}_{n_ops}ops", "start_vectors": n0, "ops": n_ops,
+           "load": load, "saturation_qps": sat, "arrival_rate_ops": round(rate, 1),
+           "update_wait_s": update_wait, "server": server, "maintain_every": maintain_every,
+           "n_leaf": n_leaf, "streams": 4, "max_batch": 2048}
+    del ix
+    torch.cuda.empty_cache()
+    return st, cfg, clk.summary()
+
+
+def run_serve(args):
+    """The serving workload on the whole stream: reports p50/p99 latency and QPS."""
+    import torch
+    torch.cuda.set_device(0)
+    st, cfg, clocks = serve_stream(args.ops, args.serve_load, args.server, args.update_wait, args.start)
     line = {"metric": "serving p50/p99 latency and QPS (dynamic skewed stream)",
             "value": st["search_qps"], "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": round(1e3 * st["wall_s"], 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic skewed stream",
-            "config": {"workload": f"serve_{n0}x{D}_{args.ops}ops", "start_vectors": n0, "ops": args.ops,
-                       "load": args.serve_load, "saturation_qps": sat, "arrival_rate_ops": round(rate, 1),
-                       "update_wait_s": args.update_wait, "server": args.server,
-                       "n_leaf": n_leaf, "streams": 4, "max_batch": 2048},
-            "latency": st, "clocks": clk.summary()}
+            "config": cfg, "latency": st, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -888,6 +1024,8 @@ def main():
                          "serve: the continuous-batching request loop on a dynamic skewed stream")
     ap.add_argument("--ops", type=int, default=1_000_000, help="operations of the serving stream")
     ap.add_argument("--serve-load", type=float, default=0.5, help="query arrival rate / saturation")
+    ap.add_argument("--serve-ops", type=int, default=100_000,
+                    help="operations of the bounded serving sample in the default run (0: none)")
     ap.add_argument("--start", type=int, default=2_000_000, help="vectors in the index when the stream starts")
     ap.add_argument("--server", default="native", choices=["native", "python"],
                     help="the scheduler in the library (qk_server_*) or the Python loop of serving.py")
@@ -919,6 +1057,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"],
                     help="leaf storage: FP32, or BF16 / FP8 E4M3 with an FP32 re-rank of 4k candidates")
     ap.add_argument("--rerank", type=int, default=4)
+    ap.add_argument("--rounds", type=int, default=4, help="rounds of the batched APS search")
     args = ap.parse_args()
     global N, N_COMP, NQ, N_LEAF, N_PARENT, WORKLOAD, STORAGE
     N, NQ, N_LEAF, N_PARENT = args.n, args.nq, args.leaves, args.parents

@@ -619,10 +619,29 @@ qk_status qk_aps_batch_capture(qk_aps_batch* plan, const float* q, int64_t nq, f
                                int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall,
                                void* stream);
 qk_status qk_aps_batch_replay(qk_aps_batch* plan, void* stream);
+/* Stage timing of uncaptured batches: with timing on, qk_aps_batch_search
+ * records CUDA events on its stream between its steps; qk_aps_batch_stage_times
+ * waits for the last timed batch and writes 4 + rounds durations in
+ * milliseconds: the prepare step (root scoring and upper level), every replay
+ * together, every grouping together, every grouped scan together, then the
+ * grouped scan of each round.  QK_ERR_STATE if no batch ran with timing on. */
+qk_status qk_aps_batch_set_timing(qk_aps_batch* plan, int32_t on);
+qk_status qk_aps_batch_stage_times(qk_aps_batch* plan, float* ms);
 /* For the last batch (synchronous): per round, the items asked for and the
  * items Algorithm 1 took in (the rest were scanned beyond a query's stop);
  * arrays of the plan's round count. */
 qk_status qk_aps_batch_round_stats(qk_aps_batch* plan, int64_t* asked, int64_t* taken);
+
+/* SPANN's early-termination rule, the comparator of Sec. 2 "Early Termination"
+ * and Table 6: query i scans the candidates of its set S (the same S as APS
+ * builds: the ceil(f_M_leaf * n_leaf) nearest leaves with one level, the upper
+ * level's APS result with two), nearest first, whose Euclidean centroid
+ * distance is at most (1 + eps) times the nearest one's; eps > 0 is the rule's
+ * tuned parameter.  out_nprobe[nq] (optional) receives the count scanned,
+ * out_scanned0 (optional, nq x cap0) the leaves scanned, as in
+ * qk_search_scanned.  Host or device buffers. */
+qk_status qk_search_ratio(qk_index* index, const float* q, int64_t nq, int32_t k, float eps, int64_t* out_ids,
+                          float* out_dist, int32_t* out_nprobe, int32_t* out_scanned0, int32_t cap0, void* stream);
 
 /* Fixed-nprobe search with one nprobe per query through the per-query search
  * kernel (one CTA per query; the comparison point of the batched path and of

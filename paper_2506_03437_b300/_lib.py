@@ -25,14 +25,14 @@ EXPORTS = [
     "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load",
     "qk_search", "qk_search_scanned", "qk_stats", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_export_quantized", "qk_get_hits", "qk_cap_fraction",
     "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain", "qk_nearest_centroids",
-    "qk_search_nprobe", "qk_batch_create", "qk_batch_destroy", "qk_batch_get_tiles", "qk_batch_set_tiles",
+    "qk_search_nprobe", "qk_search_ratio", "qk_batch_create", "qk_batch_destroy", "qk_batch_get_tiles", "qk_batch_set_tiles",
     "qk_batch_search", "qk_batch_capture", "qk_batch_replay", "qk_batch_autotune", "qk_batch_set_timing",
     "qk_batch_stage_times", "qk_maintain_prepare", "qk_maintain_commit", "qk_profile_scan", "qk_save", "qk_restore",
     "qk_server_config_default", "qk_server_create", "qk_server_destroy", "qk_server_submit_search",
     "qk_server_submit_insert", "qk_server_submit_delete", "qk_server_results", "qk_server_drain",
     "qk_server_get_stats", "qk_aps_batch_create", "qk_aps_batch_destroy", "qk_aps_batch_set_rounds",
     "qk_aps_batch_set_tiles", "qk_aps_batch_search", "qk_aps_batch_capture", "qk_aps_batch_replay",
-    "qk_aps_batch_round_stats",
+    "qk_aps_batch_round_stats", "qk_aps_batch_set_timing", "qk_aps_batch_stage_times",
 ]
 
 
@@ -121,6 +121,7 @@ def _load():
         "qk_maintain": (i32, [vp, C.POINTER(QkMaintParams), C.POINTER(QkMaintAction), i32,
                               C.POINTER(C.c_int32), vp]),
         "qk_search_nprobe": (i32, [vp, vp, i64, i32, vp, vp, vp, vp]),
+        "qk_search_ratio": (i32, [vp, vp, i64, i32, f32, vp, vp, vp, vp, i32, vp]),
         "qk_maintain_prepare": (i32, [vp, C.POINTER(QkMaintParams), C.POINTER(QkMaintAction), i32,
                                       C.POINTER(C.c_int32), vp]),
         "qk_maintain_commit": (i32, [vp, vp]),
@@ -154,6 +155,8 @@ def _load():
         "qk_aps_batch_capture": (i32, [vp, vp, i64, f32, vp, vp, vp, vp, vp]),
         "qk_aps_batch_replay": (i32, [vp, vp]),
         "qk_aps_batch_round_stats": (i32, [vp, vp, vp]),
+        "qk_aps_batch_set_timing": (i32, [vp, i32]),
+        "qk_aps_batch_stage_times": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -415,6 +415,12 @@ struct qk_aps_batch {
   cudaGraphExec_t graph = nullptr;
   uint64_t graph_version = 0;
   int64_t graph_nq = 0;
+  // stage timing of uncaptured batches: events before the prepare step, after
+  // it, after the first replay, then per round after grouping, after the scan
+  // and after the replay
+  bool timing = false, timed = false;
+  int timed_rounds = 0;
+  cudaEvent_t ev[3 + 3 * ab::kMaxRounds] = {};
 };
 
 namespace {
@@ -507,6 +513,12 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   if (capturing && !(b->scan_tiles.queries_per_warp == tl.queries_per_warp && b->scan_tiles.tile_rows == tl.tile_rows))
     b->scan_blocks = 0;
   Trace tr("aps_batch");
+  const bool timing = b->timing && !capturing;
+  auto mark = [&](int i) -> qk_status {
+    if (timing) QK_CUDA(cudaEventRecord(b->ev[i], s));
+    return QK_OK;
+  };
+  QK_TRY(mark(0));
   // 1. root scoring and upper-level APS per query; S and t_i exported
   SearchArgs sa;
   base_search_args(ix, k, recall_target, 0, sa);
@@ -524,6 +536,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   sa.xs_mcap = mcap;
   QK_TRY(launch_search(sa, s));
   tr.mark("prepare");
+  QK_TRY(mark(1));
   if (b->rstats) QK_CUDA(cudaMemsetAsync(b->rstats, 0, sizeof(unsigned long long) * 2 * (ab::kMaxRounds + 1), s));
   // 2. the first requests
   ab::ReplayArgs ra;
@@ -564,6 +577,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   ra.final_request = b->rounds == 1;
   ab::aps_replay_kernel<<<rgrid, ab::kThreads, 0, s>>>(ra);
   QK_CUDA(cudaGetLastError());
+  QK_TRY(mark(2));
   ra.first = 0;
   const int G = bt::kWarps * tl.queries_per_warp;
   for (int rd = 0; rd < b->rounds; ++rd) {
@@ -594,6 +608,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     ab::fill_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(b->st.req, b->st.nreq, b->st.cand, nq, mcap,
                                                                    b->pstart, b->pcur, b->qlist, b->qpos);
     QK_CUDA(cudaGetLastError());
+    QK_TRY(mark(3 + 3 * rd));
     // 4. every item's own top-k
     QK_CUDA(cudaMemsetAsync(b->qcnt, 0, sizeof(int32_t) * nq, s));
     QK_CUDA(cudaMemsetAsync(b->work, 0, sizeof(unsigned long long), s));
@@ -625,14 +640,20 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     sc.cpos = b->cpos;
     QK_TRY(launch_scan_rounds(sc, d, tl.queries_per_warp, b->n_sm, capturing, &b->scan_blocks, s));
     b->scan_tiles = tl;
+    QK_TRY(mark(4 + 3 * rd));
     // 5. Algorithm 1 over the round, and the next requests
     QK_CUDA(cudaMemsetAsync(b->pcount, 0, sizeof(int32_t) * K, s));
     ra.round = rd;
     ra.final_request = rd + 1 == b->rounds - 1;
     ab::aps_replay_kernel<<<rgrid, ab::kThreads, 0, s>>>(ra);
     QK_CUDA(cudaGetLastError());
+    QK_TRY(mark(5 + 3 * rd));
   }
   tr.mark("rounds");
+  if (timing) {
+    b->timed = true;
+    b->timed_rounds = b->rounds;
+  }
   ix->queries_seen += nq;
   return QK_OK;
 }
@@ -804,6 +825,8 @@ qk_status qk_aps_batch_create(qk_index* ix, int64_t max_nq, int32_t k, qk_aps_ba
 void qk_aps_batch_destroy(qk_aps_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (cudaEvent_t& e : b->ev)
+    if (e) cudaEventDestroy(e);
   free_all(b);
   delete b;
 }
@@ -914,6 +937,52 @@ qk_status qk_aps_batch_replay(qk_aps_batch* b, void* stream) {
   }
   QK_CUDA(cudaGraphLaunch(b->graph, (cudaStream_t)stream));
   b->ix->queries_seen += b->graph_nq;
+  return QK_OK;
+  QK_GUARD_END
+}
+
+qk_status qk_aps_batch_set_timing(qk_aps_batch* b, int32_t on) {
+  QK_GUARD_BEGIN
+  if (!b) {
+    set_error("null plan");
+    return QK_ERR_ARG;
+  }
+  if (on && !b->ev[0])
+    for (cudaEvent_t& e : b->ev) QK_CUDA(cudaEventCreate(&e));
+  b->timing = on != 0;
+  b->timed = false;
+  return QK_OK;
+  QK_GUARD_END
+}
+
+qk_status qk_aps_batch_stage_times(qk_aps_batch* b, float* ms) {
+  QK_GUARD_BEGIN
+  if (!b || !ms) {
+    set_error("null argument");
+    return QK_ERR_ARG;
+  }
+  if (!b->timed) {
+    set_error("no batch ran with timing on");
+    return QK_ERR_STATE;
+  }
+  const int R = b->timed_rounds;
+  QK_CUDA(cudaEventSynchronize(b->ev[2 + 3 * R]));
+  auto span = [&](int i, int j) {
+    float v = 0.f;
+    cudaEventElapsedTime(&v, b->ev[i], b->ev[j]);
+    return v;
+  };
+  ms[0] = span(0, 1);
+  ms[1] = span(1, 2);
+  ms[2] = ms[3] = 0.f;
+  for (int r = 0; r < R; ++r) {
+    const int prev = r == 0 ? 2 : 2 + 3 * r;
+    const float g = span(prev, 3 + 3 * r), sc = span(3 + 3 * r, 4 + 3 * r), rp = span(4 + 3 * r, 5 + 3 * r);
+    ms[1] += rp;
+    ms[2] += g;
+    ms[3] += sc;
+    ms[4 + r] = sc;
+  }
   return QK_OK;
   QK_GUARD_END
 }

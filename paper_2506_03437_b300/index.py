@@ -144,6 +144,28 @@ class Index:
         out["hits"] = list(st.hits)
         return out
 
+    def search_ratio(self, q, k, eps, cap0=0, stream=None):
+        """SPANN's early-termination rule (qk_search_ratio): returns (ids, dist,
+        nprobe[, scanned0]) on the device of `q`."""
+        q = _as(q, np.float32)
+        nq = int(q.shape[0])
+        if hasattr(q, "data_ptr"):
+            import torch
+            dev = q.device
+            out = (torch.empty((nq, k), dtype=torch.int64, device=dev),
+                   torch.empty((nq, k), dtype=torch.float32, device=dev),
+                   torch.empty(nq, dtype=torch.int32, device=dev))
+            if cap0:
+                out = out + (torch.empty((nq, cap0), dtype=torch.int32, device=dev),)
+        else:
+            out = (np.empty((nq, k), np.int64), np.empty((nq, k), np.float32), np.empty(nq, np.int32))
+            if cap0:
+                out = out + (np.empty((nq, cap0), np.int32),)
+        s0 = out[3] if cap0 else None
+        L.check(L.lib.qk_search_ratio(self._h, L.ptr(q), nq, int(k), float(eps), L.ptr(out[0]), L.ptr(out[1]),
+                                      L.ptr(out[2]), L.ptr(s0), int(cap0), L.stream_ptr(stream)))
+        return out
+
     def search_nprobe(self, q, k, nprobe, out=None, stream=None):
         """Fixed-nprobe search, one nprobe per query, through the per-query kernel.
         Returns (ids, dist) on the device of `q`."""
@@ -442,6 +464,17 @@ class ApsBatchPlan:
 
     def replay(self, stream):
         L.check(L.lib.qk_aps_batch_replay(self._h, L.stream_ptr(stream)))
+
+    def set_timing(self, on=True):
+        L.check(L.lib.qk_aps_batch_set_timing(self._h, 1 if on else 0))
+
+    def stage_times(self):
+        """Milliseconds of the last timed batch: prepare, replay, grouping, scan (all
+        rounds together) and the scan of every round (waits for the batch)."""
+        ms = np.zeros(4 + self.rounds, np.float32)
+        L.check(L.lib.qk_aps_batch_stage_times(self._h, L.ptr(ms)))
+        return {"prepare": float(ms[0]), "replay": float(ms[1]), "grouping": float(ms[2]),
+                "scan": float(ms[3]), "scan_per_round": ms[4:].tolist()}
 
     def round_stats(self):
         """Per round of the last batch: (items asked for, items Algorithm 1 took in)."""

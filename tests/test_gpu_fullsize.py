@@ -39,6 +39,16 @@ def test_full_size_aps_sampled_parity(storage):
     sel = np.random.default_rng(0).choice(nq, 40, replace=False)
     orc = aps.search(levels, Q[sel], aps.Params(k=10, recall_target=0.9, f_M=(0.1, 0.25)))
     compare_search(tuple(a[sel] for a in out), orc, 10, label="APS 1M x 128, 40 sampled queries")
+    # the batched path, in the launch configuration the benchmark times (4 rounds)
+    plan = I.ApsBatchPlan(ix, nq, 10, rounds=4)
+    bo = tuple(a.cpu().numpy() for a in plan.search(torch.from_numpy(Q).cuda(), 0.9, cap0=100))
+    ix.check()
+    compare_search(tuple(a[sel] for a in bo) + (out[5][sel],), orc, 10,
+                   label="batched APS 1M x 128, 40 sampled queries")
+    agree = np.mean([np.array_equal(bo[0][j], gi[j]) and bo[2][j] == gn[j] and np.array_equal(bo[4][j], out[4][j])
+                     for j in range(nq)])
+    print(f"[parity] batched APS vs the per-query kernel: {agree:.4f} of {nq} queries identical")
+    assert agree >= 0.999
     # recall of the sample against FP64 brute force
     gtD, _ = knn.knn(X, ids, Q[sel], 10, bulk=True)
     rec = knn.recall_at_k(gi[sel], exact_dist(X, Q[sel], gi[sel]), gtD, 10).mean()
