@@ -12,18 +12,31 @@
 // 11 significant bits, which moves an approximate distance by at most about
 // 2^-10 * ||x|| * ||c||.
 //
-// One CTA = 4 warps owns 128 rows and sweeps the centroids in tiles of 256.
-// Each K-slice of 32 elements of both operands is staged in shared memory
-// with cp.async in a no-swizzle K-major layout built from 8-row x 16-byte
-// core matrices, then thread 0 issues four K=8 MMAs into a 128 x 256 FP32
-// accumulator in TMEM and commits them to an mbarrier.  Two slice buffers
-// let the loads of slice s+1 overlap the MMAs of slice s.  The epilogue reads
-// the accumulator with tcgen05.ld (each warp its 32 TMEM lanes = 32 rows).
+// The kernel is persistent (one CTA per SM) and warp-specialised:
+//   warp 0     the producer: one thread streams K-slices of 32 elements of
+//              the CTA's 128 rows and of 256 centroids into a ring of shared
+//              memory stages with TMA tensor copies (cp.async.bulk.tensor,
+//              128-byte swizzle), each stage completing on its "full" mbarrier;
+//   warp 1     the MMA issuer: one thread waits for a full stage, issues four
+//              K = 8 MMAs into a 128 x 256 FP32 accumulator in TMEM and commits
+//              them to the stage's "empty" mbarrier, which frees the stage for
+//              the producer when the MMAs have read it;
+//   warps 2-5  the epilogue: each thread owns one TMEM lane (one row), reads
+//              the accumulator with tcgen05.ld and keeps its row's candidates.
+// Two accumulators (all 512 TMEM columns) alternate between the MMA issuer
+// and the epilogue ("acc full" / "acc empty" mbarriers), so the epilogue of
+// one tile of centroids runs while the MMAs of the next one do.  No CTA-wide
+// barrier sits in the main loop.  Every wait is bounded: on expiry the kernel
+// records a timeout in the status word, every role leaves its loop, copies
+// and MMAs still in flight are waited for (bounded), and TMEM is freed.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <math.h>
+#include <mutex>
 #include <stdint.h>
+#include <string>
 
 #include "common.cuh"
 
@@ -31,16 +44,19 @@ namespace qk {
 
 namespace tc {
 
-constexpr int kM = 128;        // rows per CTA (TMEM lanes)
-constexpr int kN = 256;        // centroids per tile (TMEM columns)
-constexpr int kKS = 32;        // K elements per staged slice
-constexpr int kThreads = 256;  // 8 warps: warps w and w + 4 share TMEM lanes, split the columns
+constexpr int kM = 128;        // rows per CTA tile (TMEM lanes)
+constexpr int kN = 256;        // centroids per tile (TMEM columns of one accumulator)
+constexpr int kKS = 32;        // K elements per stage (128 bytes of FP32: one swizzle row)
+constexpr int kStages = 4;     // shared-memory ring
+constexpr int kThreads = 192;  // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
 constexpr int kT = 16;         // approximate candidates kept per row (k <= 8)
 constexpr int kT1 = 4;         // ... when only the nearest centroid is wanted
 
-constexpr int kSliceA = kM * kKS * 4;    // 16 KB
-constexpr int kSliceB = kN * kKS * 4;    // 32 KB
-constexpr int kSmem = 2 * (kSliceA + kSliceB) + kN * 4 + 64;
+constexpr int kStageA = kM * kKS * 4;    // 16 KB
+constexpr int kStageB = kN * kKS * 4;    // 32 KB
+constexpr int kStageBytes = kStageA + kStageB;
+// stages (1024-byte aligned for the swizzle), then the mbarriers and the TMEM address
+constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
 
 // Instruction descriptor of kind::tf32 (PTX ISA, tcgen05 instruction
 // descriptor): D format F32 (bits 4-5 = 1), A and B format TF32 (bits 7-9
@@ -52,29 +68,34 @@ constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN 
 // Shared-memory matrix descriptor (PTX ISA, tcgen05 shared memory
 // descriptor): start address >> 4 at bits 0-13, leading-dimension byte
 // offset >> 4 at bits 16-29, stride-dimension byte offset >> 4 at bits 32-45,
-// the fixed value 1 at bits 46-47, base offset 0, no swizzle (bits 61-63 = 0).
-// For a K-major operand without swizzle the leading dimension is K (the
-// distance between core matrices adjacent in K) and the stride dimension is
-// M/N (between core matrices adjacent in rows).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// the fixed value 0b001 at bits 46-48, base offset 0 (the stages are 1024-byte
+// aligned), swizzle mode at bits 61-63 (2 = 128-byte swizzle).  The operands
+// are K-major with a 128-byte swizzle: a row's 32 FP32 of the stage form one
+// 128-byte swizzle row and 8 rows one 1024-byte atom, so the stride between
+// 8-row groups is 1024 bytes and the leading offset is unused (one atom spans
+// the stage's whole K).  The MMA of K elements 8i..8i+7 starts 32i bytes in.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 16;                     // leading offset 16 bytes (unused)
+  d |= (uint64_t)(1024 >> 4) << 32;           // 8-row group stride
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
   return d;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  int n = valid ? 16 : 0;   // src-size 0 fills the 16 bytes with zeros
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+// 2-D TMA tile copy global -> shared (box given by the tensor map), completing
+// on `bar`; x is the element column (a multiple of 32 here, so 128-byte
+// aligned), y the row.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t ncols) {
@@ -121,6 +142,23 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 }  // namespace tc
 
 // Squared norm of every centroid row (one warp per row).
@@ -134,216 +172,234 @@ __global__ void row_norms_kernel(const float* __restrict__ C, int64_t K, int d, 
   if (lane == 0) out[w] = acc;
 }
 
-// Approximate top-T candidates per row (see the file comment).  With kStore
-// the epilogue instead writes every approximate distance to dout (row r,
-// centroid c at dout[r * ldd + c]), and blockIdx.y selects the range of
-// `span` centroids (a multiple of the tile width) that this CTA sweeps.
+// Approximate top-T candidates per row (see the file comment), or with
+// kStore every approximate distance written to dout (row r, centroid c at
+// dout[r * ldd + c]).  Work item i is row tile i / splits and the range of
+// `span` centroids (whole tiles) number i % splits; the CTAs take items i =
+// blockIdx.x, blockIdx.x + gridDim.x, ...  mapX / mapC are TMA tensor maps
+// of X (n x d) and C (K x d) with boxes of 32 x 128 and 32 x 256 elements.
 template <int T, bool kStore>
-__global__ void __launch_bounds__(tc::kThreads) tc_candidates_kernel(const float* __restrict__ X, int64_t n, int d,
-                                                                     const float* __restrict__ C, int K,
-                                                                     const float* __restrict__ cnorm, int metric,
-                                                                     int32_t* __restrict__ cand,
-                                                                     int32_t* __restrict__ status,
-                                                                     float* __restrict__ dout, int64_t ldd,
-                                                                     int span) {
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    tc_score_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapC, int64_t n,
+                    int d, int K, const float* __restrict__ cnorm, int metric, int32_t* __restrict__ cand,
+                    int32_t* __restrict__ status, float* __restrict__ dout, int64_t ldd, int splits, int span,
+                    int64_t n_items) {
   using namespace tc;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  float* scn = reinterpret_cast<float*>(smem + 2 * (kSliceA + kSliceB));   // ||c||^2 of the tile
-  uint64_t* bars = reinterpret_cast<uint64_t*>(scn + kN);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int quarter = warp & 3, half = warp >> 2;   // TMEM lanes 32 * quarter.., columns 128 * half..
-  const int64_t row0 = (int64_t)blockIdx.x * kM;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // the stages must sit on 1024-byte boundaries (the swizzle atom)
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int32_t* s_abort = reinterpret_cast<volatile int32_t*>(tmem_holder + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nslices = d / kKS;
 
-  if (warp == 0) tmem_alloc(tmem_holder, kN);
+  if (warp == 1) tmem_alloc(tmem_holder, 2 * kN);
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 4 * 32);
+    }
+    mbar_init(drain, 1);
+    *s_abort = 0;
     fence_mbar_init();
   }
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_holder;
-
-  // this thread's row and its running top-T over its half of every tile (ascending)
-  const int my_lane = quarter * 32 + (tid & 31);
-  const int64_t my_row = row0 + my_lane;
-  float bd[T];
-  int32_t bi[T];
-#pragma unroll
-  for (int i = 0; i < T; ++i) {
-    bd[i] = INFINITY;
-    bi[i] = -1;
-  }
-  const int nslices = d / kKS;
-  const int n_begin = kStore ? (int)blockIdx.y * span : 0;
-  const int n_end = kStore ? min(K, n_begin + span) : K;
-  uint32_t phase[2] = {0u, 0u};
-  uint32_t issued[2] = {0u, 0u};   // commits outstanding per buffer (0 or 1)
-  bool ok = true;
-
-  // a buffer is free once the MMAs that read it have completed
-  auto free_buffer = [&](int b) {
-    if (!issued[b]) return;
-    if (!mbar_wait_bounded(&bars[b], phase[b])) {
-      ok = false;
-      atomicExch(status, DEV_TIMEOUT);
-    }
-    phase[b] ^= 1u;
-    issued[b] = 0;
+  auto fail = [&]() {
+    *s_abort = 1;
+    atomicExch(status, DEV_TIMEOUT);
   };
-  // slice ks into buffer b: 8-row groups, each holding its 8 K-chunks of 16
-  // bytes as consecutive core matrices: (row r, chunk c) at
-  // ((r / 8) * 8 + c) * 128 + (r % 8) * 16.  K stride 128 B, row-group stride
-  // 1024 B, so every address the descriptors can form stays inside the slice.
-  // Consecutive threads take consecutive 16-byte chunks of one row, so a warp
-  // reads whole 128-byte row segments from global memory.
-  auto stage = [&](int n0, int ks, int b) {
-    const uint32_t a_base = smem_u32(smem + b * kSliceA), b_base = smem_u32(smem + 2 * kSliceA + b * kSliceB);
-    for (int e = tid; e < kM * (kKS / 4); e += kThreads) {
-      int c = e % (kKS / 4), r = e / (kKS / 4);
-      int64_t gr = row0 + r;
-      bool v = gr < n;
-      const float* src = X + (v ? gr : 0) * d + ks * kKS + c * 4;
-      cp_async16(a_base + ((r >> 3) * (kKS / 4) + c) * 128 + (r & 7) * 16, src, v);
-    }
-    for (int e = tid; e < kN * (kKS / 4); e += kThreads) {
-      int c = e % (kKS / 4), r = e / (kKS / 4);
-      int gc = n0 + r;
-      bool v = gc < K;
-      const float* src = C + (int64_t)(v ? gc : 0) * d + ks * kKS + c * 4;
-      cp_async16(b_base + ((r >> 3) * (kKS / 4) + c) * 128 + (r & 7) * 16, src, v);
-    }
-    cp_async_commit();
+  auto range = [&](int64_t item, int64_t& row0, int& n_begin, int& n_end) {
+    row0 = (item / splits) * kM;
+    n_begin = (int)(item % splits) * span;
+    n_end = min(K, n_begin + span);
   };
 
-  for (int n0 = n_begin; n0 < n_end && ok; n0 += kN) {
-    // two slices in flight: slice ks + 1 is copied while slice ks is waited for
-    free_buffer(0);
-    stage(n0, 0, 0);
-    for (int j = tid; j < kN; j += kThreads) scn[j] = n0 + j < K ? cnorm[n0 + j] : INFINITY;
-    for (int ks = 0; ks < nslices; ++ks) {
-      const int b = ks & 1;
-      if (ks + 1 < nslices) {
-        free_buffer(b ^ 1);
-        stage(n0, ks + 1, b ^ 1);
-        cp_async_wait_group<1>();   // this thread's copies of slice ks have landed
-      } else {
-        cp_async_wait_group<0>();
-      }
-      fence_proxy_async();        // generic-proxy writes -> tensor-core (async proxy) reads
-      fence_before_sync();
-      __syncthreads();
-      fence_after_sync();
-      if (tid == 0) {
-        const uint32_t a_base = smem_u32(smem + b * kSliceA), b_base = smem_u32(smem + 2 * kSliceA + b * kSliceB);
-#pragma unroll
-        for (int i = 0; i < kKS / 8; ++i) {   // K = 8 per tf32 MMA: two 16-byte chunks
-          uint64_t ad = smem_desc(a_base + (2 * i) * 128, 128, (kKS / 4) * 128);
-          uint64_t bd_ = smem_desc(b_base + (2 * i) * 128, 128, (kKS / 4) * 128);
-          mma_tf32(tmem, ad, bd_, kIdesc, (ks > 0 || i > 0) ? 1u : 0u);
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t fills[kStages] = {};
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t item = blockIdx.x; item < n_items && !*s_abort; item += gridDim.x) {
+        int64_t row0;
+        int n_begin, n_end;
+        range(item, row0, n_begin, n_end);
+        for (int n0 = n_begin; n0 < n_end && !*s_abort; n0 += kN) {
+          for (int ks = 0; ks < nslices; ++ks) {
+            if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
+              fail();
+              break;
+            }
+            const uint32_t a_dst = smem_u32(smem + stage * kStageBytes);
+            mbar_arrive_expect_tx(&full[stage], kStageBytes);
+            tma_load_2d(a_dst, &mapX, ks * kKS, (int)row0, &full[stage]);
+            tma_load_2d(a_dst + kStageA, &mapC, ks * kKS, n0, &full[stage]);
+            ++fills[stage];
+            if (++stage == kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
         }
-        mma_commit(&bars[b]);
       }
-      issued[b] = 1;
+      // copies still in flight land before the CTA leaves (the n-th fill of a
+      // stage completes the phase of parity (n - 1) & 1)
+      for (int i = 0; i < kStages; ++i)
+        if (fills[i]) mbar_wait_bounded(&full[i], (fills[i] - 1u) & 1u);
     }
-    // wait for the last slice's MMAs (the commit covers every earlier MMA too)
-    const int bl = (nslices - 1) & 1;
-    if (!mbar_wait_bounded(&bars[bl], phase[bl])) {
-      ok = false;
-      atomicExch(status, DEV_TIMEOUT);
-    }
-    phase[bl] ^= 1u;
-    issued[bl] = 0;
-    if (nslices > 1 && issued[bl ^ 1]) {   // the other buffer's commit has completed as well
-      if (!mbar_wait_bounded(&bars[bl ^ 1], phase[bl ^ 1])) {
-        ok = false;
-        atomicExch(status, DEV_TIMEOUT);
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      bool issued = false;
+      for (int64_t item = blockIdx.x; item < n_items && !*s_abort; item += gridDim.x) {
+        int64_t row0;
+        int n_begin, n_end;
+        range(item, row0, n_begin, n_end);
+        for (int n0 = n_begin; n0 < n_end && !*s_abort; n0 += kN) {
+          if (!mbar_wait_bounded(&acc_empty[acc], acc_phase ^ 1u)) {   // the epilogue freed this accumulator
+            fail();
+            break;
+          }
+          fence_after_sync();
+          const uint32_t d_tmem = tmem + (uint32_t)(acc * kN);
+          for (int ks = 0; ks < nslices; ++ks) {
+            if (!mbar_wait_bounded(&full[stage], phase)) {
+              fail();
+              break;
+            }
+            fence_after_sync();
+            const uint32_t a_base = smem_u32(smem + stage * kStageBytes), b_base = a_base + kStageA;
+#pragma unroll
+            for (int i = 0; i < kKS / 8; ++i)   // K = 8 per TF32 MMA: 32 bytes into the swizzle row
+              mma_tf32(d_tmem, smem_desc_sw128(a_base + 32 * i), smem_desc_sw128(b_base + 32 * i), kIdesc,
+                       (ks > 0 || i > 0) ? 1u : 0u);
+            mma_commit(&empty[stage]);   // the stage is free once these MMAs have read it
+            issued = true;
+            if (++stage == kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (*s_abort) break;
+          mma_commit(&acc_full[acc]);   // the accumulator is complete
+          if (++acc == 2) {
+            acc = 0;
+            acc_phase ^= 1u;
+          }
+        }
       }
-      phase[bl ^ 1] ^= 1u;
-      issued[bl ^ 1] = 0;
+      // every MMA completes before TMEM is freed
+      if (issued) {
+        mma_commit(drain);
+        mbar_wait_bounded(drain, 0);
+      }
     }
-    fence_after_sync();
-    // epilogue: this thread's TMEM lane = its row, its half of the columns
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3;                 // the TMEM lanes this warp may read
+    const int my_lane = quarter * 32 + lane;      // this thread's row within the tile
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-    for (int c0 = half * (kN / 2); c0 < (half + 1) * (kN / 2); c0 += 8) {
-      float v[8];
-      tc::tmem_ld8(lane_addr + c0, v);
-      if (kStore) {
-        float o[8];
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int64_t item = blockIdx.x; item < n_items && !*s_abort; item += gridDim.x) {
+      int64_t row0;
+      int n_begin, n_end;
+      range(item, row0, n_begin, n_end);
+      const int64_t my_row = row0 + my_lane;
+      float bd[T];
+      int32_t bi[T];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) o[i] = metric == QK_METRIC_L2 ? fmaf(-2.f, v[i], scn[c0 + i]) : -v[i];
-        if (my_row < n) {
-          float* dst = dout + my_row * ldd + n0 + c0;
-          if (n0 + c0 + 8 <= K && (ldd & 3) == 0) {   // 16-byte aligned: ldd and n0 + c0 are multiples of 4
-            reinterpret_cast<float4*>(dst)[0] = make_float4(o[0], o[1], o[2], o[3]);
-            reinterpret_cast<float4*>(dst)[1] = make_float4(o[4], o[5], o[6], o[7]);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (n0 + c0 + i < K) dst[i] = o[i];
-          }
-        }
-        continue;
+      for (int i = 0; i < T; ++i) {
+        bd[i] = INFINITY;
+        bi[i] = -1;
       }
+      for (int n0 = n_begin; n0 < n_end; n0 += kN) {
+        if (*s_abort || !mbar_wait_bounded(&acc_full[acc], acc_phase)) {
+          fail();
+          break;
+        }
+        fence_after_sync();
+        for (int c0 = 0; c0 < kN; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(lane_addr + (uint32_t)(acc * kN + c0), v);
+          if (kStore) {
+            if (my_row < n) {
+              float* dst = dout + my_row * ldd + n0 + c0;
+              const bool whole = n0 + c0 + 32 <= K && (ldd & 3) == 0;   // 16-byte aligned stores
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        int col = n0 + c0 + i;
-        float dist = metric == QK_METRIC_L2 ? fmaf(-2.f, v[i], scn[c0 + i]) : (col < K ? -v[i] : INFINITY);
-        if (dist < bd[T - 1] || (dist == bd[T - 1] && col < bi[T - 1])) {
-          // insert into the sorted registers
-          float cd = dist;
-          int32_t ci = col;
+              for (int i = 0; i < 32; i += 4) {
+                float o[4];
 #pragma unroll
-          for (int j = 0; j < T; ++j) {
-            bool lt = cd < bd[j] || (cd == bd[j] && ci < bi[j]);
-            float td = bd[j];
-            int32_t ti = bi[j];
-            bd[j] = lt ? cd : td;
-            bi[j] = lt ? ci : ti;
-            cd = lt ? td : cd;
-            ci = lt ? ti : ci;
+                for (int j = 0; j < 4; ++j) {
+                  const int col = n0 + c0 + i + j;
+                  const float cn = col < K ? __ldg(&cnorm[col]) : INFINITY;
+                  o[j] = metric == QK_METRIC_L2 ? fmaf(-2.f, v[i + j], cn) : -v[i + j];
+                }
+                if (whole) {
+                  reinterpret_cast<float4*>(dst + i)[0] = make_float4(o[0], o[1], o[2], o[3]);
+                } else {
+#pragma unroll
+                  for (int j = 0; j < 4; ++j)
+                    if (n0 + c0 + i + j < K) dst[i + j] = o[j];
+                }
+              }
+            }
+            continue;
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int col = n0 + c0 + i;
+            const bool valid = col < K;
+            const float cn = valid ? __ldg(&cnorm[col]) : INFINITY;
+            const float dist = metric == QK_METRIC_L2 ? fmaf(-2.f, v[i], cn) : (valid ? -v[i] : INFINITY);
+            if (dist < bd[T - 1] || (dist == bd[T - 1] && col < bi[T - 1])) {
+              float cd = dist;
+              int32_t ci = col;
+#pragma unroll
+              for (int j = 0; j < T; ++j) {   // insert into the sorted registers
+                const bool lt = cd < bd[j] || (cd == bd[j] && ci < bi[j]);
+                const float td = bd[j];
+                const int32_t ti = bi[j];
+                bd[j] = lt ? cd : td;
+                bi[j] = lt ? ci : ti;
+                cd = lt ? td : cd;
+                ci = lt ? ti : ci;
+              }
+            }
           }
         }
+        fence_before_sync();
+        mbar_arrive(&acc_empty[acc]);   // this thread's reads of the accumulator are done
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1u;
+        }
+      }
+      if (!kStore && my_row < n && !*s_abort) {
+#pragma unroll
+        for (int i = 0; i < T; ++i) cand[my_row * kT + i] = bd[i] < INFINITY ? bi[i] : -1;
+        for (int i = T; i < kT; ++i) cand[my_row * kT + i] = -1;
       }
     }
-    fence_before_sync();
-    __syncthreads();      // every lane read before the next tile's MMAs overwrite TMEM
-    fence_after_sync();
-  }
-  if (kStore) {
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kN);
-    return;
-  }
-  // both halves' lists go to shared memory (the operand buffers are idle now)
-  float* xd = reinterpret_cast<float*>(smem) + half * kM * T;
-  int32_t* xi = reinterpret_cast<int32_t*>(smem + 2 * kM * T * 4) + half * kM * T;
-#pragma unroll
-  for (int i = 0; i < T; ++i) {
-    xd[my_lane * T + i] = bd[i];
-    xi[my_lane * T + i] = bi[i];
   }
   fence_before_sync();
   __syncthreads();
-  if (half == 0 && my_row < n) {
-    const float* ad = reinterpret_cast<const float*>(smem) + my_lane * T;
-    const int32_t* ai = reinterpret_cast<const int32_t*>(smem + 2 * kM * T * 4) + my_lane * T;
-    const float* bd2 = ad + kM * T;
-    const int32_t* bi2 = ai + kM * T;
-    int a = 0, b = 0;
-    for (int i = 0; i < T; ++i) {   // merge two ascending lists, keep T
-      bool take_b = a >= T || (b < T && (bd2[b] < ad[a] || (bd2[b] == ad[a] && bi2[b] < ai[a])));
-      float vd = take_b ? bd2[b] : ad[a];
-      int32_t vi = take_b ? bi2[b] : ai[a];
-      cand[my_row * kT + i] = vd < INFINITY ? vi : -1;
-      if (take_b) ++b; else ++a;
-    }
-    for (int i = T; i < kT; ++i) cand[my_row * kT + i] = -1;
-  }
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, kN);
+  fence_after_sync();
+  if (warp == 1) tmem_dealloc(tmem, 2 * kN);
 }
 
 // Exact FP32 re-score of the kT candidates of every row (direct differences),
@@ -398,26 +454,102 @@ __global__ void rescore_kernel(const float* __restrict__ X, int64_t n, int d, co
   }
 }
 
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point, so the
+// library does not link the driver library.
+EncodeTiled encode_fn() {
+  static const EncodeTiled fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiled) nullptr;
+    }
+    return reinterpret_cast<EncodeTiled>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of a row-major FP32 matrix (rows x d) read in boxes of 32
+// elements x box_rows rows with the 128-byte swizzle; rows past the end read
+// as zeros.
+qk_status make_map(CUtensorMap* m, const float* base, int64_t rows, int d, int box_rows) {
+  const EncodeTiled enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available");
+    return QK_ERR_CUDA;
+  }
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0) {
+    set_error("tensor-core operands must be 16-byte aligned");
+    return QK_ERR_ARG;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)d * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)tc::kKS, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return QK_ERR_CUDA;
+  }
+  return QK_OK;
+}
+
+// Sets the kernel's shared-memory limit once (the first call is never inside a
+// stream capture) and returns the number of SMs of the current device.
+template <int T, bool kStore>
+qk_status prepare_kernel(int* n_sm) {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    err = cudaFuncSetAttribute(tc_score_kernel<T, kStore>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
+  });
+  QK_CUDA(err);
+  int dev = 0;
+  QK_CUDA(cudaGetDevice(&dev));
+  QK_CUDA(cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, dev));
+  return QK_OK;
+}
+
+template <int T, bool kStore>
+qk_status launch_score(const float* X, int64_t n, int d, const float* C, int K, const float* cnorm, int metric,
+                       int32_t* cand, int32_t* status, float* dout, int64_t ldd, int splits, int span,
+                       cudaStream_t s) {
+  CUtensorMap mx, mc;
+  QK_TRY(make_map(&mx, X, n, d, tc::kM));
+  QK_TRY(make_map(&mc, C, K, d, tc::kN));
+  int n_sm = 0;
+  QK_TRY((prepare_kernel<T, kStore>(&n_sm)));
+  const int64_t items = (n + tc::kM - 1) / tc::kM * splits;
+  const unsigned grid = (unsigned)std::min<int64_t>(items, n_sm);
+  tc_score_kernel<T, kStore><<<grid, tc::kThreads, tc::kSmem, s>>>(mx, mc, n, d, K, cnorm, metric, cand, status, dout,
+                                                                   ldd, splits, span, items);
+  QK_CUDA(cudaGetLastError());
+  return QK_OK;
+}
+
+}  // namespace
+
 qk_status launch_tc_nearest(const float* X, int64_t n, int d, const float* C, int K, int metric, int k,
                             int32_t* out_idx, float* out_dist, float* cnorm, int32_t* cand, int32_t* status,
                             cudaStream_t s) {
   if (n <= 0) return QK_OK;
-  if (d % tc::kKS != 0 || k < 1 || k > tc::kT) return QK_ERR_ARG;
+  if (d % tc::kKS != 0 || k < 1 || k > tc::kT || K < 1) return QK_ERR_ARG;
   row_norms_kernel<<<(unsigned)(((int64_t)K * 32 + 255) / 256), 256, 0, s>>>(C, K, d, cnorm);
   QK_CUDA(cudaGetLastError());
-  unsigned grid = (unsigned)((n + tc::kM - 1) / tc::kM);
-  if (k == 1) {
-    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<tc::kT1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 tc::kSmem));
-    tc_candidates_kernel<tc::kT1, false>
-        <<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, cand, status, nullptr, 0, 0);
-  } else {
-    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<tc::kT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 tc::kSmem));
-    tc_candidates_kernel<tc::kT, false>
-        <<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, cand, status, nullptr, 0, 0);
-  }
-  QK_CUDA(cudaGetLastError());
+  const int span = (K + tc::kN - 1) / tc::kN * tc::kN;
+  if (k == 1)
+    QK_TRY((launch_score<tc::kT1, false>(X, n, d, C, K, cnorm, metric, cand, status, nullptr, 0, 1, span, s)));
+  else
+    QK_TRY((launch_score<tc::kT, false>(X, n, d, C, K, cnorm, metric, cand, status, nullptr, 0, 1, span, s)));
   rescore_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, d, C, cand, metric, k, out_idx, out_dist);
   QK_CUDA(cudaGetLastError());
   return QK_OK;
@@ -428,28 +560,19 @@ int tc_candidates_per_row() { return tc::kT; }
 // Approximate distance matrix (L2: ||c||^2 - 2 <x, c>, without ||x||^2; IP:
 // -<x, c>) of every row against every centroid, written to dout with row
 // stride ldd (>= K).  cnorm must hold the centroids' squared norms.  The
-// centroids are split over blockIdx.y in spans of whole tiles so that a small
-// number of 128-row tiles still covers every SM.
+// centroids are split into ranges of whole tiles so that a small number of
+// 128-row tiles still gives every SM work.
 qk_status launch_tc_distances(const float* X, int64_t n, int d, const float* C, int K, const float* cnorm, int metric,
                               float* dout, int64_t ldd, int32_t* status, int n_sm, cudaStream_t s) {
   if (n <= 0 || K <= 0) return QK_OK;
   if (d % tc::kKS != 0 || ldd < K) return QK_ERR_ARG;
   const int64_t row_tiles = (n + tc::kM - 1) / tc::kM;
   const int col_tiles = (K + tc::kN - 1) / tc::kN;
-  int splits = (int)std::min<int64_t>(col_tiles, std::max<int64_t>(1, (4LL * n_sm + row_tiles - 1) / row_tiles));
+  int splits = (int)std::min<int64_t>(col_tiles, std::max<int64_t>(1, (2LL * n_sm + row_tiles - 1) / row_tiles));
   const int tiles_per_split = (col_tiles + splits - 1) / splits;
   splits = (col_tiles + tiles_per_split - 1) / tiles_per_split;
-  static bool attr_set = false;   // set once, outside any stream capture (the first call is never captured)
-  if (!attr_set) {
-    QK_CUDA(cudaFuncSetAttribute(tc_candidates_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 tc::kSmem));
-    attr_set = true;
-  }
-  dim3 grid((unsigned)row_tiles, (unsigned)splits);
-  tc_candidates_kernel<1, true><<<grid, tc::kThreads, tc::kSmem, s>>>(X, n, d, C, K, cnorm, metric, nullptr, status,
-                                                                      dout, ldd, tiles_per_split * tc::kN);
-  QK_CUDA(cudaGetLastError());
-  return QK_OK;
+  return launch_score<1, true>(X, n, d, C, K, cnorm, metric, nullptr, status, dout, ldd, splits,
+                               tiles_per_split * tc::kN, s);
 }
 
 qk_status launch_row_norms(const float* C, int64_t K, int d, float* out, cudaStream_t s) {
