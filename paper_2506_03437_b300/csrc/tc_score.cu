@@ -21,8 +21,11 @@
 //              K = 8 MMAs into a 128 x 256 FP32 accumulator in TMEM and commits
 //              them to the stage's "empty" mbarrier, which frees the stage for
 //              the producer when the MMAs have read it;
-//   warps 2-5  the epilogue: each thread owns one TMEM lane (one row), reads
-//              the accumulator with tcgen05.ld and keeps its row's candidates.
+//   warps 2.. the epilogue: several warps per quarter of the TMEM lanes (the
+//              quarter a warp may read is its number mod 4), each thread one
+//              row and one part of the columns; it reads the accumulator with
+//              tcgen05.ld and keeps its row's candidates, and the parts' lists
+//              are merged through shared memory at the end of a row tile.
 // Two accumulators (all 512 TMEM columns) alternate between the MMA issuer
 // and the epilogue ("acc full" / "acc empty" mbarriers), so the epilogue of
 // one tile of centroids runs while the MMAs of the next one do.  No CTA-wide
@@ -48,15 +51,29 @@ constexpr int kM = 128;        // rows per CTA tile (TMEM lanes)
 constexpr int kN = 256;        // centroids per tile (TMEM columns of one accumulator)
 constexpr int kKS = 32;        // K elements per stage (128 bytes of FP32: one swizzle row)
 constexpr int kStages = 4;     // shared-memory ring
-constexpr int kThreads = 192;  // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+
 constexpr int kT = 16;         // approximate candidates kept per row (k <= 8)
 constexpr int kT1 = 4;         // ... when only the nearest centroid is wanted
 
 constexpr int kStageA = kM * kKS * 4;    // 16 KB
 constexpr int kStageB = kN * kKS * 4;    // 32 KB
 constexpr int kStageBytes = kStageA + kStageB;
-// stages (1024-byte aligned for the swizzle), then the mbarriers and the TMEM address
-constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+// Threads of one kernel shape: warp 0 the producer, warp 1 the MMA issuer,
+// then EW epilogue warps, EW / 4 per quarter of the TMEM lanes; each of
+// those P = EW / 4 warps takes kN / P columns of every tile.  Keeping the
+// k = 1 candidates (T = 4) is the lighter epilogue, so it gets 16 warps; the
+// others 8.  Shared memory: the stages (1024-byte aligned for the swizzle),
+// the candidate lists of parts 1..P-1 (distances and indices), the mbarriers
+// and the TMEM address.
+template <int T, bool kStore>
+struct Shape {
+  static constexpr int EW = (!kStore && T <= 4) ? 16 : 8;
+  static constexpr int P = EW / 4;
+  static constexpr int kThreads = 64 + 32 * EW;
+  static constexpr int kEpi = 32 * EW;
+  static constexpr int kMerge = kStore ? 0 : (P - 1) * kM * T * 8;
+  static constexpr int kSmem = kStages * kStageBytes + kMerge + 1024 + 256;
+};
 
 // Instruction descriptor of kind::tf32 (PTX ISA, tcgen05 instruction
 // descriptor): D format F32 (bits 4-5 = 1), A and B format TF32 (bits 7-9
@@ -178,17 +195,21 @@ __global__ void row_norms_kernel(const float* __restrict__ C, int64_t K, int d, 
 // `span` centroids (whole tiles) number i % splits; the CTAs take items i =
 // blockIdx.x, blockIdx.x + gridDim.x, ...  mapX / mapC are TMA tensor maps
 // of X (n x d) and C (K x d) with boxes of 32 x 128 and 32 x 256 elements.
-template <int T, bool kStore>
-__global__ void __launch_bounds__(tc::kThreads, 1)
+template <int T, bool kStore, int kMetric>
+__global__ void __launch_bounds__(tc::Shape<T, kStore>::kThreads, 1)
     tc_score_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapC, int64_t n,
                     int d, int K, const float* __restrict__ cnorm, int metric, int32_t* __restrict__ cand,
                     int32_t* __restrict__ status, float* __restrict__ dout, int64_t ldd, int splits, int span,
                     int64_t n_items) {
   using namespace tc;
+  using S = Shape<T, kStore>;
+  constexpr int kMerge = S::kMerge;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // the stages must sit on 1024-byte boundaries (the swizzle atom)
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  float* mrg_d = reinterpret_cast<float*>(smem + kStages * kStageBytes);   // (P - 1) x kM x T
+  int32_t* mrg_i = reinterpret_cast<int32_t*>(mrg_d + (S::P - 1) * kM * T);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + kMerge);
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;
   uint64_t* acc_empty = acc_full + 2;
@@ -206,7 +227,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 4 * 32);
+      mbar_init(&acc_empty[i], S::kEpi);
     }
     mbar_init(drain, 1);
     *s_abort = 0;
@@ -311,15 +332,22 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
   } else {
     // ------------------------------------------------------------ epilogue
     const int quarter = warp & 3;                 // the TMEM lanes this warp may read
+    const int part = (warp - 2) >> 2;             // the part of the columns this warp takes
+    constexpr int kPart = kN / S::P;
     const int my_lane = quarter * 32 + lane;      // this thread's row within the tile
     const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int64_t item = blockIdx.x; item < n_items && !*s_abort; item += gridDim.x) {
+    // every epilogue thread walks every item, even after an abort (then
+    // without waiting), so all of them reach the named barriers equally often
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
       int64_t row0;
       int n_begin, n_end;
       range(item, row0, n_begin, n_end);
       const int64_t my_row = row0 + my_lane;
+      // this row's best T (distance, column) in ascending order.  A thread
+      // meets its columns in increasing order, so a strict comparison keeps
+      // equal distances in column order.
       float bd[T];
       int32_t bi[T];
 #pragma unroll
@@ -333,45 +361,51 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
           break;
         }
         fence_after_sync();
-        for (int c0 = 0; c0 < kN; c0 += 32) {
+        for (int c0 = part * kPart; c0 < (part + 1) * kPart; c0 += 32) {
           float v[32];
           tc::tmem_ld32(lane_addr + (uint32_t)(acc * kN + c0), v);
+          const int cbase = n0 + c0;
+          if (cbase + 32 <= K && kMetric == QK_METRIC_L2) {   // all 32 columns exist: vector loads of the norms
+            const float4* c4 = reinterpret_cast<const float4*>(cnorm + cbase);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float4 c = __ldg(c4 + i);
+              v[4 * i] = fmaf(-2.f, v[4 * i], c.x);
+              v[4 * i + 1] = fmaf(-2.f, v[4 * i + 1], c.y);
+              v[4 * i + 2] = fmaf(-2.f, v[4 * i + 2], c.z);
+              v[4 * i + 3] = fmaf(-2.f, v[4 * i + 3], c.w);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int col = cbase + i;
+              v[i] = col >= K ? INFINITY : (kMetric == QK_METRIC_L2 ? fmaf(-2.f, v[i], __ldg(&cnorm[col])) : -v[i]);
+            }
+          }
           if (kStore) {
             if (my_row < n) {
-              float* dst = dout + my_row * ldd + n0 + c0;
-              const bool whole = n0 + c0 + 32 <= K && (ldd & 3) == 0;   // 16-byte aligned stores
+              float* dst = dout + my_row * ldd + cbase;
+              if (cbase + 32 <= K && (ldd & 3) == 0) {   // 16-byte aligned stores
 #pragma unroll
-              for (int i = 0; i < 32; i += 4) {
-                float o[4];
+                for (int i = 0; i < 32; i += 4)
+                  reinterpret_cast<float4*>(dst + i)[0] = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+              } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  const int col = n0 + c0 + i + j;
-                  const float cn = col < K ? __ldg(&cnorm[col]) : INFINITY;
-                  o[j] = metric == QK_METRIC_L2 ? fmaf(-2.f, v[i + j], cn) : -v[i + j];
-                }
-                if (whole) {
-                  reinterpret_cast<float4*>(dst + i)[0] = make_float4(o[0], o[1], o[2], o[3]);
-                } else {
-#pragma unroll
-                  for (int j = 0; j < 4; ++j)
-                    if (n0 + c0 + i + j < K) dst[i + j] = o[j];
-                }
+                for (int i = 0; i < 32; ++i)
+                  if (cbase + i < K) dst[i] = v[i];
               }
             }
             continue;
           }
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            const int col = n0 + c0 + i;
-            const bool valid = col < K;
-            const float cn = valid ? __ldg(&cnorm[col]) : INFINITY;
-            const float dist = metric == QK_METRIC_L2 ? fmaf(-2.f, v[i], cn) : (valid ? -v[i] : INFINITY);
-            if (dist < bd[T - 1] || (dist == bd[T - 1] && col < bi[T - 1])) {
-              float cd = dist;
-              int32_t ci = col;
+            const bool pass = v[i] < bd[T - 1];
+            if (__any_sync(0xffffffffu, pass) && pass) {   // the insertion only where some lane needs it
+              float cd = v[i];
+              int32_t ci = cbase + i;
 #pragma unroll
-              for (int j = 0; j < T; ++j) {   // insert into the sorted registers
-                const bool lt = cd < bd[j] || (cd == bd[j] && ci < bi[j]);
+              for (int j = 0; j < T; ++j) {
+                const bool lt = cd < bd[j];
                 const float td = bd[j];
                 const int32_t ti = bi[j];
                 bd[j] = lt ? cd : td;
@@ -389,10 +423,44 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
           acc_phase ^= 1u;
         }
       }
-      if (!kStore && my_row < n && !*s_abort) {
+      if (!kStore) {
+        // parts 1..P-1 leave their lists in shared memory; part 0 merges them
+        // into its own by (distance, column) and writes the row's candidates
+        if (part > 0) {
+          float* od = mrg_d + ((part - 1) * kM + my_lane) * T;
+          int32_t* oi = mrg_i + ((part - 1) * kM + my_lane) * T;
 #pragma unroll
-        for (int i = 0; i < T; ++i) cand[my_row * kT + i] = bd[i] < INFINITY ? bi[i] : -1;
-        for (int i = T; i < kT; ++i) cand[my_row * kT + i] = -1;
+          for (int i = 0; i < T; ++i) {
+            od[i] = bd[i];
+            oi[i] = bi[i];
+          }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(S::kEpi) : "memory");
+        if (part == 0 && my_row < n && !*s_abort) {
+          for (int o = 1; o < S::P; ++o) {
+            const float* od = mrg_d + ((o - 1) * kM + my_lane) * T;
+            const int32_t* oi = mrg_i + ((o - 1) * kM + my_lane) * T;
+            for (int e = 0; e < T; ++e) {
+              float cd = od[e];
+              int32_t ci = oi[e];
+              if (!(cd < INFINITY)) break;
+#pragma unroll
+              for (int j = 0; j < T; ++j) {
+                const bool lt = cd < bd[j] || (cd == bd[j] && ci < bi[j]);
+                const float td = bd[j];
+                const int32_t ti = bi[j];
+                bd[j] = lt ? cd : td;
+                bi[j] = lt ? ci : ti;
+                cd = lt ? td : cd;
+                ci = lt ? ti : ci;
+              }
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < T; ++i) cand[my_row * kT + i] = bd[i] < INFINITY ? bi[i] : -1;
+          for (int i = T; i < kT; ++i) cand[my_row * kT + i] = -1;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(S::kEpi) : "memory");   // the lists are read before reuse
       }
     }
   }
@@ -505,12 +573,13 @@ qk_status make_map(CUtensorMap* m, const float* base, int64_t rows, int d, int b
 
 // Sets the kernel's shared-memory limit once (the first call is never inside a
 // stream capture) and returns the number of SMs of the current device.
-template <int T, bool kStore>
+template <int T, bool kStore, int kMetric>
 qk_status prepare_kernel(int* n_sm) {
   static std::once_flag once;
   static cudaError_t err = cudaSuccess;
   std::call_once(once, [] {
-    err = cudaFuncSetAttribute(tc_score_kernel<T, kStore>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
+    err = cudaFuncSetAttribute(tc_score_kernel<T, kStore, kMetric>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tc::Shape<T, kStore>::kSmem);
   });
   QK_CUDA(err);
   int dev = 0;
@@ -519,21 +588,30 @@ qk_status prepare_kernel(int* n_sm) {
   return QK_OK;
 }
 
-template <int T, bool kStore>
-qk_status launch_score(const float* X, int64_t n, int d, const float* C, int K, const float* cnorm, int metric,
-                       int32_t* cand, int32_t* status, float* dout, int64_t ldd, int splits, int span,
-                       cudaStream_t s) {
+template <int T, bool kStore, int kMetric>
+qk_status launch_score_m(const float* X, int64_t n, int d, const float* C, int K, const float* cnorm, int32_t* cand,
+                         int32_t* status, float* dout, int64_t ldd, int splits, int span, cudaStream_t s) {
+  using S = tc::Shape<T, kStore>;
   CUtensorMap mx, mc;
   QK_TRY(make_map(&mx, X, n, d, tc::kM));
   QK_TRY(make_map(&mc, C, K, d, tc::kN));
   int n_sm = 0;
-  QK_TRY((prepare_kernel<T, kStore>(&n_sm)));
+  QK_TRY((prepare_kernel<T, kStore, kMetric>(&n_sm)));
   const int64_t items = (n + tc::kM - 1) / tc::kM * splits;
   const unsigned grid = (unsigned)std::min<int64_t>(items, n_sm);
-  tc_score_kernel<T, kStore><<<grid, tc::kThreads, tc::kSmem, s>>>(mx, mc, n, d, K, cnorm, metric, cand, status, dout,
-                                                                   ldd, splits, span, items);
+  tc_score_kernel<T, kStore, kMetric><<<grid, S::kThreads, S::kSmem, s>>>(mx, mc, n, d, K, cnorm, kMetric, cand,
+                                                                          status, dout, ldd, splits, span, items);
   QK_CUDA(cudaGetLastError());
   return QK_OK;
+}
+
+template <int T, bool kStore>
+qk_status launch_score(const float* X, int64_t n, int d, const float* C, int K, const float* cnorm, int metric,
+                       int32_t* cand, int32_t* status, float* dout, int64_t ldd, int splits, int span,
+                       cudaStream_t s) {
+  if (metric == QK_METRIC_L2)
+    return launch_score_m<T, kStore, QK_METRIC_L2>(X, n, d, C, K, cnorm, cand, status, dout, ldd, splits, span, s);
+  return launch_score_m<T, kStore, QK_METRIC_IP>(X, n, d, C, K, cnorm, cand, status, dout, ldd, splits, span, s);
 }
 
 }  // namespace
