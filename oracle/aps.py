@@ -45,6 +45,12 @@ library):
       base rows (level 0) are ranked by -<q, x>, and rho is ||q - x_k|| (R1).
       On unit-norm rows and queries -<q, x> = (||q - x||^2 - 2) / 2, so
       there the inner-product search coincides with the L2 search.
+  R12 SPANN's early-termination rule (Sec. 2 "Early Termination", the
+      comparator of Table 6): scan the candidates of S, nearest first, whose
+      Euclidean centroid distance is at most (1 + eps) times the nearest
+      one's; eps is the rule's tuned parameter.  S is the candidate set APS
+      uses (the f_M nearest with one level, the upper level's APS result
+      with two), and the candidates kept form a prefix of S.
 """
 
 import math
@@ -59,7 +65,7 @@ class Params:
     """Search parameters (defaults from Sec. 5 and Sec. 8.1)."""
 
     def __init__(self, k=10, recall_target=0.9, nprobe=0, f_M=(0.1, 0.25),
-                 tau_rho=0.01, upper_recall=0.99, beta_mode="table", p0_reading="raw"):
+                 tau_rho=0.01, upper_recall=0.99, beta_mode="table", p0_reading="raw", ratio_eps=0.0):
         self.k = k
         self.recall_target = recall_target
         self.nprobe = nprobe
@@ -70,6 +76,7 @@ class Params:
         if p0_reading not in ("raw", "normalised"):
             raise ValueError("p0_reading is 'raw' (R3) or 'normalised' (Eq. 8 read literally)")
         self.p0_reading = p0_reading
+        self.ratio_eps = ratio_eps      # > 0 with recall_target <= 0: SPANN's rule (R12)
 
 
 def n_candidates(f, n):
@@ -224,6 +231,13 @@ def aps_level(q, level, cand, cand_D, k, tau_R, params, d, metric, table,
     return dict(dist=R.dist, ids=R.ids, scanned=order, r=float(r), trace=trace, steps=steps)
 
 
+def ratio_rule_count(cand_D, eps):
+    """R12: how many candidates (sorted by squared distance D) lie within
+    (1 + eps) of the nearest one's Euclidean distance."""
+    r = np.sqrt(np.maximum(np.asarray(cand_D, np.float64), 0.0))
+    return int(np.count_nonzero(r <= (1.0 + eps) * r[0])) if r.shape[0] else 0
+
+
 def root_candidates(q, top_level, f):
     """Score the single top partition (all centroids of the top level, squared
     Euclidean distance, R11) and keep M."""
@@ -253,7 +267,8 @@ def search(levels, Q, params, metric=L2):
     out_r = np.zeros(nq)
     scanned = [[None] * nq for _ in range(L)]
     traces = [[None] * nq for _ in range(L)]
-    fixed = params.nprobe if params.recall_target <= 0 else 0
+    ratio = params.recall_target <= 0 and params.ratio_eps > 0
+    fixed = params.nprobe if params.recall_target <= 0 and not ratio else 0
     for j in range(nq):
         q = Q[j]
         top = levels[L - 1]
@@ -271,8 +286,9 @@ def search(levels, Q, params, metric=L2):
             scanned[1][j] = [int(cand1[p]) for p in res1["scanned"]]
             traces[1][j] = res1["trace"]
             cand, cD = res1["ids"], res1["dist"]
+        nfix = ratio_rule_count(cD, params.ratio_eps) if ratio else fixed     # R12
         res = aps_level(q, levels[0], list(cand), cD, k, params.recall_target,
-                        params, d, metric, table, fixed_nprobe=fixed)
+                        params, d, metric, table, fixed_nprobe=nfix)
         n = res["ids"].shape[0]
         out_D[j, :n] = res["dist"]
         out_I[j, :n] = res["ids"]

@@ -798,7 +798,7 @@ qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, c
 static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,
                              const int32_t* nprobe_q, int64_t* out_ids, float* out_dist, int32_t* out_nprobe,
                              float* out_recall, void* stream, int32_t* scan0 = nullptr, int32_t cap0 = 0,
-                             int32_t* scan1 = nullptr, int32_t cap1 = 0) {
+                             int32_t* scan1 = nullptr, int32_t cap1 = 0, float ratio_eps = 0.f) {
   QK_TRY(check_ready(ix));
   if (nq < 0 || k < 1 || k > 1024 || (nq > 0 && (!q || !out_ids || !out_dist))) {
     set_error("invalid search arguments");
@@ -854,6 +854,12 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   a.Q = dq;
   a.nq = nq;
   a.nprobe_q = a.fixed_nprobe > 0 ? nprobe_q : nullptr;
+  if (ratio_eps > 0.f) {   // SPANN's rule within the candidate set APS uses
+    a.ratio_eps = ratio_eps;
+    if (a.L == 1) a.M_root = n_candidates(ix->cfg.f_M_leaf, ix->n_leaf);
+    a.kcap = std::max({a.k0, a.k1, a.M_root});
+    a.mcap = std::max({a.M_root, a.k1, 1});
+  }
   a.out_ids = dids;
   a.out_dist = ddist;
   a.out_nprobe = out_nprobe ? dnp : nullptr;
@@ -892,6 +898,18 @@ qk_status qk_search_scanned(qk_index* ix, const float* q, int64_t nq, int32_t k,
   QK_GUARD_BEGIN
   return search_impl(ix, q, nq, k, recall_target, nprobe, nullptr, out_ids, out_dist, out_nprobe, out_recall, stream,
                      out_scanned0, cap0, out_scanned1, cap1);
+  QK_GUARD_END
+}
+
+qk_status qk_search_ratio(qk_index* ix, const float* q, int64_t nq, int32_t k, float eps, int64_t* out_ids,
+                          float* out_dist, int32_t* out_nprobe, int32_t* out_scanned0, int32_t cap0, void* stream) {
+  QK_GUARD_BEGIN
+  if (!(eps > 0.f) || !(eps < INFINITY)) {
+    set_error("the ratio rule needs a finite eps > 0");
+    return QK_ERR_ARG;
+  }
+  return search_impl(ix, q, nq, k, 0.0f, 1, nullptr, out_ids, out_dist, out_nprobe, nullptr, stream, out_scanned0,
+                     cap0, nullptr, 0, eps);
   QK_GUARD_END
 }
 

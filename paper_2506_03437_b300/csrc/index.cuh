@@ -75,6 +75,7 @@ struct SearchArgs {
   int32_t scan_cap0 = 0;
   int32_t* scan1 = nullptr;      // optional: level-1 partitions scanned per query, nq x scan_cap1, -1 padded
   int32_t scan_cap1 = 0;
+  float ratio_eps = 0.f;         // > 0: SPANN's rule at level 0 (scan the prefix of S within (1 + eps) of the nearest)
   int32_t* xs_M = nullptr;       // batched APS: per query, leaf candidates exported (-1: refused query)
   int32_t* xs_cand = nullptr;    // nq x xs_mcap leaf candidate partitions, nearest first
   double* xs_t = nullptr;        // nq x xs_mcap their bisector distances t_i

@@ -753,6 +753,19 @@ struct Block {
     sort_range(rc);
   }
 
+  // SPANN's early-termination rule over the candidates (cpart, cD) sorted by
+  // squared distance: how many have a Euclidean distance within (1 + eps) of
+  // the nearest one's (a prefix of the list; the same count in every thread).
+  __device__ int ratio_count(int M, float eps) {
+    const float lim = (1.f + eps) * sqrtf(fmaxf(cD[0], 0.f));
+    int n = 0;
+    for (int base = 0; base < M; base += kThreads) {
+      const int i = base + tid;
+      n += __syncthreads_count(i < M && sqrtf(fmaxf(cD[i], 0.f)) <= lim);
+    }
+    return n;
+  }
+
   // R -> candidate list of the next level.
   __device__ int take_candidates() {
     int M = s->r_count;
@@ -879,7 +892,8 @@ __global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
       __syncthreads();
       continue;
     }
-    const int fixed = args.nprobe_q ? args.nprobe_q[qi] : args.fixed_nprobe;
+    int fixed = args.nprobe_q ? args.nprobe_q[qi] : args.fixed_nprobe;
+    if (args.ratio_eps > 0.f) fixed = b.ratio_count(M, args.ratio_eps);
     b.metric = args.metric;
     if (args.scan0) b.record_start(args.scan0 + qi * args.scan_cap0, args.scan_cap0);
     b.aps(args.lv[0], M, args.k0, args.kq, args.tau0, fixed, args.hits0, args.mode0, args.lv[0].vec, r, np);

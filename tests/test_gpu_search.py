@@ -246,3 +246,22 @@ def test_per_query_nprobe_on_two_levels_equals_fixed_nprobe(I):
         assert np.array_equal(ui, fi) and np.array_equal(ud, fd)
         sel = per == n
         assert np.array_equal(gi[sel], fi[sel])
+
+
+@pytest.mark.parametrize("two_level", [False, True])
+def test_ratio_rule_matches_oracle(I, two_level):
+    """SPANN's early-termination rule (reading R12): the partitions scanned, their
+    number and the results equal the oracle's for several eps."""
+    X, ids, Q = synth.aps_search(seed=15, n=20_000, d=64, n_comp=40, sigma=1.0, nq=120)
+    levels = kmeans.build_index(X, ids, 150, 10 if two_level else 0, iters=4, seed=5)
+    fm = (0.2, 0.5) if two_level else (0.2,)
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.2, f_M_parent=0.5)
+    counts = []
+    for eps in (0.02, 0.1, 0.3):
+        gi, gd, gn, s0 = ix.search_ratio(Q, 10, eps, cap0=30)
+        orc = aps.search(levels, Q, aps.Params(k=10, recall_target=0.0, ratio_eps=eps, f_M=fm))
+        n_ok, n_exc = compare_search((gi, gd, gn, np.full(Q.shape[0], np.nan), s0, None), orc, 10, check_r=False,
+                                     label=f"ratio rule eps {eps}, {'two levels' if two_level else 'one level'}")
+        assert n_exc == 0
+        counts.append(gn.mean())
+    assert counts[0] < counts[-1]                  # the rule really varied nprobe
