@@ -608,6 +608,12 @@ qk_status qk_aps_batch_create(qk_index* index, int64_t max_nq, int32_t k, qk_aps
 void qk_aps_batch_destroy(qk_aps_batch* plan);
 /* Number of rounds, 1 to 16 (default 4). */
 qk_status qk_aps_batch_set_rounds(qk_aps_batch* plan, int32_t rounds);
+/* How a round's items are scanned.  0 (the only mode available) = on the
+ * CUDA cores, FP32 direct differences for every row.  1 = on the tensor cores
+ * (TF32 MMAs with a margin filter and an exact FP32 re-score) is refused with
+ * QK_ERR_UNSUPPORTED: it is held back until a fault seen on a B300 is
+ * explained. */
+qk_status qk_aps_batch_set_scan(qk_aps_batch* plan, int32_t mode);
 /* Tiles of the grouped scan (as qk_batch_set_tiles; default 2 queries per
  * warp, tile_rows 8192 / d capped to [8, 64], chunk_rows 4096). */
 qk_status qk_aps_batch_set_tiles(qk_aps_batch* plan, const qk_batch_tiles* tiles);
@@ -631,6 +637,10 @@ qk_status qk_aps_batch_stage_times(qk_aps_batch* plan, float* ms);
  * items Algorithm 1 took in (the rest were scanned beyond a query's stop);
  * arrays of the plan's round count. */
 qk_status qk_aps_batch_round_stats(qk_aps_batch* plan, int64_t* asked, int64_t* taken);
+/* For the last batch on the tensor cores (synchronous): how many (query,
+ * partition chunk) lists could not vouch for their top-k and were scanned
+ * exactly instead. */
+qk_status qk_aps_batch_fallbacks(qk_aps_batch* plan, int64_t* n);
 
 /* SPANN's early-termination rule, the comparator of Sec. 2 "Early Termination"
  * and Table 6: query i scans the candidates of its set S (the same S as APS

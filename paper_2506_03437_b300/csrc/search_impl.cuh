@@ -778,8 +778,11 @@ struct Block {
   }
 };
 
+// Three CTAs per SM keep the memory system busy while each waits on its own
+// query's tiles; up to d = 256 their shared memory allows it, so the
+// registers are held to a third of the file (beyond, two CTAs fit anyway).
 template <int TPR, int NV>
-__global__ void __launch_bounds__(kThreads) aps_search_kernel(SearchArgs args) {
+__global__ void __launch_bounds__(kThreads, (NV * 4 * TPR <= 256) ? 3 : 2) aps_search_kernel(SearchArgs args) {
   using B = Block<TPR, NV>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ Scalars sc;

@@ -42,22 +42,15 @@
 #include <string>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace qk {
 
 namespace tc {
 
-constexpr int kM = 128;        // rows per CTA tile (TMEM lanes)
-constexpr int kN = 256;        // centroids per tile (TMEM columns of one accumulator)
-constexpr int kKS = 32;        // K elements per stage (128 bytes of FP32: one swizzle row)
-constexpr int kStages = 4;     // shared-memory ring
-
 constexpr int kT = 16;         // approximate candidates kept per row (k <= 8)
 constexpr int kT1 = 4;         // ... when only the nearest centroid is wanted
 
-constexpr int kStageA = kM * kKS * 4;    // 16 KB
-constexpr int kStageB = kN * kKS * 4;    // 32 KB
-constexpr int kStageBytes = kStageA + kStageB;
 // Threads of one kernel shape: warp 0 the producer, warp 1 the MMA issuer,
 // then EW epilogue warps, EW / 4 per quarter of the TMEM lanes; each of
 // those P = EW / 4 warps takes kN / P columns of every tile.  Keeping the
@@ -74,107 +67,6 @@ struct Shape {
   static constexpr int kMerge = kStore ? 0 : (P - 1) * kM * T * 8;
   static constexpr int kSmem = kStages * kStageBytes + kMerge + 1024 + 256;
 };
-
-// Instruction descriptor of kind::tf32 (PTX ISA, tcgen05 instruction
-// descriptor): D format F32 (bits 4-5 = 1), A and B format TF32 (bits 7-9
-// and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
-// M >> 4 at bits 24-28, dense, no negation.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                            ((uint32_t)(kM >> 4) << 24);
-
-// Shared-memory matrix descriptor (PTX ISA, tcgen05 shared memory
-// descriptor): start address >> 4 at bits 0-13, leading-dimension byte
-// offset >> 4 at bits 16-29, stride-dimension byte offset >> 4 at bits 32-45,
-// the fixed value 0b001 at bits 46-48, base offset 0 (the stages are 1024-byte
-// aligned), swizzle mode at bits 61-63 (2 = 128-byte swizzle).  The operands
-// are K-major with a 128-byte swizzle: a row's 32 FP32 of the stage form one
-// 128-byte swizzle row and 8 rows one 1024-byte atom, so the stride between
-// 8-row groups is 1024 bytes and the leading offset is unused (one atom spans
-// the stage's whole K).  The MMA of K elements 8i..8i+7 starts 32i bytes in.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;                     // leading offset 16 bytes (unused)
-  d |= (uint64_t)(1024 >> 4) << 32;           // 8-row group stride
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
-  return d;
-}
-
-// 2-D TMA tile copy global -> shared (box given by the tensor map), completing
-// on `bar`; x is the element column (a multiple of 32 here, so 128-byte
-// aligned), y the row.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_before_sync() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 8 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 }  // namespace tc
 
