@@ -913,39 +913,71 @@ def run_sweep(args):
                              "mean_nprobe": round(on.double().mean().item(), 2), "qps": round(NQ / ms * 1e3, 1)})
             ix.check(stream)
             del ix
-    # early-termination comparators on the default targets (tau_1 = 0.99): the fixed nprobe
-    # that reaches mean recall@10 0.9, and the "oracle" nprobe (each query's smallest nprobe
-    # whose own recall@10 reaches 0.9, found by scanning nprobe = 1..64)
+    # Early-termination comparators on the default upper target (tau_1 = 0.99), the
+    # synthetic counterpart of Table 6, at recall targets 0.8, 0.9 and 0.95:
+    #   fixed   the smallest nprobe whose mean recall@10 reaches the target;
+    #   SPANN   the ratio rule (qk_search_ratio) with eps bisected to the smallest whose
+    #           mean recall@10 reaches the target, as its threshold is tuned;
+    #   oracle  each query's smallest nprobe whose own recall@10 reaches it (nprobe 1..64);
+    #   APS     the grid's (0.99, target) entry.
     ix = I.Index(D, n_leaf=N_LEAF, n_parent=N_PARENT, kmeans_iters=ITERS, seed=SEED,
                  f_M_leaf=F_M_LEAF, f_M_parent=F_M_PARENT)
     ix.load(Xd, idd, leaf_centroids=C0, leaf_of_row=lor, parent_centroids=C1, parent_of_leaf=pol)
     kth = gtD[:, K - 1]
     thr = kth + 1e-5 * kth.abs() + 1e-5
     Q64 = Qd.double()
-    oracle_np = torch.full((NQ,), 64, dtype=torch.int32, device="cuda")
-    fixed_np = None
+
+    def per_query_recall(fi):
+        rows = X64[fi.clamp(min=0)]
+        return ((fi >= 0) & (((rows - Q64[:, None, :]) ** 2).sum(-1) <= thr[:, None])).sum(1).double() / K
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return round(NQ / (e0.elapsed_time(e1) / args.steps) * 1e3, 1)
+
+    per_n = {}
     for n_ in range(1, 65):
         fi, _, _, _ = ix.search(Qd, K, recall_target=0.0, nprobe=n_, stream=stream)
-        rows = X64[fi.clamp(min=0)]
-        hit = ((fi >= 0) & (((rows - Q64[:, None, :]) ** 2).sum(-1) <= thr[:, None])).sum(1)
-        per_q = hit.double() / K
-        oracle_np[(per_q >= 0.9) & (oracle_np == 64)] = n_
-        if fixed_np is None and per_q.mean().item() >= 0.9:
-            fixed_np = n_
-    on_ = oracle_np.cpu().numpy()
-    oi, od = ix.search_nprobe(Qd, K, oracle_np, stream=stream)
-    orc_rec = recall(torch, X64, Qd, oi, gtD, K)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        ix.search_nprobe(Qd, K, oracle_np, out=(oi, od), stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    orc = {"mean_nprobe": round(float(on_.mean()), 2), "recall_at_10": round(orc_rec, 4),
-           "qps": round(NQ / (e0.elapsed_time(e1) / args.steps) * 1e3, 1),
-           "note": "per-query nprobe known only after the fact: a lower bound on the partitions any "
-                   "early-termination rule must scan"}
+        per_n[n_] = per_query_recall(fi)
+    table = []
+    for target in (0.8, 0.9, 0.95):
+        row = {"target": target}
+        aps_g = next((g for g in grid if g["tau_1"] == 0.99 and g["tau_0"] == target), None)
+        if aps_g:
+            row["aps"] = {k_: aps_g[k_] for k_ in ("recall_at_10", "mean_nprobe", "qps")}
+        fixed_np = next((n_ for n_ in range(1, 65) if per_n[n_].mean().item() >= target), None)
+        if fixed_np:
+            fo = ix.search(Qd, K, recall_target=0.0, nprobe=fixed_np, stream=stream)
+            row["fixed"] = {"nprobe": fixed_np, "recall_at_10": round(per_n[fixed_np].mean().item(), 4),
+                            "qps": timed(lambda: ix.search(Qd, K, recall_target=0.0, nprobe=fixed_np, out=fo,
+                                                           stream=stream))}
+        lo, hi = 1e-4, 4.0
+        if per_query_recall(ix.search_ratio(Qd, K, hi, stream=stream)[0]).mean().item() >= target:
+            for _ in range(24):
+                mid = (lo * hi) ** 0.5
+                if per_query_recall(ix.search_ratio(Qd, K, mid, stream=stream)[0]).mean().item() >= target:
+                    hi = mid
+                else:
+                    lo = mid
+            so = ix.search_ratio(Qd, K, hi, stream=stream)
+            row["spann"] = {"eps": round(hi, 5), "mean_nprobe": round(so[2].double().mean().item(), 2),
+                            "recall_at_10": round(per_query_recall(so[0]).mean().item(), 4),
+                            "qps": timed(lambda: ix.search_ratio(Qd, K, hi, stream=stream))}
+        oracle_np = torch.full((NQ,), 64, dtype=torch.int32, device="cuda")
+        for n_ in range(64, 0, -1):
+            oracle_np[per_n[n_] >= target] = n_
+        oi, od = ix.search_nprobe(Qd, K, oracle_np, stream=stream)
+        row["oracle"] = {"mean_nprobe": round(oracle_np.double().mean().item(), 2),
+                         "recall_at_10": round(recall(torch, X64, Qd, oi, gtD, K), 4),
+                         "qps": timed(lambda: ix.search_nprobe(Qd, K, oracle_np, out=(oi, od), stream=stream))}
+        table.append(row)
+        print(json.dumps({"early_termination": row}), file=sys.stderr, flush=True)
     best = max((g for g in grid if g["recall_at_10"] >= 0.9), key=lambda g: g["qps"], default=None)
     print(json.dumps({
         "metric": "per-level recall-target sweep (QPS and recall@10 per (tau_1, tau_0))",
@@ -953,7 +985,9 @@ def run_sweep(args):
         "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded Gaussian mixture; stands in for Sift1M-shaped data)",
         "config": {"workload": WORKLOAD, "best_at_recall_0.9": best, "grid": grid,
-                   "fixed_nprobe_at_recall_0.9": fixed_np, "oracle_nprobe": orc},
+                   "early_termination": table,
+                   "note": "oracle nprobe is known only after the fact: a lower bound on the partitions any "
+                           "early-termination rule must scan"},
         "clocks": clk.summary()}), flush=True)
 
 
