@@ -23,8 +23,17 @@
  *  - Device buffers must be memory of the current GPU (or managed memory).
  *  - Calls on one index are not thread-safe; use one index per host thread or
  *    serialise the calls.  Searches with device buffers may be in flight on up
- *    to 16 streams at once; insert, delete, maintain and build must not overlap
- *    a search in flight (synchronise its stream first).
+ *    to 16 streams at once.
+ *  - Copy-on-write views (Sec. 9, "Concurrency"): every search reads the
+ *    version of the index that was current when it was launched, to its end.
+ *    Insert, delete, build, load and a maintenance commit need not wait for
+ *    the searches in flight: they build the next version beside the current
+ *    one and publish it when they return; what the older versions use is
+ *    freed once the searches launched on them have completed (checked at the
+ *    next update, and waited for by qk_destroy).  A search launched after an
+ *    update returns reads the updated version.  A search that the caller
+ *    captured into a CUDA graph is not tracked: replay such a graph only
+ *    while the version it captured is current (qk_stats' version).
  */
 #ifndef QUAKE_B300_H
 #define QUAKE_B300_H
@@ -207,12 +216,14 @@ typedef struct {
   double mean_size;           /* live vectors per leaf partition */
   int64_t arena_rows;         /* rows reserved in the leaf arena */
   int64_t arena_used;         /* rows below the free tail: partitions' rooms and holes */
-  int64_t arena_holes;        /* rows left behind by partitions that moved to the tail */
+  int64_t arena_holes;        /* rows below the tail that no partition holds (moved-out rooms) */
   int64_t arena_free;         /* rows of the free tail */
   int64_t arena_bytes;        /* device bytes of the arena (FP32 rows, ids, low-precision copy) */
   int64_t hits[2];            /* scanned (query, partition) pairs since the last reset, per level */
   int64_t queries_seen;       /* queries searched since the last build or maintenance (|W|) */
   uint64_t version;           /* changes with every build, insert, delete and maintenance commit */
+  int64_t searches_in_flight; /* search launches not yet known to have completed */
+  int64_t retired_rows;       /* arena rows kept, among the holes, for searches of older versions */
 } qk_index_stats;
 qk_status qk_stats(const qk_index* index, qk_index_stats* out);
 
@@ -223,8 +234,12 @@ qk_status qk_stats(const qk_index* index, qk_index_stats* out);
  * index; centroids are not moved) and is appended to that leaf partition,
  * in batch order.  An id already in the index or repeated in the batch gives
  * QK_ERR_DUP_ID and NaN gives QK_ERR_ARG; in both cases nothing is inserted.
- * A partition whose reserved rows run out is moved, with all others, into a
- * freshly laid-out arena.  Synchronous.
+ * The new rows go behind each partition's live rows, which no published
+ * version reads.  A partition whose reserved rows run out is copied to free
+ * arena rows with more room (a range a finished version gave back, else the
+ * free tail); when none is large enough the arena is first laid out again
+ * into new memory.  Returns once the new version is published; searches in
+ * flight keep the old one.  Synchronous.
  */
 qk_status qk_insert(qk_index* index, const float* x, const int64_t* ids, int64_t n, void* stream);
 
@@ -233,6 +248,8 @@ qk_status qk_insert(qk_index* index, const float* x, const int64_t* ids, int64_t
  * partition, the vector is removed with immediate compaction).  Deletes apply
  * in order; each moves the partition's last row into the freed slot.  Unknown
  * ids are skipped; *n_removed (if not NULL) receives the number removed.
+ * Every partition that loses a row is first copied to free arena rows, and
+ * the deletes edit the copy, so searches in flight keep the old version.
  * Synchronous.
  */
 qk_status qk_delete(qk_index* index, const int64_t* ids, int64_t n, int64_t* n_removed, void* stream);
@@ -408,9 +425,9 @@ qk_status qk_maintain(qk_index* index, const qk_maint_params* params, qk_maint_a
  *    streams (or other host threads) meanwhile; inserts and deletes must
  *    not.  The log arguments are as for qk_maintain.  Returns when the new
  *    structure is complete.  It needs room for a second arena.
- *  - qk_maintain_commit makes the prepared structure the index's and frees
- *    the old one.  No search of the index may be in flight.  It is quick
- *    (pointer and host-state exchange plus freeing the old arena).
+ *  - qk_maintain_commit makes the prepared structure the index's.  Searches
+ *    in flight keep reading the old one, which is freed once they have
+ *    completed.  It is quick (pointer and host-state exchange).
  *    QK_ERR_STATE if nothing was prepared, or if the index changed (insert,
  *    delete, build, load, maintenance) after the prepare: the prepared pass
  *    is then discarded.

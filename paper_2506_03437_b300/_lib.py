@@ -78,7 +78,8 @@ class QkIndexStats(C.Structure):
                 ("min_size", C.c_int32), ("max_size", C.c_int32), ("mean_size", C.c_double),
                 ("arena_rows", C.c_int64), ("arena_used", C.c_int64), ("arena_holes", C.c_int64),
                 ("arena_free", C.c_int64), ("arena_bytes", C.c_int64), ("hits", C.c_int64 * 2),
-                ("queries_seen", C.c_int64), ("version", C.c_uint64)]
+                ("queries_seen", C.c_int64), ("version", C.c_uint64), ("searches_in_flight", C.c_int64),
+                ("retired_rows", C.c_int64)]
 
 
 class QkServerStats(C.Structure):

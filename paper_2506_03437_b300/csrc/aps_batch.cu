@@ -484,6 +484,8 @@ int unit_queries(const qk_aps_batch* b, bool tensor) {
 qk_status refresh(qk_aps_batch* b, cudaStream_t s) {
   qk_index* ix = b->ix;
   if (b->version == ix->version && b->K == ix->n_leaf) return QK_OK;
+  // the plan's batches still in flight on s use the workspace re-sized below
+  QK_CUDA(cudaStreamSynchronize(s));
   const int32_t K = ix->n_leaf;
   const int32_t mcap = n_candidates(ix->cfg.f_M_leaf, K);
   const int CH = b->tiles.chunk_rows;
@@ -944,7 +946,9 @@ qk_status qk_aps_batch_search(qk_aps_batch* b, const float* q, int64_t nq, float
   if (nq == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   QK_TRY(refresh(b, s));
-  return enqueue(b, q, nq, recall_target, out_ids, out_dist, out_nprobe, out_recall, out_scanned0, cap0, s);
+  QK_TRY(enqueue(b, q, nq, recall_target, out_ids, out_dist, out_nprobe, out_recall, out_scanned0, cap0, s));
+  note_readers(b->ix, s);
+  return QK_OK;
   QK_GUARD_END
 }
 
@@ -1010,6 +1014,7 @@ qk_status qk_aps_batch_replay(qk_aps_batch* b, void* stream) {
     return QK_ERR_STATE;
   }
   QK_CUDA(cudaGraphLaunch(b->graph, (cudaStream_t)stream));
+  note_readers(b->ix, (cudaStream_t)stream);
   b->ix->queries_seen += b->graph_nq;
   return QK_OK;
   QK_GUARD_END

@@ -472,6 +472,8 @@ bool tiles_valid(const qk_batch* b, const qk_batch_tiles& t, std::string* why) {
 qk_status refresh(qk_batch* b, cudaStream_t s) {
   qk_index* ix = b->ix;
   if (b->version == ix->version && b->K == ix->n_leaf) return QK_OK;
+  // the plan's batches still in flight on s use the workspace re-sized below
+  QK_CUDA(cudaStreamSynchronize(s));
   const int32_t K = ix->n_leaf;
   const int64_t ldd = ((int64_t)K + 3) / 4 * 4;
   const int64_t need_cand =
@@ -784,7 +786,9 @@ qk_status qk_batch_search(qk_batch* b, const float* q, int64_t nq, const int32_t
   if (nq == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
   QK_TRY(refresh(b, s));
-  return enqueue(b, q, nq, nprobe, out_ids, out_dist, s);
+  QK_TRY(enqueue(b, q, nq, nprobe, out_ids, out_dist, s));
+  note_readers(b->ix, s);
+  return QK_OK;
   QK_GUARD_END
 }
 
@@ -840,6 +844,7 @@ qk_status qk_batch_replay(qk_batch* b, void* stream) {
     return QK_ERR_STATE;
   }
   QK_CUDA(cudaGraphLaunch(b->graph, (cudaStream_t)stream));
+  note_readers(b->ix, (cudaStream_t)stream);
   return QK_OK;
   QK_GUARD_END
 }

@@ -59,6 +59,7 @@ qk_status launch_tc_nearest(const float* X, int64_t n, int d, const float* C, in
                             int32_t* out_idx, float* out_dist, float* cnorm, int32_t* cand, int32_t* status,
                             cudaStream_t s);
 int tc_candidates_per_row();
+void preload_update_kernels();
 
 static int elem_bytes(int storage) { return storage == QK_STORE_BF16 ? 2 : (storage == QK_STORE_FP8 ? 1 : 4); }
 
@@ -133,9 +134,11 @@ static qk_status in_device(const T* src, size_t count, Tmp& tmp, const T** out, 
   return QK_OK;
 }
 
+// Index memory (mem_alloc / mem_free): stream-ordered on a private stream,
+// so that handing back an old version's memory never waits for the device.
 template <class T>
 static void dfree(T*& p) {
-  if (p) cudaFree(p);
+  mem_free(p);
   p = nullptr;
 }
 
@@ -143,8 +146,7 @@ template <class T>
 static qk_status dalloc(T** p, size_t count) {
   dfree(*p);
   if (count == 0) count = 1;
-  QK_CUDA(cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)));
-  return QK_OK;
+  return mem_alloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
 static qk_status ensure(Buffer& b, size_t bytes) {
@@ -180,6 +182,12 @@ static void free_structure(qk_index* ix) {
   dfree(ix->hits1);
   dfree(ix->lp0);
   dfree(ix->lp_scale0);
+  for (Table& t : ix->spare0) {
+    dfree(t.off);
+    dfree(t.size);
+  }
+  ix->spare0.clear();
+  ix->free0.clear();
   ix->ready = false;
   ix->where.clear();
 }
@@ -202,6 +210,9 @@ void swap_structure(qk_index* a, qk_index* b) {
   swap(a->h_cap_part0, b->h_cap_part0);
   swap(a->h_size0, b->h_size0);
   swap(a->h_ids0, b->h_ids0);
+  swap(a->arena_id, b->arena_id);
+  swap(a->free0, b->free0);
+  swap(a->spare0, b->spare0);
   swap(a->vec1, b->vec1);
   swap(a->ids1, b->ids1);
   swap(a->off1, b->off1);
@@ -276,11 +287,23 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
   const int d = ix->cfg.d;
   const int32_t N0 = ix->cfg.n_leaf, N1 = ix->cfg.n_parent;
   Trace tr("install");
+  // searches in flight keep the structure they were launched on
+  if (ix->vec0) retire_structure(ix);
   free_structure(ix);
   QK_TRY(group_rows(X, ids, n, d, leaf_of_row, N0, true, ix->status, &ix->vec0, &ix->ids0, &ix->off0,
                     &ix->size0, ix->h_off0, ix->h_size0, &ix->h_cap_part0, &ix->cap0, &ix->used0, s,
                     skip_unlabelled));
   ix->holes0 = 0;
+  ix->arena_id = next_arena_id();
+  for (int i = 0; i < 2; ++i) {   // spare partition tables for the updates to come
+    Table t;
+    t.n = N0;
+    QK_TRY(dalloc(&t.off, (size_t)N0));
+    qk_status ts = dalloc(&t.size, (size_t)N0);
+    if (ts != QK_OK) dfree(t.off);
+    QK_TRY(ts);
+    ix->spare0.push_back(t);
+  }
   QK_TRY(dalloc(&ix->cent0, (size_t)N0 * d));
   QK_CUDA(cudaMemcpyAsync(ix->cent0, C0, sizeof(float) * (size_t)N0 * d, cudaMemcpyDeviceToDevice, s));
   if (ix->cfg.storage != QK_STORE_F32) {
@@ -324,6 +347,7 @@ qk_status install(qk_index* ix, const float* X, const int64_t* ids, int64_t n, c
     }
   }
   tr.mark("id_map");
+  preload_update_kernels();
   ++ix->version;
   ix->n = n;
   ix->n_leaf = N0;
@@ -419,82 +443,35 @@ static qk_status check_ready(const qk_index* ix) {
   return QK_OK;
 }
 
-// Gives every level-0 partition room for need[j] rows: partitions whose
-// capacity is exceeded get capacity_for(need[j]); the arena is re-laid out
-// into fresh memory (all partitions keep their slots).
-// Makes room for need[j] rows in every partition j.  A partition that
-// outgrows its reserved rows moves, alone, to the free tail of the arena with
-// fresh room (its old rows become a hole).  When the tail is too small the
-// arena is compacted into a new allocation with a fresh tail.  Offsets on
-// host and device, the id mirror and the low-precision copy follow the rows.
-static qk_status grow_arena(qk_index* ix, const std::vector<int32_t>& need, cudaStream_t s) {
+// ---- copy-on-write updates of level 0 ----------------------------------
+// An update never writes a row or a table entry that a published version can
+// read.  It takes free arena rows (take_rows) for every partition whose rows
+// change in place, copies the partition there, edits the copy, and publishes
+// a fresh partition table; the rows and table the old version used are
+// retired until the searches launched on it have completed.
+
+// Lays the arena out again into new memory with every partition keeping its
+// room, and a free tail of at least tail_min rows; publishes the result (same
+// content, new layout) and retires the old arena.
+static qk_status compact(qk_index* ix, int64_t tail_min, cudaStream_t s) {
   const int d = ix->cfg.d;
   const int32_t N0 = ix->n_leaf;
   const int rb = ix->lp0 ? d * elem_bytes(ix->cfg.storage) : 0;
-  std::vector<int64_t> cap(ix->h_cap_part0);
-  std::vector<int32_t> moved;
-  int64_t extra = 0;
-  for (int32_t j = 0; j < N0; ++j)
-    if (need[j] > cap[j]) {
-      cap[j] = capacity_for(need[j]);
-      moved.push_back(j);
-      extra += cap[j];
-    }
-  if (moved.empty()) return QK_OK;
-  if (ix->used0 + extra <= ix->cap0) {
-    const int32_t m = (int32_t)moved.size();
-    std::vector<int64_t> offs(2 * (size_t)m);   // old offsets, then new offsets
-    std::vector<int32_t> sz(m);
-    int64_t o = ix->used0;
-    for (int32_t i = 0; i < m; ++i) {
-      const int32_t j = moved[i];
-      offs[i] = ix->h_off0[j];
-      offs[m + i] = o;
-      sz[i] = ix->h_size0[j];
-      o += cap[j];
-      ix->holes0 += ix->h_cap_part0[j];
-    }
-    Tmp toffs(s), tsz(s);
-    int64_t* doffs = nullptr;
-    int32_t* dsz = nullptr;
-    QK_TRY(toffs.alloc<int64_t>(offs.size(), &doffs));
-    QK_TRY(tsz.alloc<int32_t>((size_t)m, &dsz));
-    QK_CUDA(cudaMemcpyAsync(doffs, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice, s));
-    QK_CUDA(cudaMemcpyAsync(dsz, sz.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
-    // source and destination rows are disjoint: the destinations lie in the tail
-    QK_TRY(launch_relayout(ix->vec0, ix->ids0, doffs, doffs + m, dsz, m, d, ix->vec0, ix->ids0, s));
-    if (ix->lp0) QK_TRY(launch_relayout_bytes(ix->lp0, doffs, doffs + m, dsz, m, rb, ix->lp0, s));
-    for (int32_t i = 0; i < m; ++i) {
-      const int32_t j = moved[i];
-      for (int32_t t = 0; t < sz[i]; ++t) {
-        ix->h_ids0[offs[m + i] + t] = ix->h_ids0[offs[i] + t];
-        ix->h_ids0[offs[i] + t] = -1;
-      }
-      ix->h_off0[j] = offs[m + i];
-    }
-    QK_CUDA(cudaMemcpyAsync(ix->off0, ix->h_off0.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
-    QK_CUDA(cudaStreamSynchronize(s));
-    ix->used0 = o;
-    ix->h_cap_part0 = cap;
-    return QK_OK;
-  }
-  // compaction into a new arena
   std::vector<int64_t> off(N0);
   int64_t reserved = 0;
   for (int32_t j = 0; j < N0; ++j) {
     off[j] = reserved;
-    reserved += cap[j];
+    reserved += ix->h_cap_part0[j];
   }
-  const int64_t total = reserved + tail_rows(reserved);
+  const int64_t total = reserved + std::max(tail_rows(reserved), tail_min);
   float* nvec = nullptr;
   int64_t* nids = nullptr;
   unsigned char* nlp = nullptr;
-  Tmp toff(s);
-  int64_t* doff = nullptr;
+  Table t;
   qk_status st = dalloc(&nvec, (size_t)total * d);
   if (st == QK_OK) st = dalloc(&nids, (size_t)total);
   if (st == QK_OK && ix->lp0) st = dalloc(&nlp, (size_t)total * rb);
-  if (st == QK_OK) st = toff.alloc<int64_t>(N0, &doff);
+  if (st == QK_OK) st = take_table(ix, &t);
   if (st != QK_OK) {
     dfree(nvec);
     dfree(nids);
@@ -502,28 +479,128 @@ static qk_status grow_arena(qk_index* ix, const std::vector<int32_t>& need, cuda
     return st;
   }
   QK_CUDA(cudaMemsetAsync(nids, 0xff, sizeof(int64_t) * (size_t)total, s));
-  QK_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
-  QK_TRY(launch_relayout(ix->vec0, ix->ids0, ix->off0, doff, ix->size0, N0, d, nvec, nids, s));
-  if (ix->lp0) QK_TRY(launch_relayout_bytes(ix->lp0, ix->off0, doff, ix->size0, N0, rb, nlp, s));
-  QK_CUDA(cudaMemcpyAsync(ix->off0, doff, sizeof(int64_t) * N0, cudaMemcpyDeviceToDevice, s));
+  QK_CUDA(cudaMemcpyAsync(t.off, off.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s));
+  QK_CUDA(cudaMemcpyAsync(t.size, ix->size0, sizeof(int32_t) * N0, cudaMemcpyDeviceToDevice, s));
+  QK_TRY(launch_relayout(ix->vec0, ix->ids0, ix->off0, t.off, ix->size0, N0, d, nvec, nids, s));
+  if (ix->lp0) QK_TRY(launch_relayout_bytes(ix->lp0, ix->off0, t.off, ix->size0, N0, rb, nlp, s));
   QK_CUDA(cudaStreamSynchronize(s));
-  dfree(ix->vec0);
-  dfree(ix->ids0);
-  ix->vec0 = nvec;
-  ix->ids0 = nids;
-  if (ix->lp0) {
-    dfree(ix->lp0);
-    ix->lp0 = nlp;
-  }
   std::vector<int64_t> mirror((size_t)total, -1);
   for (int32_t j = 0; j < N0; ++j)
-    for (int32_t t = 0; t < ix->h_size0[j]; ++t) mirror[off[j] + t] = ix->h_ids0[ix->h_off0[j] + t];
+    for (int32_t r = 0; r < ix->h_size0[j]; ++r) mirror[off[j] + r] = ix->h_ids0[ix->h_off0[j] + r];
+  Retired old;
+  old.version = ix->version;
+  old.table = Table{ix->off0, ix->size0, N0};
+  old.device = {ix->vec0, ix->ids0};
+  if (ix->lp0) old.device.push_back(ix->lp0);
+  ix->vec0 = nvec;
+  ix->ids0 = nids;
+  if (ix->lp0) ix->lp0 = nlp;
+  ix->off0 = t.off;
+  ix->size0 = t.size;
   ix->h_ids0.swap(mirror);
   ix->h_off0 = off;
-  ix->h_cap_part0 = cap;
   ix->cap0 = total;
   ix->used0 = reserved;
   ix->holes0 = 0;
+  ix->free0.clear();
+  ix->arena_id = next_arena_id();
+  ++ix->version;
+  retire(ix, std::move(old));
+  return QK_OK;
+}
+
+// Gives each partition moved[i] fresh rows of capacity room[i] and copies
+// its current rows there.  The new offsets go to off (a working copy of
+// h_off0) and the host id mirror; the old rows are added to `old`, to be
+// retired when the new table is published.  Compacts first when the free
+// ranges and the tail cannot hold them all.
+static qk_status relocate(qk_index* ix, const std::vector<int32_t>& moved, const std::vector<int64_t>& room,
+                          std::vector<int64_t>& off, std::vector<int64_t>& cap, Retired& old, cudaStream_t s) {
+  const int32_t m = (int32_t)moved.size();
+  if (m == 0) return QK_OK;
+  const int d = ix->cfg.d;
+  const int rb = ix->lp0 ? d * elem_bytes(ix->cfg.storage) : 0;
+  std::vector<int64_t> dst(m, -1);
+  {
+    const auto free_saved = ix->free0;
+    const int64_t used_saved = ix->used0, holes_saved = ix->holes0;
+    bool fits = true;
+    for (int32_t i = 0; i < m && fits; ++i) fits = (dst[i] = take_rows(ix, room[i])) >= 0;
+    if (!fits) {
+      ix->free0 = free_saved;
+      ix->used0 = used_saved;
+      ix->holes0 = holes_saved;
+      int64_t want = 0;
+      for (int32_t i = 0; i < m; ++i) want += room[i];
+      QK_TRY(compact(ix, want, s));
+      off = ix->h_off0;
+      cap = ix->h_cap_part0;
+      for (int32_t i = 0; i < m; ++i)
+        if ((dst[i] = take_rows(ix, room[i])) < 0) {
+          set_error("arena: no room after compaction");
+          return QK_ERR_INTERNAL;
+        }
+    }
+  }
+  std::vector<int64_t> offs(2 * (size_t)m);   // old offsets, then new offsets
+  std::vector<int32_t> sz(m);
+  for (int32_t i = 0; i < m; ++i) {
+    const int32_t j = moved[i];
+    offs[i] = off[j];
+    offs[m + i] = dst[i];
+    sz[i] = ix->h_size0[j];
+  }
+  Tmp toffs(s), tsz(s);
+  int64_t* doffs = nullptr;
+  int32_t* dsz = nullptr;
+  QK_TRY(toffs.alloc<int64_t>(offs.size(), &doffs));
+  QK_TRY(tsz.alloc<int32_t>((size_t)m, &dsz));
+  QK_CUDA(cudaMemcpyAsync(doffs, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice, s));
+  QK_CUDA(cudaMemcpyAsync(dsz, sz.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+  // the destinations are free rows: no published version reads them
+  QK_TRY(launch_relayout(ix->vec0, ix->ids0, doffs, doffs + m, dsz, m, d, ix->vec0, ix->ids0, s));
+  if (ix->lp0) QK_TRY(launch_relayout_bytes(ix->lp0, doffs, doffs + m, dsz, m, rb, ix->lp0, s));
+  QK_CUDA(cudaStreamSynchronize(s));   // the temporaries above are stream-ordered; the copies must land first
+  old.arena = ix->arena_id;
+  for (int32_t i = 0; i < m; ++i) {
+    const int32_t j = moved[i];
+    for (int32_t r = 0; r < sz[i]; ++r) {
+      ix->h_ids0[offs[m + i] + r] = ix->h_ids0[offs[i] + r];
+      ix->h_ids0[offs[i] + r] = -1;
+    }
+    old.rows.emplace_back(off[j], cap[j]);
+    ix->holes0 += cap[j];
+    off[j] = dst[i];
+    cap[j] = room[i];
+  }
+  return QK_OK;
+}
+
+// Publishes the level-0 table (off, size) as the next version: uploads it
+// into a spare table, waits for the update's own stream, exchanges the
+// pointers and retires the previous table with `old`.
+static qk_status publish(qk_index* ix, const std::vector<int64_t>& off, const std::vector<int64_t>& cap,
+                         const std::vector<int32_t>& size, Retired&& old, cudaStream_t s) {
+  const int32_t N0 = ix->n_leaf;
+  Table t;
+  QK_TRY(take_table(ix, &t));
+  cudaError_t e = cudaMemcpyAsync(t.off, off.data(), sizeof(int64_t) * N0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t.size, size.data(), sizeof(int32_t) * N0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    ix->spare0.push_back(t);
+    return cuda_status(e, "publishing a partition table");
+  }
+  old.version = ix->version;
+  old.arena = ix->arena_id;
+  old.table = Table{ix->off0, ix->size0, N0};
+  ix->off0 = t.off;
+  ix->size0 = t.size;
+  ix->h_off0 = off;
+  ix->h_cap_part0 = cap;
+  ix->h_size0 = size;
+  ++ix->version;
+  retire(ix, std::move(old));
   return QK_OK;
 }
 
@@ -712,6 +789,7 @@ qk_status qk_create(const qk_config* cfg, qk_index** out) {
 
 void qk_destroy(qk_index* ix) {
   if (!ix) return;
+  reclaim(ix, true);
   if (ix->pending) {
     free_structure(ix->pending);
     delete ix->pending;
@@ -869,6 +947,7 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   a.scan1 = scan1 ? ds1 : nullptr;
   a.scan_cap1 = cap1;
   QK_TRY(launch_search(a, s));
+  note_readers(ix, s);
   tr.mark("launch");
   ix->queries_seen += nq;
   if (!all_dev) {
@@ -951,6 +1030,7 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   cudaStream_t s = (cudaStream_t)stream;
   const int d = ix->cfg.d;
   Trace tr("insert");
+  reclaim(ix, false);
   std::vector<int64_t> hid;
   QK_TRY(to_host(ids, (size_t)n, hid, s));
   {
@@ -995,23 +1075,33 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   QK_CUDA(cudaStreamSynchronize(s));
   tr.mark("checks_descent");
   std::vector<int32_t> need(ix->h_size0);
-  bool grow = false;
   for (int64_t r = 0; r < n; ++r) {
     int32_t j = hleaf[r];
     if (j < 0 || j >= ix->n_leaf) {
       set_error("insert: descent reached an empty parent partition");
       return QK_ERR_STATE;
     }
-    if (++need[j] > ix->h_cap_part0[j]) grow = true;
+    ++need[j];
   }
-  if (grow) QK_TRY(grow_arena(ix, need, s));
+  // appends go to rows behind every partition's live rows, which no version
+  // reads; a partition whose room runs out moves to fresh rows first
+  std::vector<int64_t> off(ix->h_off0), cap(ix->h_cap_part0);
+  std::vector<int32_t> moved;
+  std::vector<int64_t> room;
+  for (int32_t j = 0; j < ix->n_leaf; ++j)
+    if (need[j] > cap[j]) {
+      moved.push_back(j);
+      room.push_back(capacity_for(need[j]));
+    }
+  Retired old;
+  QK_TRY(relocate(ix, moved, room, off, cap, old, s));
   tr.mark("grow");
   std::vector<int64_t> dst((size_t)n);
   std::vector<int32_t> cur(ix->h_size0);
   for (int64_t r = 0; r < n; ++r) {
     int32_t j = hleaf[r];
     int32_t slot = cur[j]++;
-    dst[r] = ix->h_off0[j] + slot;
+    dst[r] = off[j] + slot;
   }
   int64_t* ddst = nullptr;
   QK_TRY(tdst.alloc<int64_t>((size_t)n, &ddst));
@@ -1019,17 +1109,14 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   QK_TRY(launch_place_rows(X, I, n, d, ddst, ix->vec0, ix->ids0, s));
   if (ix->lp0)   // FP8 rows use their partition's current scale (values beyond it saturate)
     QK_TRY(launch_quantize_rows(X, n, d, ddst, leaf, ix->cfg.storage, ix->lp_scale0, ix->lp0, s));
-  QK_CUDA(cudaMemcpyAsync(ix->size0, cur.data(), sizeof(int32_t) * ix->n_leaf, cudaMemcpyHostToDevice, s));
-  QK_CUDA(cudaStreamSynchronize(s));
+  QK_TRY(publish(ix, off, cap, cur, std::move(old), s));
   for (int64_t r = 0; r < n; ++r) {
     int32_t j = hleaf[r];
-    int64_t slot = dst[r] - ix->h_off0[j];
+    int64_t slot = dst[r] - off[j];
     ix->where[hid[r]] = ((int64_t)j << 32) | (uint32_t)slot;
     ix->h_ids0[dst[r]] = hid[r];
   }
-  ix->h_size0 = cur;
   ix->n += n;
-  ++ix->version;
   tr.mark("place");
   return QK_OK;
   QK_GUARD_END
@@ -1047,10 +1134,34 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
   cudaStream_t s = (cudaStream_t)stream;
   const int d = ix->cfg.d;
   Trace tr("delete");
+  reclaim(ix, false);
   std::vector<int64_t> hid;
   QK_TRY(to_host(ids, (size_t)n, hid, s));
-  // Replay the deletes in order on the host mirror (swap-with-last), keeping,
-  // for every slot that changed, the arena slot its final content came from.
+  // Every partition that loses a row is first copied to fresh rows (the rows
+  // a search in flight may read stay as they are); the deletes are then
+  // replayed in order on the copy, each moving the partition's last row
+  // into the freed slot.
+  std::vector<int32_t> moved;
+  std::vector<int64_t> room;
+  {
+    std::vector<char> hit(ix->n_leaf, 0);
+    for (int64_t r = 0; r < n; ++r) {
+      auto it = ix->where.find(hid[r]);
+      if (it == ix->where.end()) continue;
+      const int32_t j = (int32_t)(it->second >> 32);
+      if (!hit[j]) {
+        hit[j] = 1;
+        moved.push_back(j);
+        room.push_back(ix->h_cap_part0[j]);
+      }
+    }
+  }
+  if (moved.empty()) return QK_OK;
+  std::vector<int64_t> off(ix->h_off0), cap(ix->h_cap_part0);
+  Retired old;
+  QK_TRY(relocate(ix, moved, room, off, cap, old, s));
+  tr.mark("copy");
+  // for every slot that changed, the slot its final content came from
   std::unordered_map<int32_t, std::unordered_map<int32_t, int32_t>> src_of;
   std::vector<int32_t> size(ix->h_size0);
   int64_t removed = 0;
@@ -1063,12 +1174,12 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
     if (slot != last) {
       auto lt = m.find(last);
       m[slot] = lt == m.end() ? last : lt->second;
-      int64_t moved = ix->h_ids0[ix->h_off0[j] + last];
-      ix->h_ids0[ix->h_off0[j] + slot] = moved;
-      ix->where[moved] = ((int64_t)j << 32) | (uint32_t)slot;
+      int64_t mv = ix->h_ids0[off[j] + last];
+      ix->h_ids0[off[j] + slot] = mv;
+      ix->where[mv] = ((int64_t)j << 32) | (uint32_t)slot;
     }
     m.erase(last);
-    ix->h_ids0[ix->h_off0[j] + last] = -1;
+    ix->h_ids0[off[j] + last] = -1;
     ix->where.erase(it);
     size[j] = last;
     ++removed;
@@ -1077,8 +1188,8 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
   for (auto& kv : src_of)
     for (auto& mv : kv.second)
       if (mv.first < size[kv.first] && mv.first != mv.second) {
-        src.push_back(ix->h_off0[kv.first] + mv.second);
-        dst.push_back(ix->h_off0[kv.first] + mv.first);
+        src.push_back(off[kv.first] + mv.second);
+        dst.push_back(off[kv.first] + mv.first);
       }
   tr.mark("replay");
   const int64_t m = (int64_t)src.size();
@@ -1099,11 +1210,8 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
                                reinterpret_cast<unsigned char*>(dtv), s));
     }
   }
-  QK_CUDA(cudaMemcpyAsync(ix->size0, size.data(), sizeof(int32_t) * ix->n_leaf, cudaMemcpyHostToDevice, s));
-  QK_CUDA(cudaStreamSynchronize(s));
-  ix->h_size0 = size;
+  QK_TRY(publish(ix, off, cap, size, std::move(old), s));
   ix->n -= removed;
-  ++ix->version;
   tr.mark("moves");
   if (n_removed) *n_removed = removed;
   return QK_OK;
@@ -1170,6 +1278,8 @@ qk_status qk_stats(const qk_index* ix, qk_index_stats* out) {
   }
   st.queries_seen = ix->queries_seen.load();
   st.version = ix->version;
+  st.searches_in_flight = readers_in_flight(const_cast<qk_index*>(ix));
+  st.retired_rows = retired_rows(const_cast<qk_index*>(ix));
   *out = st;
   return QK_OK;
   QK_GUARD_END

@@ -15,13 +15,24 @@
 //            scanned as one partition whose row index is the id.
 //   beta     the FP64 1024-point table of I_x((d+1)/2, 1/2).
 //   hits     int64 access counters per partition and level.
+//
+// Copy-on-write views (Sec. 9, "Concurrency"): a search reads the partition
+// table (off0, size0) and the arena pointers it was launched with.  Inserts,
+// deletes, compaction and maintenance never write a row or a table entry that
+// a published version can read: they fill free rows and a spare table, then
+// publish the new table with a pointer exchange.  What the older versions
+// used is retired and handed back only once every search launched on them
+// has completed (their completion events are recorded per launch).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "../../include/quake_b300.h"
@@ -89,6 +100,29 @@ struct Buffer {
   size_t bytes = 0;
 };
 
+// A level-0 partition table: offsets and sizes of n_leaf partitions.
+struct Table {
+  int64_t* off = nullptr;
+  int32_t* size = nullptr;
+  int32_t n = 0;
+};
+
+// A search launch that may still be in flight, and the index version it reads.
+struct ViewReader {
+  cudaEvent_t ev = nullptr;
+  uint64_t version = 0;
+};
+
+// Memory that searches of versions up to `version` may still read.
+struct Retired {
+  uint64_t version = 0;
+  uint64_t arena = 0;                                 // arena the row ranges belong to
+  std::vector<std::pair<int64_t, int64_t>> rows;      // (first row, rows) of that arena
+  Table table;                                        // a partition table
+  std::vector<void*> device;                          // allocations (a replaced arena)
+  qk_index* structure = nullptr;                      // a whole replaced structure
+};
+
 struct qk_index_impl;
 
 }  // namespace qk
@@ -113,6 +147,9 @@ struct qk_index {
   std::vector<int64_t> h_off0, h_cap_part0;
   std::vector<int32_t> h_size0;
   std::vector<int64_t> h_ids0;   // host mirror of ids0 (arena slot -> id)
+  uint64_t arena_id = 0;         // names the arena that free0 and retired row ranges refer to
+  std::map<int64_t, int64_t> free0;   // arena rows free to take again: first row -> rows
+  std::vector<qk::Table> spare0; // partition tables no published version uses
   // level 1
   float* vec1 = nullptr;
   int64_t* ids1 = nullptr;
@@ -140,6 +177,11 @@ struct qk_index {
   // committed, and the index version it was planned from
   qk_index* pending = nullptr;
   uint64_t pending_version = 0;
+  // copy-on-write views: searches in flight and what older versions still use
+  std::mutex view_mu;
+  std::vector<qk::ViewReader> readers;
+  std::vector<cudaEvent_t> idle_events;
+  std::vector<qk::Retired> retired;
 };
 
 namespace qk {
@@ -165,4 +207,33 @@ int32_t n_candidates(double f, int32_t n);
 // recall target and fixed nprobe (queries, outputs and records not set).
 void base_search_args(qk_index* ix, int32_t k, float recall_target, int32_t nprobe, SearchArgs& a);
 qk_status launch_search(const SearchArgs& a, cudaStream_t stream);
+
+// Copy-on-write views (views.cu).
+// Records that the work just enqueued on `s` reads the current version
+// (no-op while `s` is capturing a graph: a replay records itself).
+void note_readers(qk_index* ix, cudaStream_t s);
+// Hands back what no search in flight can read any more: row ranges of the
+// current arena go to free0, tables to spare0, the rest is freed.  With
+// wait, first waits for every search in flight.
+void reclaim(qk_index* ix, bool wait);
+// Keeps `r` until the searches of versions up to r.version have completed.
+void retire(qk_index* ix, Retired&& r);
+// Moves the index's whole structure into a fresh object and retires it.
+void retire_structure(qk_index* ix);
+// Searches recorded and not yet known complete; arena rows kept for them.
+int64_t readers_in_flight(qk_index* ix);
+int64_t retired_rows(qk_index* ix);
+// Arena rows for a partition of `rows` rows: the smallest free range that
+// fits, else the free tail; -1 when neither has room.
+int64_t take_rows(qk_index* ix, int64_t rows);
+// A partition table of n_leaf entries that no published version uses.
+qk_status take_table(qk_index* ix, Table* t);
+// A fresh arena id.
+uint64_t next_arena_id();
+// Device memory of the index structure (arena, tables, levels): allocated and
+// freed in stream order on a private stream of the current device; a free
+// never waits for other work on the device.  The memory must no longer be in
+// use by any kernel when it is freed.
+qk_status mem_alloc(void** p, size_t bytes);
+void mem_free(void* p);
 }  // namespace qk

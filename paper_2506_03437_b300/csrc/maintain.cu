@@ -572,13 +572,16 @@ static qk_status maintain_plan(qk_index* ix, const qk_maint_params* params, qk_m
   return QK_OK;
 }
 
-// Makes nx's structure the index's and frees the old one.  Nothing may still
-// read the old arena (no search of the index in flight).
+// Makes nx's structure the index's.  The old one is retired: searches still
+// in flight keep reading it, and it is freed once they have completed.
 static qk_status commit_structure(qk_index* ix, qk_index* nx, cudaStream_t s) {
   QK_CUDA(cudaStreamSynchronize(s));
+  reclaim(ix, false);
   swap_structure(ix, nx);
-  release_structure(nx);
-  delete nx;
+  Retired r;
+  r.version = ix->version;
+  r.structure = nx;
+  retire(ix, std::move(r));
   ix->queries_seen = 0;
   ++ix->version;
   return QK_OK;

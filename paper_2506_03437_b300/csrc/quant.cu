@@ -96,6 +96,17 @@ __global__ void relayout_bytes_kernel(const unsigned char* __restrict__ old_a, c
   for (int64_t e = threadIdx.x; e < n16; e += blockDim.x) o[e] = s[e];
 }
 
+// Loads this file's kernels into the context (see preload_update_kernels).
+void preload_quant_kernels() {
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, partition_scale_kernel);
+  cudaFuncGetAttributes(&fa, quantize_arena_kernel);
+  cudaFuncGetAttributes(&fa, quantize_rows_kernel);
+  cudaFuncGetAttributes(&fa, gather_bytes_kernel);
+  cudaFuncGetAttributes(&fa, place_bytes_kernel);
+  cudaFuncGetAttributes(&fa, relayout_bytes_kernel);
+}
+
 qk_status launch_quantize_arena(const float* vec, const int64_t* off, const int32_t* size, int32_t n_part, int d,
                                 int storage, float* scale, unsigned char* lp, cudaStream_t s) {
   if (n_part <= 0) return QK_OK;

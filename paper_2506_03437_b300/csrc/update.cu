@@ -10,6 +10,8 @@
 
 namespace qk {
 
+void preload_quant_kernels();
+
 // Second step of the greedy descent for a two-level index: among the leaf
 // centroids grouped under parent[r] (rows [off1[p], off1[p] + size1[p]) of the
 // level-1 arena, ids = leaf index), the nearest one; ties to the lower leaf.
@@ -87,6 +89,21 @@ __global__ void gather_moves_kernel(const float* __restrict__ vec, const int64_t
   float4* o = reinterpret_cast<float4*>(tvec + w * d);
   for (int j = lane; j < d / 4; j += 32) o[j] = s[j];
   if (lane == 0) tids[w] = ids[src[w]];
+}
+
+// Loads the update kernels into the context.  With lazy module loading a
+// kernel is loaded at its first launch, and that load waits for the work in
+// flight on the device; an index loads them when it is installed, so that its
+// first insert or delete does not wait for the searches running beside it.
+void preload_update_kernels() {
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, descend_children_kernel);
+  cudaFuncGetAttributes(&fa, nan_check_kernel);
+  cudaFuncGetAttributes(&fa, relayout_kernel);
+  cudaFuncGetAttributes(&fa, place_rows_kernel);
+  cudaFuncGetAttributes(&fa, gather_moves_kernel);
+  preload_quant_kernels();
+  cudaGetLastError();
 }
 
 qk_status launch_descend_children(const float* X, int64_t n, int d, const int32_t* parent, const float* vec1,
