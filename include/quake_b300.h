@@ -692,12 +692,14 @@ qk_status qk_search_nprobe(qk_index* index, const float* q, int64_t nq, int32_t 
  *    batches overlap and new requests join the next free slot; a batch is held
  *    back while free device memory is below min_free_bytes;
  *  - updates wait until update_batch are pending or the oldest has waited
- *    update_wait_s, then the searches in flight are drained and the group is
- *    applied as its net effect (one delete call, one insert call);
+ *    update_wait_s, then the group is applied as its net effect (one delete
+ *    call, one insert call) on the server's update stream, beside the batches
+ *    in flight, which finish on the version they were launched on;
  *  - every maintain_every requests a maintenance pass runs with *maint: with
  *    concurrent_maintenance it is prepared by a worker thread beside the
- *    searches (qk_maintain_prepare; updates wait meanwhile) and committed at
- *    the next drain, otherwise it runs in place.
+ *    searches (qk_maintain_prepare; updates wait meanwhile) and committed
+ *    when ready, otherwise it runs in place; neither waits for the batches
+ *    in flight.
  * A request's latency runs from its submission to the moment its result is in
  * host memory.  Inserted ids must be new (a duplicate fails the whole group and
  * stops the server).  The index must not be used directly while a server runs

@@ -8,16 +8,19 @@
 //     and requests that arrive meanwhile join the next free slot; a batch
 //     is held back while free device memory is below min_free_bytes;
 //   - updates wait until update_batch of them are pending or the oldest has
-//     waited update_wait_s; then the searches in flight are drained and the
-//     group is applied as its net effect (one delete call, one insert call:
-//     an id inserted and deleted inside the group never reaches the index, an
-//     id deleted and inserted again is deleted first);
+//     waited update_wait_s; then the group is applied, on its own stream and
+//     beside the batches in flight, as its net effect (one delete call, one
+//     insert call: an id inserted and deleted inside the group never reaches
+//     the index, an id deleted and inserted again is deleted first).  The
+//     index's copy-on-write views let the batches in flight finish on the
+//     version they were launched on; batches launched afterwards see the
+//     update;
 //   - every maintain_every operations a maintenance pass (Sec. 4) runs.  With
 //     concurrent maintenance a worker thread prepares it on its own stream
 //     (qk_maintain_prepare) while searches go on, updates wait, and the pass
-//     is committed at the next drain; otherwise the scheduler drains and runs
-//     it in place.  A pass also needs min_window queries since the previous
-//     one (its statistics window).
+//     is committed as soon as it is ready; otherwise the scheduler runs it in
+//     place.  Neither waits for the batches in flight.  A pass also needs
+//     min_window queries since the previous one (its statistics window).
 // A request's latency runs from its submission to the moment its result is in
 // host memory.  Every GPU step is a call of the index's own C ABI.
 #include <cuda_runtime.h>
@@ -98,6 +101,7 @@ struct qk_server {
   std::atomic<int> prep_state{0};          // 0 idle, 1 running, 2 ready, 3 failed
   std::string prep_error;
   cudaStream_t maint_stream = nullptr;
+  cudaStream_t update_stream = nullptr;
   int64_t ops_seen = 0, passes = 0, searched_since = 0;
   // statistics
   std::atomic<int64_t> n_search{0}, n_insert{0}, n_delete{0}, batches{0}, drains{0};
@@ -143,14 +147,6 @@ bool fail(qk_server* sv, qk_status st, const char* what) {
   return true;
 }
 
-void drain(qk_server* sv) {
-  for (Slot& s : sv->slots)
-    if (s.busy) {
-      cudaEventSynchronize(s.event);
-      finish_slot(sv, s);
-    }
-}
-
 bool free_ok(qk_server* sv) {
   if (sv->cfg.min_free_bytes <= 0) return true;
   size_t fr = 0, tot = 0;
@@ -161,7 +157,6 @@ bool free_ok(qk_server* sv) {
 // Applies a group of updates as its net effect (see the file comment).
 void apply_updates(qk_server* sv, std::vector<Op>& group) {
   const auto c0 = Clock::now();
-  drain(sv);
   struct St {
     bool del = false;
     int64_t ins = -1;   // position in group of the live insert
@@ -200,10 +195,11 @@ void apply_updates(qk_server* sv, std::vector<Op>& group) {
   }
   if (!del_ids.empty()) {
     int64_t removed = 0;
-    fail(sv, qk_delete(sv->ix, del_ids.data(), (int64_t)del_ids.size(), &removed, nullptr), "delete");
+    fail(sv, qk_delete(sv->ix, del_ids.data(), (int64_t)del_ids.size(), &removed, sv->update_stream), "delete");
   }
   if (!ins_ids.empty())
-    fail(sv, qk_insert(sv->ix, ins_x.data(), ins_ids.data(), (int64_t)ins_ids.size(), nullptr), "insert");
+    fail(sv, qk_insert(sv->ix, ins_x.data(), ins_ids.data(), (int64_t)ins_ids.size(), sv->update_stream),
+         "insert");
   const auto now = Clock::now();
   for (const Op& o : group) {
     set_done(sv, o.ticket, o.t, now);
@@ -235,12 +231,11 @@ void scheduler_body(qk_server* sv) {
     // finished batches
     for (Slot& s : sv->slots)
       if (s.busy && cudaEventQuery(s.event) == cudaSuccess) finish_slot(sv, s);
-    // a prepared maintenance pass: drain and commit
+    // a prepared maintenance pass: commit (the batches in flight keep the old structure)
     const int ps = sv->prep_state.load();
     if (ps == 2 || ps == 3) {
       sv->preparer.join();
       const auto c0 = Clock::now();
-      drain(sv);
       if (ps == 2) fail(sv, qk_maintain_commit(sv->ix, sv->maint_stream), "maintain_commit");
       else if (!sv->failed.exchange(1)) sv->error = "maintain_prepare: " + sv->prep_error;
       ++sv->passes;
@@ -281,8 +276,7 @@ void scheduler_body(qk_server* sv) {
         sv->preparer = std::thread(run_prepare, sv);
       } else {
         const auto c0 = Clock::now();
-        drain(sv);
-        fail(sv, qk_maintain(sv->ix, &sv->maint, nullptr, 0, nullptr, nullptr), "maintain");
+        fail(sv, qk_maintain(sv->ix, &sv->maint, nullptr, 0, nullptr, sv->update_stream), "maintain");
         ++sv->passes;
         sv->searched_since = 0;
         sv->maint_stall_s += secs(c0, Clock::now());
@@ -476,6 +470,7 @@ qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server*
     ck(cudaMalloc(&s.dist_dev, sizeof(float) * mb * k));
   }
   ck(cudaStreamCreateWithFlags(&sv->maint_stream, cudaStreamNonBlocking));
+  ck(cudaStreamCreateWithFlags(&sv->update_stream, cudaStreamNonBlocking));
   if (st != QK_OK) {
     qk_server_destroy(sv);
     return st;
@@ -609,6 +604,7 @@ void qk_server_destroy(qk_server* sv) {
     if (s.dist_dev) cudaFree(s.dist_dev);
   }
   if (sv->maint_stream) cudaStreamDestroy(sv->maint_stream);
+  if (sv->update_stream) cudaStreamDestroy(sv->update_stream);
   delete sv;
 }
 

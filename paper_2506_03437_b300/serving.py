@@ -7,10 +7,12 @@ admitted as soon as a slot frees up, and their work overlaps on the device.
 A batch is also held back while free device memory is below
 `min_free_bytes`.
 
-Inserts and deletes change the arena, so they are applied between batches:
-pending updates wait until `update_batch` of them have arrived or the oldest
-has waited `update_wait_s`; then the searches in flight are drained and the
-pending group is applied as one delete call followed by one insert call.
+Inserts and deletes are applied between batch launches: pending updates wait
+until `update_batch` of them have arrived or the oldest has waited
+`update_wait_s`; then the pending group is applied, on its own stream, as one
+delete call followed by one insert call.  The searches in flight are not
+waited for: the index's copy-on-write views let them finish on the version
+they were launched on, and batches launched afterwards see the update.
 That order gives the same index as applying the group one by one, because the
 group is first reduced to its net effect: an id inserted and then deleted
 inside the group is dropped from both calls, and an id deleted and then
@@ -21,9 +23,9 @@ Every `maintain_every` operations the maintenance pass runs (Sec. 4; its
 statistics window is the queries since the previous pass).  With
 `concurrent_maintenance` (the default) the pass is prepared by a host thread
 on its own stream while searches go on (qk_maintain_prepare builds the new
-partitions aside); updates wait meanwhile, and once the pass is ready the
-searches in flight are drained and it is committed.  Otherwise the searches
-in flight are drained and the whole pass runs in place.  A request's latency
+partitions aside); updates wait meanwhile, and once the pass is ready it is
+committed.  Otherwise the whole pass runs in place.  Neither waits for the
+searches in flight.  A request's latency
 runs from its arrival to the moment its result is in host memory.
 
 The index's kernels do all the work; this module only schedules calls to the
@@ -94,6 +96,7 @@ class Server:
         self.concurrent = concurrent_maintenance
         self.device = torch.cuda.current_device()
         self.maint_stream = torch.cuda.Stream()
+        self.update_stream = torch.cuda.Stream()
         self.ix, self.d, self.k, self.tau = index, d, k, recall_target
         self.max_batch, self.min_free = max_batch, min_free_bytes
         self.maintain_every, self.maint_args = maintain_every, maint_args or {}
@@ -141,12 +144,6 @@ class Server:
             self.out_dist[rows] = slot["dist_host"].numpy()[:n]
         slot["busy"] = False
 
-    def _drain(self, inflight, clock):
-        while inflight:
-            b = inflight.pop(0)
-            b["event"].synchronize()
-            self._finish(b, clock())
-
     def _free_ok(self):
         if self.min_free <= 0:
             return True
@@ -164,10 +161,10 @@ class Server:
         ops = self.ops
         dpos, ipos = net_updates(ops.kind[rows], ops.ref[rows])
         if dpos.shape[0]:
-            self.ix.delete(ops.ref[rows[dpos]])
+            self.ix.delete(ops.ref[rows[dpos]], stream=self.update_stream)
         if ipos.shape[0]:
             r = rows[ipos]
-            self.ix.insert(ops.vec[r], ops.ref[r])
+            self.ix.insert(ops.vec[r], ops.ref[r], stream=self.update_stream)
         self.lat[rows] = clock() - ops.t[rows]
 
     # ------------------------------------------------------------------- run
@@ -187,7 +184,7 @@ class Server:
         n_s, n_u = s_rows.shape[0], u_rows.shape[0]
         qs = us = 0          # next search / update not yet taken
         t_upd = t_maint = t_host = t_prep = 0.0
-        batches = drains = passes = 0
+        batches = groups = passes = 0
         inflight = []
         prep = None          # the maintenance pass being prepared: [thread, error, start time]
         searched = 0         # queries launched since the last pass (its statistics window)
@@ -204,10 +201,9 @@ class Server:
             # results of finished batches
             while inflight and inflight[0]["event"].query():
                 self._finish(inflight.pop(0), clock())
-            # a prepared maintenance pass: drain, commit, then updates may go on
+            # a prepared maintenance pass: commit, then updates may go on
             if prep is not None and not prep[0].is_alive():
                 c0 = clock()
-                self._drain(inflight, clock)
                 if prep[1] is not None:
                     raise prep[1]
                 self.ix.maintain_commit(stream=self.maint_stream)
@@ -216,14 +212,13 @@ class Server:
                 t_maint += clock() - c0
                 t_prep += c0 - prep[2]
                 prep = None
-            # updates: between batches, after draining the searches in flight
+            # updates: between batch launches, beside the searches in flight
             if prep is None and ua > us and (ua - us >= self.update_batch or now - u_t[us] >= self.update_wait
                                              or qa == n_s):
                 c0 = clock()
-                self._drain(inflight, clock)
                 self._apply_updates(u_rows[us:ua], clock)
                 us = ua
-                drains += 1
+                groups += 1
                 t_upd += clock() - c0
             if (self.maintain_every and prep is None and (qa + ua) // self.maintain_every > passes
                     and searched >= min_window):
@@ -231,18 +226,16 @@ class Server:
                     # pending updates first, so the pass plans from the current index
                     if ua > us:
                         c0 = clock()
-                        self._drain(inflight, clock)
                         self._apply_updates(u_rows[us:ua], clock)
                         us = ua
-                        drains += 1
+                        groups += 1
                         t_upd += clock() - c0
                     prep = [None, None, clock()]
                     prep[0] = threading.Thread(target=self._prepare, args=(prep,), daemon=True)
                     prep[0].start()
                 else:
                     c0 = clock()
-                    self._drain(inflight, clock)
-                    self.ix.maintain(**self.maint_args)
+                    self.ix.maintain(stream=self.update_stream, **self.maint_args)
                     passes += 1
                     searched = 0
                     t_maint += clock() - c0
@@ -267,7 +260,7 @@ class Server:
                     if np.isfinite(wait) and wait > 0:
                         time.sleep(min(wait, 1e-3))
         wall = clock()
-        out = {"wall_s": round(wall, 4), "batches": batches, "maintenance_passes": passes, "update_drains": drains,
+        out = {"wall_s": round(wall, 4), "batches": batches, "maintenance_passes": passes, "update_groups": groups,
                "update_s": round(t_upd, 4), "maintenance_stall_s": round(t_maint, 4),
                "maintenance_prepare_s": round(t_prep, 4), "launch_host_s": round(t_host, 4),
                "concurrent_maintenance": self.concurrent}
@@ -408,7 +401,7 @@ class NativeServer:
         lat = lat + lag
         self.out_ids, self.out_dist = ids, dist
         out = {"wall_s": round(wall, 4), "batches": stt.batches, "maintenance_passes": stt.maintenance_passes,
-               "update_drains": stt.update_groups, "update_s": round(stt.update_s, 4),
+               "update_groups": stt.update_groups, "update_s": round(stt.update_s, 4),
                "maintenance_stall_s": round(stt.maintenance_stall_s, 4),
                "maintenance_prepare_s": round(stt.maintenance_prepare_s, 4),
                "driver_lag_p99_ms": round(float(np.percentile(lag, 99)) * 1e3, 4),
