@@ -314,13 +314,21 @@ qk_status qk_cap_fraction(int32_t d, int32_t mode, const double* t, const double
  * not NULL, out_dist (n x k, exact FP32 distances: squared L2, or the negated
  * inner product) in (distance, index) order.  This is the centroid scoring of
  * the top-down search and of k-means assignment (Sec. 3): tensor cores
- * (tcgen05, TF32 operands, FP32 accumulation) score every centroid, the 16
- * best approximate candidates of a row are re-scored exactly in FP32 from the
- * direct differences, and the k best are kept.  TF32 moves an approximate
- * distance by at most about 2^-10 ||x|| ||c||; keeping twice the largest k
- * as approximate candidates leaves a margin for that, and a true neighbour
- * outside the 16 approximate candidates is the only way the result can
- * differ from an exact scan.
+ * (tcgen05, TF32 operands, FP32 accumulation) score every centroid.
+ *  - k = 1: the result is the exact FP32 nearest centroid (ties to the lower
+ *    index), as an exact scan with the same FP32 arithmetic gives it.  Each
+ *    row keeps its smallest approximate distance and the runner-up; when the
+ *    gap exceeds a proven bound on the TF32 and FP32 errors (about 2^-6
+ *    ||x|| max||c||) the smallest is the answer; the other rows are scored
+ *    again, every centroid within that bound of their smallest approximate
+ *    distance is scored exactly, and the best is kept.  Synchronises the
+ *    stream once (to size the second pass).
+ *  - k > 1: the 16 best approximate candidates of a row are re-scored
+ *    exactly in FP32 and the k best are kept.  TF32 moves an approximate
+ *    distance by at most about 2^-9 ||x|| ||c||; keeping twice the largest k
+ *    as approximate candidates leaves a margin for that, and a true neighbour
+ *    outside the 16 approximate candidates is the only way the result can
+ *    differ from an exact scan.
  */
 qk_status qk_nearest_centroids(const float* x, int64_t n, int32_t d, const float* c, int32_t K, int32_t metric,
                                int32_t k, int32_t* out_idx, float* out_dist, void* stream);

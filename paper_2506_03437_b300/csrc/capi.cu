@@ -1407,6 +1407,11 @@ qk_status qk_nearest_centroids(const float* x, int64_t n, int32_t d, const float
   }
   if (n == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    keep_pool_memory(dev);   // the scratch of repeated calls stays in the pool
+  }
   Tmp tx(s), tcen(s), ti(s), td(s), tn(s), tcand(s), ts(s);
   const float *X = nullptr, *C = nullptr;
   QK_TRY(in_device(x, (size_t)n * d, tx, &X, s));
