@@ -67,12 +67,19 @@ STORAGE = "f32"
 TRAFFIC_BYTES = 120.52e9 + 0.411e9
 TRAFFIC_KERNEL_HASH = "bfca0f4e553054f7"
 KERNEL_SOURCES = ["search_impl.cuh", "common.cuh", "capvol.cuh", "index.cuh"]
+# DRAM traffic of the grouped scans of one batched APS step on the full workload
+# (its four launches, one per round, summed), from the single-pass ncu capture
+# summarised in profiles/aps_batch_launches_1Mx128.md; it belongs to these
+# sources with this hash.
+SCAN_TRAFFIC_BYTES = (461.61 + 5.95 + 530.17 + 33.22 + 0.142 + 0.142) * 1e6
+SCAN_TRAFFIC_HASH = "564a749f5048bd10"
+SCAN_SOURCES = ["grouped.cuh", "common.cuh", "index.cuh", "aps_batch.cu"]
 
 
-def kernel_hash():
+def kernel_hash(sources=None):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2506_03437_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -432,9 +439,16 @@ def scan_roofline(pairs, scan_s, peak_ops, bytes_unique, bytes_items, step_s, hb
     of the paper's effective scan rate."""
     ops = 2.0 * pairs * D
     achieved = ops / scan_s / 1e12
+    full = N == 1_000_000 and NQ == 10_000 and D == 128
+    traffic = SCAN_TRAFFIC_BYTES if (full and kernel_hash(SCAN_SOURCES) == SCAN_TRAFFIC_HASH) else None
+    extra = {}
+    if traffic is not None:
+        extra = {"dram_gbs": round(traffic / scan_s / 1e9, 1), "dram_frac": round(traffic / scan_s / 1e9 / hbm_peak, 4),
+                 "reread_factor": round(traffic / bytes_unique, 2),
+                 "traffic_note": "ncu DRAM read + write bytes of the step's grouped-scan launches, summed"}
     return {"bound": "alu", "kernel": "grouped_scan_kernel", "achieved": round(achieved, 2),
             "peak": round(peak_ops, 2), "unit": "Tops/s", "frac": round(achieved / peak_ops, 4),
-            "traffic": None, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x max SM clock",
+            "traffic": traffic, **extra, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x max SM clock",
             "scan_ms_per_step": round(1e3 * scan_s, 4), "pairs_per_step": round(pairs),
             "hbm": {"unique_gbs": round(bytes_unique / step_s / 1e9, 1),
                     "unique_frac": round(bytes_unique / step_s / 1e9 / hbm_peak, 4),
