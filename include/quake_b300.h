@@ -21,9 +21,15 @@
  *  - No C++ exception crosses the ABI.  A failing call returns a non-zero
  *    qk_status and leaves a message for qk_last_error() (thread-local).
  *  - Device buffers must be memory of the current GPU (or managed memory).
- *  - Calls on one index are not thread-safe; use one index per host thread or
- *    serialise the calls.  Searches with device buffers may be in flight on up
- *    to 16 streams at once.
+ *  - Threads: one host thread may update an index (insert, delete, build,
+ *    load, maintain, maintain_commit; one such call at a time) while other
+ *    threads search it (qk_search*, the batch plans, each plan used by one
+ *    thread at a time) and inspect it (qk_info, qk_stats, qk_export_*,
+ *    qk_get_hits).  An update holds the index exclusively only while it
+ *    exchanges the published pointers (build and load: for the whole call).
+ *    qk_maintain_prepare must not overlap an insert or delete.  Searches with
+ *    device buffers may be in flight on up to 16 streams at once; searches
+ *    with host buffers share staging memory, one at a time.
  *  - Copy-on-write views (Sec. 9, "Concurrency"): every search reads the
  *    version of the index that was current when it was launched, to its end.
  *    Insert, delete, build, load and a maintenance commit need not wait for
@@ -701,8 +707,9 @@ qk_status qk_search_nprobe(qk_index* index, const float* q, int64_t nq, int32_t 
  *    back while free device memory is below min_free_bytes;
  *  - updates wait until update_batch are pending or the oldest has waited
  *    update_wait_s, then the group is applied as its net effect (one delete
- *    call, one insert call) on the server's update stream, beside the batches
- *    in flight, which finish on the version they were launched on;
+ *    call, one insert call) by the server's update thread on its own stream,
+ *    while the scheduler keeps launching batches; every batch reads the
+ *    version current at its launch (copy-on-write views);
  *  - every maintain_every requests a maintenance pass runs with *maint: with
  *    concurrent_maintenance it is prepared by a worker thread beside the
  *    searches (qk_maintain_prepare; updates wait meanwhile) and committed
@@ -755,9 +762,9 @@ qk_status qk_server_submit_delete(qk_server* server, int64_t id, int64_t* ticket
  * latencies in seconds (-1 where not done).  Any output may be NULL. */
 qk_status qk_server_results(qk_server* server, int64_t first, int64_t count, int32_t* done, int64_t* ids,
                             float* dist, double* latency_s);
-/* Waits until every request submitted so far is done (timeout_s <= 0: no
- * limit; QK_ERR_TIMEOUT after it).  QK_ERR_STATE if the server stopped after
- * an error (the message names it). */
+/* Waits until every request submitted so far is done and a maintenance pass
+ * they made due has run (timeout_s <= 0: no limit; QK_ERR_TIMEOUT after it).
+ * QK_ERR_STATE if the server stopped after an error (the message names it). */
 qk_status qk_server_drain(qk_server* server, double timeout_s);
 qk_status qk_server_get_stats(const qk_server* server, qk_server_stats* out);
 

@@ -942,6 +942,9 @@ qk_status qk_aps_batch_search(qk_aps_batch* b, const float* q, int64_t nq, float
                               float* out_dist, int32_t* out_nprobe, float* out_recall, int32_t* out_scanned0,
                               int32_t cap0, void* stream) {
   QK_GUARD_BEGIN
+  // the index's published structure stays put while this captures and enqueues it
+  std::shared_lock<std::shared_mutex> pub;
+  if (b && b->ix) pub = std::shared_lock<std::shared_mutex>(b->ix->pub_mu);
   QK_TRY(check_call(b, q, nq, recall_target, out_ids, out_dist, out_nprobe, out_recall, out_scanned0, cap0));
   if (nq == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
@@ -955,6 +958,9 @@ qk_status qk_aps_batch_search(qk_aps_batch* b, const float* q, int64_t nq, float
 qk_status qk_aps_batch_capture(qk_aps_batch* b, const float* q, int64_t nq, float recall_target, int64_t* out_ids,
                                float* out_dist, int32_t* out_nprobe, float* out_recall, void* stream) {
   QK_GUARD_BEGIN
+  // the index's published structure stays put while this captures and enqueues it
+  std::shared_lock<std::shared_mutex> pub;
+  if (b && b->ix) pub = std::shared_lock<std::shared_mutex>(b->ix->pub_mu);
   QK_TRY(check_call(b, q, nq, recall_target, out_ids, out_dist, out_nprobe, out_recall, nullptr, 0));
   if (nq == 0) {
     set_error("nothing to capture");
@@ -1005,6 +1011,9 @@ qk_status qk_aps_batch_capture(qk_aps_batch* b, const float* q, int64_t nq, floa
 
 qk_status qk_aps_batch_replay(qk_aps_batch* b, void* stream) {
   QK_GUARD_BEGIN
+  // the index's published structure stays put while this captures and enqueues it
+  std::shared_lock<std::shared_mutex> pub;
+  if (b && b->ix) pub = std::shared_lock<std::shared_mutex>(b->ix->pub_mu);
   if (!b || !b->graph) {
     set_error("no captured graph");
     return QK_ERR_STATE;

@@ -782,6 +782,9 @@ qk_status qk_batch_set_tiles(qk_batch* b, const qk_batch_tiles* t) {
 qk_status qk_batch_search(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
                           float* out_dist, void* stream) {
   QK_GUARD_BEGIN
+  // the index's published structure stays put while this captures and enqueues it
+  std::shared_lock<std::shared_mutex> pub;
+  if (b && b->ix) pub = std::shared_lock<std::shared_mutex>(b->ix->pub_mu);
   QK_TRY(check_call(b, q, nq, nprobe, out_ids, out_dist));
   if (nq == 0) return QK_OK;
   cudaStream_t s = (cudaStream_t)stream;
@@ -795,6 +798,9 @@ qk_status qk_batch_search(qk_batch* b, const float* q, int64_t nq, const int32_t
 qk_status qk_batch_capture(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
                            float* out_dist, void* stream) {
   QK_GUARD_BEGIN
+  // the index's published structure stays put while this captures and enqueues it
+  std::shared_lock<std::shared_mutex> pub;
+  if (b && b->ix) pub = std::shared_lock<std::shared_mutex>(b->ix->pub_mu);
   QK_TRY(check_call(b, q, nq, nprobe, out_ids, out_dist));
   if (nq == 0) {
     set_error("nothing to capture");
@@ -835,6 +841,9 @@ qk_status qk_batch_capture(qk_batch* b, const float* q, int64_t nq, const int32_
 
 qk_status qk_batch_replay(qk_batch* b, void* stream) {
   QK_GUARD_BEGIN
+  // the index's published structure stays put while this captures and enqueues it
+  std::shared_lock<std::shared_mutex> pub;
+  if (b && b->ix) pub = std::shared_lock<std::shared_mutex>(b->ix->pub_mu);
   if (!b || !b->graph) {
     set_error("no captured batch");
     return QK_ERR_STATE;
@@ -852,6 +861,9 @@ qk_status qk_batch_replay(qk_batch* b, void* stream) {
 qk_status qk_batch_autotune(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
                             float* out_dist, int32_t reps, qk_batch_tiles* chosen, void* stream) {
   QK_GUARD_BEGIN
+  // the index's published structure stays put while this captures and enqueues it
+  std::shared_lock<std::shared_mutex> pub;
+  if (b && b->ix) pub = std::shared_lock<std::shared_mutex>(b->ix->pub_mu);
   QK_TRY(check_call(b, q, nq, nprobe, out_ids, out_dist));
   if (nq == 0) {
     set_error("nothing to tune on");

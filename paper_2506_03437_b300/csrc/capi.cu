@@ -35,8 +35,8 @@ qk_status launch_scatter(const float* X, const int64_t* ids, int64_t n, int d, c
                          const int64_t* off, int32_t* cursor, float* vec, int64_t* ids_out, cudaStream_t s);
 
 qk_status launch_descend_children(const float* X, int64_t n, int d, const int32_t* parent, const float* vec1,
-                                  const int64_t* ids1, const int64_t* off1, const int32_t* size1, int32_t* leaf,
-                                  cudaStream_t s);
+                                  const int64_t* ids1, const int64_t* off1, const int32_t* size1, int32_t n_parent,
+                                  int32_t* leaf, cudaStream_t s);
 qk_status launch_nan_check(const float* X, int64_t total, int32_t* flag, cudaStream_t s);
 qk_status launch_relayout(const float* old_vec, const int64_t* old_ids, const int64_t* old_off, const int64_t* new_off,
                           const int32_t* size, int32_t n_part, int d, float* new_vec, int64_t* new_ids,
@@ -487,6 +487,7 @@ static qk_status compact(qk_index* ix, int64_t tail_min, cudaStream_t s) {
   std::vector<int64_t> mirror((size_t)total, -1);
   for (int32_t j = 0; j < N0; ++j)
     for (int32_t r = 0; r < ix->h_size0[j]; ++r) mirror[off[j] + r] = ix->h_ids0[ix->h_off0[j] + r];
+  std::unique_lock<std::shared_mutex> pub(ix->pub_mu);
   Retired old;
   old.version = ix->version;
   old.table = Table{ix->off0, ix->size0, N0};
@@ -505,6 +506,7 @@ static qk_status compact(qk_index* ix, int64_t tail_min, cudaStream_t s) {
   ix->free0.clear();
   ix->arena_id = next_arena_id();
   ++ix->version;
+  pub.unlock();
   retire(ix, std::move(old));
   return QK_OK;
 }
@@ -560,7 +562,7 @@ static qk_status relocate(qk_index* ix, const std::vector<int32_t>& moved, const
   // the destinations are free rows: no published version reads them
   QK_TRY(launch_relayout(ix->vec0, ix->ids0, doffs, doffs + m, dsz, m, d, ix->vec0, ix->ids0, s));
   if (ix->lp0) QK_TRY(launch_relayout_bytes(ix->lp0, doffs, doffs + m, dsz, m, rb, ix->lp0, s));
-  QK_CUDA(cudaStreamSynchronize(s));   // the temporaries above are stream-ordered; the copies must land first
+  // no wait here: the work that follows is on the same stream, and publish waits for it all
   old.arena = ix->arena_id;
   for (int32_t i = 0; i < m; ++i) {
     const int32_t j = moved[i];
@@ -580,7 +582,7 @@ static qk_status relocate(qk_index* ix, const std::vector<int32_t>& moved, const
 // into a spare table, waits for the update's own stream, exchanges the
 // pointers and retires the previous table with `old`.
 static qk_status publish(qk_index* ix, const std::vector<int64_t>& off, const std::vector<int64_t>& cap,
-                         const std::vector<int32_t>& size, Retired&& old, cudaStream_t s) {
+                         const std::vector<int32_t>& size, Retired&& old, int64_t dn, cudaStream_t s) {
   const int32_t N0 = ix->n_leaf;
   Table t;
   QK_TRY(take_table(ix, &t));
@@ -591,6 +593,7 @@ static qk_status publish(qk_index* ix, const std::vector<int64_t>& off, const st
     ix->spare0.push_back(t);
     return cuda_status(e, "publishing a partition table");
   }
+  std::unique_lock<std::shared_mutex> pub(ix->pub_mu);
   old.version = ix->version;
   old.arena = ix->arena_id;
   old.table = Table{ix->off0, ix->size0, N0};
@@ -599,7 +602,9 @@ static qk_status publish(qk_index* ix, const std::vector<int64_t>& off, const st
   ix->h_off0 = off;
   ix->h_cap_part0 = cap;
   ix->h_size0 = size;
+  ix->n += dn;
   ++ix->version;
+  pub.unlock();
   retire(ix, std::move(old));
   return QK_OK;
 }
@@ -807,6 +812,13 @@ void qk_destroy(qk_index* ix) {
 
 qk_status qk_build(qk_index* ix, const float* x, const int64_t* ids, int64_t n, void* stream) {
   QK_GUARD_BEGIN
+  if (ix) ix->pub_mu.lock();   // the structure is replaced: no search captures it meanwhile
+  struct Unlock {
+    qk_index* ix;
+    ~Unlock() {
+      if (ix) ix->pub_mu.unlock();
+    }
+  } unlock_pub{ix};
   if (!ix || !x || !ids || n < 1) {
     set_error("null argument or empty input");
     return QK_ERR_ARG;
@@ -843,6 +855,13 @@ qk_status qk_load(qk_index* ix, const float* x, const int64_t* ids, int64_t n, c
                   const int32_t* leaf_of_row, const float* parent_centroids, const int32_t* parent_of_leaf,
                   void* stream) {
   QK_GUARD_BEGIN
+  if (ix) ix->pub_mu.lock();   // the structure is replaced: no search captures it meanwhile
+  struct Unlock {
+    qk_index* ix;
+    ~Unlock() {
+      if (ix) ix->pub_mu.unlock();
+    }
+  } unlock_pub{ix};
   if (!ix || !x || !ids || n < 0 || !leaf_centroids || !leaf_of_row) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -877,6 +896,9 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
                              const int32_t* nprobe_q, int64_t* out_ids, float* out_dist, int32_t* out_nprobe,
                              float* out_recall, void* stream, int32_t* scan0 = nullptr, int32_t cap0 = 0,
                              int32_t* scan1 = nullptr, int32_t cap1 = 0, float ratio_eps = 0.f) {
+  if (!ix) return check_ready(ix);
+  // the published structure stays put while the launch captures it
+  std::shared_lock<std::shared_mutex> pub(ix->pub_mu);
   QK_TRY(check_ready(ix));
   if (nq < 0 || k < 1 || k > 1024 || (nq > 0 && (!q || !out_ids || !out_dist))) {
     set_error("invalid search arguments");
@@ -948,6 +970,7 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   a.scan_cap1 = cap1;
   QK_TRY(launch_search(a, s));
   note_readers(ix, s);
+  pub.unlock();
   tr.mark("launch");
   ix->queries_seen += nq;
   if (!all_dev) {
@@ -1052,14 +1075,8 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   QK_TRY(tflag.alloc<int32_t>(1, &flag));
   QK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));
   QK_TRY(launch_nan_check(X, n * d, flag, s));
-  int32_t hflag = 0;
-  QK_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  QK_CUDA(cudaStreamSynchronize(s));
-  if (hflag) {
-    set_error("insert: NaN in vectors; nothing was inserted");
-    return QK_ERR_ARG;
-  }
-  // greedy descent (Sec. 3): nearest centroid at each level, ties to the lower index
+  // greedy descent (Sec. 3): nearest centroid at each level, ties to the lower
+  // index; a row with NaN gets no leaf, and the flag refuses the whole batch
   int32_t* leaf = nullptr;
   QK_TRY(tleaf.alloc<int32_t>((size_t)n, &leaf));
   if (ix->n_parent == 0) {
@@ -1068,11 +1085,17 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
     int32_t* par = nullptr;
     QK_TRY(tpar.alloc<int32_t>((size_t)n, &par));
     QK_TRY(assign_nearest(X, n, d, ix->cent1, ix->n_parent, par, s));
-    QK_TRY(launch_descend_children(X, n, d, par, ix->vec1, ix->ids1, ix->off1, ix->size1, leaf, s));
+    QK_TRY(launch_descend_children(X, n, d, par, ix->vec1, ix->ids1, ix->off1, ix->size1, ix->n_parent, leaf, s));
   }
   std::vector<int32_t> hleaf((size_t)n);
+  int32_t hflag = 0;
   QK_CUDA(cudaMemcpyAsync(hleaf.data(), leaf, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  QK_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   QK_CUDA(cudaStreamSynchronize(s));
+  if (hflag) {
+    set_error("insert: NaN in vectors; nothing was inserted");
+    return QK_ERR_ARG;
+  }
   tr.mark("checks_descent");
   std::vector<int32_t> need(ix->h_size0);
   for (int64_t r = 0; r < n; ++r) {
@@ -1109,14 +1132,13 @@ qk_status qk_insert(qk_index* ix, const float* x, const int64_t* ids, int64_t n,
   QK_TRY(launch_place_rows(X, I, n, d, ddst, ix->vec0, ix->ids0, s));
   if (ix->lp0)   // FP8 rows use their partition's current scale (values beyond it saturate)
     QK_TRY(launch_quantize_rows(X, n, d, ddst, leaf, ix->cfg.storage, ix->lp_scale0, ix->lp0, s));
-  QK_TRY(publish(ix, off, cap, cur, std::move(old), s));
+  QK_TRY(publish(ix, off, cap, cur, std::move(old), n, s));
   for (int64_t r = 0; r < n; ++r) {
     int32_t j = hleaf[r];
     int64_t slot = dst[r] - off[j];
     ix->where[hid[r]] = ((int64_t)j << 32) | (uint32_t)slot;
     ix->h_ids0[dst[r]] = hid[r];
   }
-  ix->n += n;
   tr.mark("place");
   return QK_OK;
   QK_GUARD_END
@@ -1210,8 +1232,7 @@ qk_status qk_delete(qk_index* ix, const int64_t* ids, int64_t n, int64_t* n_remo
                                reinterpret_cast<unsigned char*>(dtv), s));
     }
   }
-  QK_TRY(publish(ix, off, cap, size, std::move(old), s));
-  ix->n -= removed;
+  QK_TRY(publish(ix, off, cap, size, std::move(old), -removed, s));
   tr.mark("moves");
   if (n_removed) *n_removed = removed;
   return QK_OK;
@@ -1230,6 +1251,8 @@ qk_status qk_check(qk_index* ix, void* stream) {
 
 qk_status qk_info(const qk_index* ix, int64_t* n_vectors, int32_t* n_leaf, int32_t* n_parent, int32_t* d) {
   QK_GUARD_BEGIN
+  std::shared_lock<std::shared_mutex> pub;
+  if (ix) pub = std::shared_lock<std::shared_mutex>(ix->pub_mu);
   if (!ix) {
     set_error("null index");
     return QK_ERR_ARG;
@@ -1244,6 +1267,8 @@ qk_status qk_info(const qk_index* ix, int64_t* n_vectors, int32_t* n_leaf, int32
 
 qk_status qk_stats(const qk_index* ix, qk_index_stats* out) {
   QK_GUARD_BEGIN
+  std::shared_lock<std::shared_mutex> pub;
+  if (ix) pub = std::shared_lock<std::shared_mutex>(ix->pub_mu);
   QK_TRY(check_ready(ix));
   if (!out) {
     set_error("null output");
@@ -1288,6 +1313,8 @@ qk_status qk_stats(const qk_index* ix, qk_index_stats* out) {
 qk_status qk_export_level(const qk_index* ix, int32_t level, int32_t* sizes, float* centroids, int64_t* ids,
                           float* vectors) {
   QK_GUARD_BEGIN
+  std::shared_lock<std::shared_mutex> pub;
+  if (ix) pub = std::shared_lock<std::shared_mutex>(ix->pub_mu);
   QK_TRY(check_ready(ix));
   const int d = ix->cfg.d;
   if (level == 0) {
@@ -1333,6 +1360,8 @@ qk_status qk_export_level(const qk_index* ix, int32_t level, int32_t* sizes, flo
 
 qk_status qk_export_quantized(const qk_index* ix, uint8_t* codes, float* scales) {
   QK_GUARD_BEGIN
+  std::shared_lock<std::shared_mutex> pub;
+  if (ix) pub = std::shared_lock<std::shared_mutex>(ix->pub_mu);
   QK_TRY(check_ready(ix));
   if (!ix->lp0) {
     set_error("the index stores FP32 only");
@@ -1356,6 +1385,8 @@ qk_status qk_export_quantized(const qk_index* ix, uint8_t* codes, float* scales)
 
 qk_status qk_get_hits(qk_index* ix, int32_t level, int64_t* hits, int32_t reset) {
   QK_GUARD_BEGIN
+  std::shared_lock<std::shared_mutex> pub;
+  if (ix) pub = std::shared_lock<std::shared_mutex>(ix->pub_mu);
   QK_TRY(check_ready(ix));
   unsigned long long* src = level == 0 ? ix->hits0 : (level == 1 ? ix->hits1 : nullptr);
   int32_t n = level == 0 ? ix->n_leaf : ix->n_parent;

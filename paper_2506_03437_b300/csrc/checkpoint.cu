@@ -290,7 +290,7 @@ static qk_status restore_impl(const char* path, qk_config* cfg_out, qk_index** o
 
 extern "C" qk_status qk_save(qk_index* ix, const char* path) {
   try {
-    return save_impl(ix, path);
+    return save_impl(ix, path);   // its reads (qk_export_level, qk_get_hits) lock for themselves
   } catch (const std::bad_alloc&) {
     set_error("qk_save: out of host memory");
     return QK_ERR_OOM;

@@ -31,6 +31,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <shared_mutex>
 #include <unordered_map>
 #include <utility>
 #include <vector>
@@ -171,12 +172,17 @@ struct qk_index {
   // id -> (partition, slot) for deletes
   std::unordered_map<int64_t, int64_t> where;
   std::atomic<int64_t> queries_seen{0};   // searched queries since the last install/maintain (the window |W|)
-  uint64_t search_seq = 0;       // launches so far (selects the work counter)
+  std::atomic<uint64_t> search_seq{0};   // launches so far (selects the work counter)
   uint64_t version = 0;          // bumped by every change of the partitions (install, insert, delete)
   // a maintenance pass planned and built by qk_maintain_prepare, not yet
   // committed, and the index version it was planned from
   qk_index* pending = nullptr;
   uint64_t pending_version = 0;
+  // Publication lock: searches (and other readers of the published structure)
+  // hold it shared while they capture pointers and enqueue work; an update
+  // holds it exclusively only to exchange pointers and host tables, so one
+  // updating thread and any number of searching threads may run together.
+  mutable std::shared_mutex pub_mu;
   // copy-on-write views: searches in flight and what older versions still use
   std::mutex view_mu;
   std::vector<qk::ViewReader> readers;

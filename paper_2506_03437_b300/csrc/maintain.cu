@@ -392,6 +392,9 @@ using namespace qk;
 // index object.  ix is only read, so searches of ix may run meanwhile.
 static qk_status maintain_plan(qk_index* ix, const qk_maint_params* params, qk_maint_action* log, int32_t log_cap,
                                int32_t* n_log, void* stream, qk_index** out) {
+  // planning only reads the published structure; updates wait, searches do not
+  std::shared_lock<std::shared_mutex> pub;
+  if (ix) pub = std::shared_lock<std::shared_mutex>(ix->pub_mu);
   *out = nullptr;
   if (!ix || !params) {
     set_error("null argument");
@@ -577,13 +580,15 @@ static qk_status maintain_plan(qk_index* ix, const qk_maint_params* params, qk_m
 static qk_status commit_structure(qk_index* ix, qk_index* nx, cudaStream_t s) {
   QK_CUDA(cudaStreamSynchronize(s));
   reclaim(ix, false);
+  std::unique_lock<std::shared_mutex> pub(ix->pub_mu);
   swap_structure(ix, nx);
   Retired r;
   r.version = ix->version;
   r.structure = nx;
-  retire(ix, std::move(r));
   ix->queries_seen = 0;
   ++ix->version;
+  pub.unlock();
+  retire(ix, std::move(r));
   return QK_OK;
 }
 

@@ -8,13 +8,13 @@
 //     and requests that arrive meanwhile join the next free slot; a batch
 //     is held back while free device memory is below min_free_bytes;
 //   - updates wait until update_batch of them are pending or the oldest has
-//     waited update_wait_s; then the group is applied, on its own stream and
-//     beside the batches in flight, as its net effect (one delete call, one
+//     waited update_wait_s; then the group goes to the update thread, which
+//     applies it on its own stream as its net effect (one delete call, one
 //     insert call: an id inserted and deleted inside the group never reaches
-//     the index, an id deleted and inserted again is deleted first).  The
-//     index's copy-on-write views let the batches in flight finish on the
-//     version they were launched on; batches launched afterwards see the
-//     update;
+//     the index, an id deleted and inserted again is deleted first), in
+//     arrival order of the groups.  The scheduler keeps launching batches
+//     meanwhile: the index's copy-on-write views let every batch read the
+//     version current at its launch;
 //   - every maintain_every operations a maintenance pass (Sec. 4) runs.  With
 //     concurrent maintenance a worker thread prepares it on its own stream
 //     (qk_maintain_prepare) while searches go on, updates wait, and the pass
@@ -102,6 +102,17 @@ struct qk_server {
   std::string prep_error;
   cudaStream_t maint_stream = nullptr;
   cudaStream_t update_stream = nullptr;
+  // the update thread and its queue of groups (upd_busy: queued or running)
+  std::thread updater;
+  mutable std::mutex upd_mu;
+  std::condition_variable upd_cv;
+  std::deque<std::vector<Op>> upd_groups;
+  int upd_busy = 0;
+  bool upd_stop = false;
+  bool hold_updates = false;   // a maintenance pass is due: take no new group until it has started
+  // drain handshake: the scheduler acknowledges a request once it has passed
+  // its maintenance step with no pass due or being prepared
+  std::atomic<int64_t> drain_req{0}, drain_ack{0};
   int64_t ops_seen = 0, passes = 0, searched_since = 0;
   // statistics
   std::atomic<int64_t> n_search{0}, n_insert{0}, n_delete{0}, batches{0}, drains{0};
@@ -207,7 +218,48 @@ void apply_updates(qk_server* sv, std::vector<Op>& group) {
     else ++sv->n_delete;
   }
   ++sv->drains;
+  std::lock_guard<std::mutex> g(sv->upd_mu);
   sv->update_s += secs(c0, now);
+}
+
+// The update thread: applies the queued groups one after the other.
+void updater_loop(qk_server* sv) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    std::vector<Op> group;
+    {
+      std::unique_lock<std::mutex> lk(sv->upd_mu);
+      sv->upd_cv.wait(lk, [&] { return sv->upd_stop || !sv->upd_groups.empty(); });
+      if (sv->upd_groups.empty()) return;
+      group = std::move(sv->upd_groups.front());
+      sv->upd_groups.pop_front();
+    }
+    try {
+      apply_updates(sv, group);
+    } catch (const std::exception& e) {
+      set_error(std::string("update thread: ") + e.what());
+      fail(sv, QK_ERR_INTERNAL, "update thread");
+    }
+    {
+      std::lock_guard<std::mutex> lk(sv->upd_mu);
+      --sv->upd_busy;
+    }
+    sv->cv.notify_all();
+  }
+}
+
+void queue_updates(qk_server* sv, std::vector<Op>&& group) {
+  {
+    std::lock_guard<std::mutex> lk(sv->upd_mu);
+    sv->upd_groups.push_back(std::move(group));
+    ++sv->upd_busy;
+  }
+  sv->upd_cv.notify_one();
+}
+
+bool updates_idle(qk_server* sv) {
+  std::lock_guard<std::mutex> lk(sv->upd_mu);
+  return sv->upd_busy == 0;
 }
 
 void run_prepare(qk_server* sv) {
@@ -228,6 +280,7 @@ void scheduler_body(qk_server* sv) {
       sv->cfg.maintain_every > 0 ? std::max<int64_t>(1, std::min<int64_t>(1000, sv->cfg.maintain_every / 10)) : 1;
   Clock::time_point prep_t0{};
   for (;;) {
+    const int64_t drain_req = sv->drain_req.load();
     // finished batches
     for (Slot& s : sv->slots)
       if (s.busy && cudaEventQuery(s.event) == cudaSuccess) finish_slot(sv, s);
@@ -245,12 +298,12 @@ void scheduler_body(qk_server* sv) {
       sv->prep_state.store(0);
     }
     const bool preparing = sv->prep_state.load() == 1;
-    // take the due updates (not while a pass is being prepared)
+    // take the due updates (not while a pass is being prepared or is due)
     std::vector<Op> group;
     bool maint_due = false;
     {
       std::unique_lock<std::mutex> g(sv->mu);
-      if (!preparing && !sv->updates.empty()) {
+      if (!preparing && !sv->hold_updates && !sv->updates.empty()) {
         const double waited = secs(sv->updates.front().t, Clock::now());
         if ((int64_t)sv->updates.size() >= sv->cfg.update_batch || waited >= sv->cfg.update_wait_s ||
             (sv->searches.empty() && sv->stopping)) {
@@ -261,26 +314,45 @@ void scheduler_body(qk_server* sv) {
       maint_due = sv->cfg.maintain_every > 0 && sv->prep_state.load() == 0 &&
                   sv->ops_seen / sv->cfg.maintain_every > sv->passes && sv->searched_since >= min_window;
     }
-    if (!group.empty()) apply_updates(sv, group);
+    if (!group.empty()) queue_updates(sv, std::move(group));
     if (maint_due) {
-      if (sv->cfg.concurrent_maintenance) {
+      // the pass plans from the current index: the pending updates go first,
+      // and no new group is taken until the update thread is idle
+      if (!sv->hold_updates) {
         std::vector<Op> pending;
         {
-          std::lock_guard<std::mutex> g(sv->mu);   // the pass plans from the current index
+          std::lock_guard<std::mutex> g(sv->mu);
           pending.assign(sv->updates.begin(), sv->updates.end());
           sv->updates.clear();
+          sv->hold_updates = true;
         }
-        if (!pending.empty()) apply_updates(sv, pending);
-        prep_t0 = Clock::now();
-        sv->prep_state.store(1);
-        sv->preparer = std::thread(run_prepare, sv);
-      } else {
-        const auto c0 = Clock::now();
-        fail(sv, qk_maintain(sv->ix, &sv->maint, nullptr, 0, nullptr, sv->update_stream), "maintain");
-        ++sv->passes;
-        sv->searched_since = 0;
-        sv->maint_stall_s += secs(c0, Clock::now());
+        if (!pending.empty()) queue_updates(sv, std::move(pending));
       }
+      if (updates_idle(sv)) {
+        {
+          std::lock_guard<std::mutex> g(sv->mu);
+          sv->hold_updates = false;
+        }
+        if (sv->cfg.concurrent_maintenance) {
+          prep_t0 = Clock::now();
+          sv->prep_state.store(1);
+          sv->preparer = std::thread(run_prepare, sv);
+        } else {
+          const auto c0 = Clock::now();
+          fail(sv, qk_maintain(sv->ix, &sv->maint, nullptr, 0, nullptr, sv->update_stream), "maintain");
+          ++sv->passes;
+          sv->searched_since = 0;
+          sv->maint_stall_s += secs(c0, Clock::now());
+        }
+      }
+    }
+    {
+      bool quiet;
+      {
+        std::lock_guard<std::mutex> g(sv->mu);
+        quiet = !sv->hold_updates;
+      }
+      if (quiet && sv->prep_state.load() == 0 && updates_idle(sv)) sv->drain_ack.store(drain_req);
     }
     // launch batches while a slot is free and memory allows
     bool launched = false;
@@ -337,7 +409,9 @@ void scheduler_body(qk_server* sv) {
       continue;
     }
     std::unique_lock<std::mutex> g(sv->mu);
-    if (sv->stopping && sv->searches.empty() && sv->updates.empty() && sv->prep_state.load() == 0) return;
+    if (sv->stopping && sv->searches.empty() && sv->updates.empty() && sv->prep_state.load() == 0 &&
+        !sv->hold_updates && updates_idle(sv))   // a due pass still runs
+      return;
     sv->cv.wait_for(g, std::chrono::microseconds(200));
   }
 }
@@ -470,11 +544,16 @@ qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server*
     ck(cudaMalloc(&s.dist_dev, sizeof(float) * mb * k));
   }
   ck(cudaStreamCreateWithFlags(&sv->maint_stream, cudaStreamNonBlocking));
-  ck(cudaStreamCreateWithFlags(&sv->update_stream, cudaStreamNonBlocking));
+  {   // updates take the highest priority: their short kernels go before queued batches
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    ck(cudaStreamCreateWithPriority(&sv->update_stream, cudaStreamNonBlocking, hi));
+  }
   if (st != QK_OK) {
     qk_server_destroy(sv);
     return st;
   }
+  sv->updater = std::thread(updater_loop, sv);
   sv->scheduler = std::thread(scheduler_loop, sv);
   *out = sv;
   return QK_OK;
@@ -554,7 +633,23 @@ qk_status qk_server_drain(qk_server* sv, double timeout_s) {
       std::lock_guard<std::mutex> g(sv->res_mu);
       for (int64_t j = n - 1; j >= 0 && all; --j) all = sv->results[(size_t)j].done.load() != 0;
     }
-    if (all) return QK_OK;
+    if (all) {
+      // every request is answered; a maintenance pass they made due must also
+      // have run: wait for the scheduler to pass its maintenance step once more
+      const int64_t req = ++sv->drain_req;
+      while (sv->drain_ack.load() < req) {
+        if (sv->failed.load()) {
+          set_error("the server stopped after an error: " + sv->error);
+          return QK_ERR_STATE;
+        }
+        if (timeout_s > 0 && secs(t0, Clock::now()) > timeout_s) {
+          set_error("drain timed out");
+          return QK_ERR_TIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+      }
+      return QK_OK;
+    }
     if (timeout_s > 0 && secs(t0, Clock::now()) > timeout_s) {
       set_error("drain timed out");
       return QK_ERR_TIMEOUT;
@@ -576,7 +671,10 @@ qk_status qk_server_get_stats(const qk_server* sv, qk_server_stats* out) {
   out->batches = sv->batches.load();
   out->update_groups = sv->drains.load();
   out->maintenance_passes = sv->passes;
-  out->update_s = sv->update_s;
+  {
+    std::lock_guard<std::mutex> lk(sv->upd_mu);
+    out->update_s = sv->update_s;
+  }
   out->maintenance_stall_s = sv->maint_stall_s;
   out->maintenance_prepare_s = sv->maint_prepare_s;
   return QK_OK;
@@ -592,6 +690,12 @@ void qk_server_destroy(qk_server* sv) {
   sv->cv.notify_all();
   if (sv->scheduler.joinable()) sv->scheduler.join();
   if (sv->preparer.joinable()) sv->preparer.join();
+  {
+    std::lock_guard<std::mutex> lk(sv->upd_mu);
+    sv->upd_stop = true;
+  }
+  sv->upd_cv.notify_all();
+  if (sv->updater.joinable()) sv->updater.join();
   for (Slot& s : sv->slots) {
     if (s.busy && s.event) cudaEventSynchronize(s.event);
     if (s.event) cudaEventDestroy(s.event);

@@ -19,11 +19,16 @@ void preload_quant_kernels();
 __global__ void descend_children_kernel(const float* __restrict__ X, int64_t n, int d,
                                         const int32_t* __restrict__ parent, const float* __restrict__ vec1,
                                         const int64_t* __restrict__ ids1, const int64_t* __restrict__ off1,
-                                        const int32_t* __restrict__ size1, int32_t* __restrict__ leaf) {
+                                        const int32_t* __restrict__ size1, int32_t n_parent,
+                                        int32_t* __restrict__ leaf) {
   int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (w >= n) return;
   int p = parent[w];
+  if (p < 0 || p >= n_parent) {   // no parent (a row the assignment could not place): no leaf
+    if (lane == 0) leaf[w] = -1;
+    return;
+  }
   const float* x = X + w * d;
   float best = INFINITY;
   int64_t best_leaf = INT64_MAX;
@@ -107,11 +112,11 @@ void preload_update_kernels() {
 }
 
 qk_status launch_descend_children(const float* X, int64_t n, int d, const int32_t* parent, const float* vec1,
-                                  const int64_t* ids1, const int64_t* off1, const int32_t* size1, int32_t* leaf,
-                                  cudaStream_t s) {
+                                  const int64_t* ids1, const int64_t* off1, const int32_t* size1, int32_t n_parent,
+                                  int32_t* leaf, cudaStream_t s) {
   if (n <= 0) return QK_OK;
   descend_children_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, d, parent, vec1, ids1, off1, size1,
-                                                                           leaf);
+                                                                           n_parent, leaf);
   QK_CUDA(cudaGetLastError());
   return QK_OK;
 }

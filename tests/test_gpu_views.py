@@ -217,3 +217,81 @@ def test_retired_rows_come_back(env):
     assert max(used[1:]) <= used[0] + room, used
     ix.insert((Q[:1] + 0.0).contiguous(), torch.tensor([10 ** 9], dtype=torch.int64, device="cuda"))
     assert ix.stats()["retired_rows"] == 0
+
+
+def test_updates_from_another_thread(env):
+    """One thread applies a sequence of inserts and deletes while another keeps searching the
+    same index.  Every search must equal, bit for bit, the search run alone on one of the
+    versions the sequence goes through, and the versions the searches see never go back.
+    The versions' own results come from a second index loaded with the same partitions and
+    given the same updates one by one."""
+    import threading
+    torch, I = env
+    X, ids, Q, g = mixture(torch, seed=14)
+    a = fresh(torch, I, X, ids)
+    sizes, cents, grouped = a.export_level(0)
+    lab = np.empty(N, np.int32)
+    lab[grouped] = np.repeat(np.arange(N_LEAF, dtype=np.int32), sizes)
+    s1, c1, g1 = a.export_level(1)
+    pol = np.empty(N_LEAF, np.int32)
+    pol[g1] = np.repeat(np.arange(N_PARENT, dtype=np.int32), s1)
+    b = I.Index(D, n_leaf=N_LEAF, n_parent=N_PARENT, kmeans_iters=4, seed=3)
+    b.load(X, ids, leaf_centroids=cents, leaf_of_row=lab, parent_centroids=c1, parent_of_leaf=pol)
+    torch.cuda.synchronize()
+    steps = []
+    nxt = N
+    for i in range(6):
+        if i % 2 == 0:
+            rows = (Q[i * 300:(i + 1) * 300] + 0.01 * torch.randn(300, D, device="cuda", generator=g)).contiguous()
+            steps.append(("insert", rows, torch.arange(nxt, nxt + 300, dtype=torch.int64, device="cuda")))
+            nxt += 300
+        else:
+            steps.append(("delete", torch.randperm(N, device="cuda", generator=g)[:500].contiguous()))
+    want = [alone(torch, b, Q)]
+    for st in steps:
+        if st[0] == "insert":
+            b.insert(st[1], st[2])
+        else:
+            b.delete(st[1])
+        want.append(alone(torch, b, Q))
+    assert all(not same(want[i], want[i + 1]) for i in range(len(steps)))
+    assert same(alone(torch, a, Q), want[0])
+
+    done = threading.Event()
+    errors = []
+
+    def updater():
+        try:
+            su = torch.cuda.Stream()
+            for st in steps:
+                if st[0] == "insert":
+                    a.insert(st[1], st[2], stream=su)
+                else:
+                    a.delete(st[1], stream=su)
+        except Exception as e:   # reported below
+            errors.append(e)
+        finally:
+            done.set()
+
+    ss = torch.cuda.Stream()
+    got = []
+    th = threading.Thread(target=updater)
+    th.start()
+    extra = 0
+    while extra < 5:
+        o = outputs(torch)
+        a.search(Q, K, recall_target=0.9, out=o, stream=ss)
+        ss.synchronize()
+        got.append([t.clone() for t in o[:3]])
+        if done.is_set():
+            extra += 1
+    th.join()
+    assert not errors, errors
+    seen = []
+    for r in got:
+        match = [i for i, w in enumerate(want) if same(r, w)]
+        assert match, "a search matched no version"
+        seen.append(match[0])
+    print(f"[views] {len(got)} searches during {len(steps)} updates from another thread saw versions "
+          f"{sorted(set(seen))}")
+    assert seen == sorted(seen) and seen[-1] == len(steps)
