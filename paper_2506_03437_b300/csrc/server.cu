@@ -532,9 +532,15 @@ qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server*
   auto ck = [&](cudaError_t e) {
     if (e != cudaSuccess && st == QK_OK) st = cuda_status(e, "server buffers");
   };
+  // stream priorities: updates (short kernels) first, then the search
+  // batches, then the maintenance pass prepared beside them (the default,
+  // lowest priority), so a pass's long kernels give way to the batches
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  const int prio_search = prio_hi < prio_lo ? prio_hi + 1 : prio_hi;
   sv->slots.resize(cfg->streams);
   for (Slot& s : sv->slots) {
-    ck(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+    ck(cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio_search));
     ck(cudaEventCreateWithFlags(&s.event, cudaEventDisableTiming));
     ck(cudaMallocHost(&s.q_host, sizeof(float) * mb * d));
     ck(cudaMallocHost(&s.ids_host, sizeof(int64_t) * mb * k));
@@ -544,11 +550,7 @@ qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server*
     ck(cudaMalloc(&s.dist_dev, sizeof(float) * mb * k));
   }
   ck(cudaStreamCreateWithFlags(&sv->maint_stream, cudaStreamNonBlocking));
-  {   // updates take the highest priority: their short kernels go before queued batches
-    int lo = 0, hi = 0;
-    cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    ck(cudaStreamCreateWithPriority(&sv->update_stream, cudaStreamNonBlocking, hi));
-  }
+  ck(cudaStreamCreateWithPriority(&sv->update_stream, cudaStreamNonBlocking, prio_hi));
   if (st != QK_OK) {
     qk_server_destroy(sv);
     return st;
