@@ -274,9 +274,11 @@ def run_ours(args):
     # the hot path: batched APS (the same decisions and results, the leaf scans
     # of all queries grouped by partition)
     batched = args.storage == "f32"
+    tiles = None
     if batched:
         plan = I.ApsBatchPlan(ix, NQ, K, rounds=args.rounds)
         bout = plan.outputs(Qd)
+        tiles = plan.autotune(Qd, tau, out=bout, reps=2, stream=stream)
 
         def step(q_):
             plan.search(q_, tau, out=bout, stream=stream)
@@ -372,6 +374,8 @@ def run_ours(args):
                        "fixed_nprobe_path": fixed, "per_query_kernel": per_query,
                        "path": (f"batched APS, {args.rounds} rounds (qk_aps_batch_search)" if plan else
                                 "per-query kernel (qk_search)"),
+                       "tiles": ({"queries_per_warp": tiles[0], "tile_rows": tiles[1], "chunk_rows": tiles[2],
+                                  "chosen_by": "autotuner (qk_aps_batch_autotune)"} if tiles else None),
                        "same_as_per_query_kernel": same,
                        "stage_ms": {k_: (round(v_, 4) if isinstance(v_, float) else [round(x, 4) for x in v_])
                                     for k_, v_ in stages.items()},

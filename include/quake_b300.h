@@ -639,6 +639,14 @@ qk_status qk_aps_batch_create(qk_index* index, int64_t max_nq, int32_t k, qk_aps
 void qk_aps_batch_destroy(qk_aps_batch* plan);
 /* Number of rounds, 1 to 16 (default 4). */
 qk_status qk_aps_batch_set_rounds(qk_aps_batch* plan, int32_t rounds);
+/* Times the tile shapes (queries_per_warp x tile_rows x chunk_rows from
+ * {1,2,4} x {16,32,64} x {1024,4096,16384}) that are valid here and keep the
+ * grouped scan's arithmetic, hence the results, unchanged (the same lanes per
+ * row as the current shape), reps batches each after one warm-up, keeps the
+ * fastest in the plan and returns it.  Synchronises the stream. */
+qk_status qk_aps_batch_autotune(qk_aps_batch* plan, const float* q, int64_t nq, float recall_target,
+                                int64_t* out_ids, float* out_dist, int32_t reps, qk_batch_tiles* chosen,
+                                void* stream);
 /* How a round's items are scanned.  0 (the only mode available) = on the
  * CUDA cores, FP32 direct differences for every row.  1 = on the tensor cores
  * (TF32 MMAs with a margin filter and an exact FP32 re-score) is refused with

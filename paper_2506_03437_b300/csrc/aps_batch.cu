@@ -918,23 +918,102 @@ qk_status qk_aps_batch_set_scan(qk_aps_batch* b, int32_t mode) {
   QK_GUARD_END
 }
 
+namespace {
+bool aps_tiles_valid(int d, const qk_batch_tiles& t) {
+  return (t.queries_per_warp == 1 || t.queries_per_warp == 2 || t.queries_per_warp == 4) &&
+         !(t.queries_per_warp == 4 && d > 512) && t.tile_rows >= 1 &&
+         (size_t)bt::kStages * t.tile_rows * d * 4 <= 200 * 1024 && t.chunk_rows >= t.tile_rows &&
+         t.chunk_rows >= 1024;
+}
+
+// Lanes that sum one row in the grouped scan for queries_per_warp qw; shapes
+// with the same count give bitwise the same distances.
+int scan_lanes(int d, int qw) {
+  switch (d) {
+#define QK_LANES(D) \
+  case D: return qw == 1 ? bt::tpr_for(D, 1) : qw == 2 ? bt::tpr_for(D, 2) : bt::tpr_for(D, 4);
+    QK_LANES(32) QK_LANES(64) QK_LANES(96) QK_LANES(128) QK_LANES(192) QK_LANES(256) QK_LANES(384)
+    QK_LANES(512) QK_LANES(768) QK_LANES(1024)
+#undef QK_LANES
+    default: return 0;
+  }
+}
+}  // namespace
+
 qk_status qk_aps_batch_set_tiles(qk_aps_batch* b, const qk_batch_tiles* t) {
   QK_GUARD_BEGIN
   if (!b || !t) {
     set_error("null argument");
     return QK_ERR_ARG;
   }
-  const int d = b->ix->cfg.d;
-  if ((t->queries_per_warp != 1 && t->queries_per_warp != 2 && t->queries_per_warp != 4) ||
-      (t->queries_per_warp == 4 && d > 512) || t->tile_rows < 1 ||
-      (size_t)bt::kStages * t->tile_rows * d * 4 > 200 * 1024 || t->chunk_rows < t->tile_rows ||
-      t->chunk_rows < 1024) {
+  if (!aps_tiles_valid(b->ix->cfg.d, *t)) {
     set_error("invalid tiles (queries_per_warp 1, 2 or 4; 3 tiles within 200 KB; chunk_rows >= 1024)");
     return QK_ERR_ARG;
   }
   b->tiles = *t;
   b->version = ~0ull;   // the candidate buffer depends on chunk_rows
   return QK_OK;
+  QK_GUARD_END
+}
+
+qk_status qk_aps_batch_autotune(qk_aps_batch* b, const float* q, int64_t nq, float recall_target, int64_t* out_ids,
+                                float* out_dist, int32_t reps, qk_batch_tiles* chosen, void* stream) {
+  QK_GUARD_BEGIN
+  std::shared_lock<std::shared_mutex> pub;
+  if (b && b->ix) pub = std::shared_lock<std::shared_mutex>(b->ix->pub_mu);
+  QK_TRY(check_call(b, q, nq, recall_target, out_ids, out_dist, nullptr, nullptr, nullptr, 0));
+  if (nq == 0) {
+    set_error("nothing to tune on");
+    return QK_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int d = b->ix->cfg.d;
+  const int lanes = scan_lanes(d, b->tiles.queries_per_warp);
+  reps = std::max(1, reps);
+  std::vector<qk_batch_tiles> cands;
+  for (int qw : {1, 2, 4})
+    for (int tr : {16, 32, 64})
+      for (int ch : {1024, 4096, 16384}) {
+        const qk_batch_tiles t{qw, tr, ch};
+        if (aps_tiles_valid(d, t) && scan_lanes(d, qw) == lanes) cands.push_back(t);
+      }
+  cudaEvent_t e0, e1;
+  QK_CUDA(cudaEventCreate(&e0));
+  QK_CUDA(cudaEventCreate(&e1));
+  float best = INFINITY;
+  const qk_batch_tiles keep = b->tiles;
+  qk_batch_tiles best_t = keep;
+  qk_status st = QK_OK;
+  for (const qk_batch_tiles& t : cands) {
+    b->tiles = t;
+    b->version = ~0ull;
+    st = refresh(b, s);
+    if (st == QK_OK)   // warm-up
+      st = enqueue(b, q, nq, recall_target, out_ids, out_dist, nullptr, nullptr, nullptr, 0, s);
+    if (st != QK_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == QK_OK; ++r)
+      st = enqueue(b, q, nq, recall_target, out_ids, out_dist, nullptr, nullptr, nullptr, 0, s);
+    cudaEventRecord(e1, s);
+    if (st != QK_OK) break;
+    const cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      st = cuda_status(e, "autotune");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tiles = st == QK_OK ? best_t : keep;
+  b->version = ~0ull;
+  if (chosen) *chosen = b->tiles;
+  return st;
   QK_GUARD_END
 }
 

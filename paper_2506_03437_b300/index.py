@@ -432,6 +432,17 @@ class ApsBatchPlan:
         t = L.QkBatchTiles(int(queries_per_warp), int(tile_rows), int(chunk_rows))
         L.check(L.lib.qk_aps_batch_set_tiles(self._h, C.byref(t)))
 
+    def autotune(self, q, recall_target=0.9, out=None, reps=3, stream=None):
+        """Times the tile shapes that keep the results unchanged on this batch and keeps
+        the fastest; returns (queries_per_warp, tile_rows, chunk_rows)."""
+        q = _as(q, np.float32)
+        out = self.outputs(q) if out is None else out
+        t = L.QkBatchTiles()
+        L.check(L.lib.qk_aps_batch_autotune(self._h, L.ptr(q), int(q.shape[0]), float(recall_target),
+                                            L.ptr(out[0]), L.ptr(out[1]), int(reps), C.byref(t),
+                                            L.stream_ptr(stream)))
+        return (t.queries_per_warp, t.tile_rows, t.chunk_rows)
+
     def set_scan(self, mode):
         """1: the rounds scan on the tensor cores (TF32 + exact re-score); 0: on the CUDA cores."""
         L.check(L.lib.qk_aps_batch_set_scan(self._h, int(mode)))

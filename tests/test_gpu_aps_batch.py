@@ -150,3 +150,22 @@ def test_batched_aps_refuses_bad_queries_and_answers_the_rest(I, two_level):
         plan.search(torch.from_numpy(Q).cuda(), 0.0)
     with pytest.raises(L.QkError):
         I.ApsBatchPlan(ix, 10, 64)                  # k > 32
+
+
+def test_autotune_keeps_results():
+    """qk_aps_batch_autotune times only shapes that keep the grouped scan's arithmetic: the
+    batch after tuning equals the batch before it, bit for bit."""
+    import torch
+    from paper_2506_03437_b300 import index as I, synth
+    X, ids, Q = synth.aps_search(seed=71, n=60_000, d=128, n_comp=60, sigma=1.2, nq=1500)
+    ix = I.Index(128, n_leaf=120, n_parent=8, kmeans_iters=3, seed=2)
+    Xd, idd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(ids).cuda(), torch.from_numpy(Q).cuda()
+    ix.build(Xd, idd)
+    plan = I.ApsBatchPlan(ix, 1500, 10)
+    before = [t.clone() for t in plan.search(Qd, 0.9)[:3]]
+    chosen = plan.autotune(Qd, 0.9, reps=1)
+    after = plan.search(Qd, 0.9)
+    torch.cuda.synchronize()
+    assert chosen[0] in (1, 2, 4) and chosen[1] in (16, 32, 64) and chosen[2] in (1024, 4096, 16384)
+    assert all(bool((a == b).all()) for a, b in zip(before, after[:3]))
+    plan.close()
