@@ -323,26 +323,26 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
           const int rr = r0 + rsub;
           const bool rv = rr < rows_t;
           const float4* x4 = reinterpret_cast<const float4*>(tile + (rv ? rr : 0) * D);
-          float acc[QW], acc2[QW];   // two independent FMA chains per query
+          // two independent FMA chains per query (elements x, z and y, w of each
+          // float4), as packed pairs: one FADD2 and one FFMA2 per two elements
+          float2 ch[QW];
 #pragma unroll
-          for (int j = 0; j < QW; ++j) acc[j] = acc2[j] = 0.f;
+          for (int j = 0; j < QW; ++j) ch[j] = make_float2(0.f, 0.f);
 #pragma unroll
           for (int f = 0; f < F4; ++f) {
             const float4 x = x4[part + TPR * f];
+            const float2 nxa = make_float2(-x.x, -x.y), nxb = make_float2(-x.z, -x.w);
 #pragma unroll
             for (int j = 0; j < QW; ++j) {
-              float e = qv[j][f].x - x.x;
-              acc[j] = fmaf(e, e, acc[j]);
-              e = qv[j][f].y - x.y;
-              acc2[j] = fmaf(e, e, acc2[j]);
-              e = qv[j][f].z - x.z;
-              acc[j] = fmaf(e, e, acc[j]);
-              e = qv[j][f].w - x.w;
-              acc2[j] = fmaf(e, e, acc2[j]);
+              const float2 ea = __fadd2_rn(make_float2(qv[j][f].x, qv[j][f].y), nxa);
+              ch[j] = __ffma2_rn(ea, ea, ch[j]);
+              const float2 eb = __fadd2_rn(make_float2(qv[j][f].z, qv[j][f].w), nxb);
+              ch[j] = __ffma2_rn(eb, eb, ch[j]);
             }
           }
+          float acc[QW];
 #pragma unroll
-          for (int j = 0; j < QW; ++j) acc[j] += acc2[j];
+          for (int j = 0; j < QW; ++j) acc[j] = ch[j].x + ch[j].y;
 #pragma unroll
           for (int j = 0; j < QW; ++j) {
 #pragma unroll
