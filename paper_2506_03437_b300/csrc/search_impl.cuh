@@ -112,9 +112,10 @@ struct ElemFP8 {
     uint32_t u = reinterpret_cast<const uint32_t*>(row)[i];
     __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3);
     __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3);
-    float2 a = __half22float2(*reinterpret_cast<__half2*>(&lo));
-    float2 b = __half22float2(*reinterpret_cast<__half2*>(&hi));
-    return make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
+    const float2 sc = make_float2(scale, scale);
+    const float2 a = __fmul2_rn(__half22float2(*reinterpret_cast<__half2*>(&lo)), sc);
+    const float2 b = __fmul2_rn(__half22float2(*reinterpret_cast<__half2*>(&hi)), sc);
+    return make_float4(a.x, a.y, b.x, b.y);
   }
 };
 
@@ -420,28 +421,27 @@ struct Block {
         const int rr = r + ROWS * i;
         if (rr < nr) {
           const unsigned char* row = tile + (size_t)rr * D * E::kBytes;
-          float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;   // four independent FMA chains
+          // four independent FMA chains, as two packed pairs (FADD2 / FFMA2
+          // do two FP32 operations per instruction, each rounded as alone)
+          float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
           if (metric == QK_METRIC_L2) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
               float4 x = E::load4(row, sub + TPR * v, scale);
-              float dx = x.x - qv[v].x, dy = x.y - qv[v].y, dz = x.z - qv[v].z, dw = x.w - qv[v].w;
-              a0 = fmaf(dx, dx, a0);
-              a1 = fmaf(dy, dy, a1);
-              a2 = fmaf(dz, dz, a2);
-              a3 = fmaf(dw, dw, a3);
+              const float2 d01 = __fadd2_rn(make_float2(x.x, x.y), make_float2(-qv[v].x, -qv[v].y));
+              const float2 d23 = __fadd2_rn(make_float2(x.z, x.w), make_float2(-qv[v].z, -qv[v].w));
+              a01 = __ffma2_rn(d01, d01, a01);
+              a23 = __ffma2_rn(d23, d23, a23);
             }
           } else {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
               float4 x = E::load4(row, sub + TPR * v, scale);
-              a0 = fmaf(x.x, qv[v].x, a0);
-              a1 = fmaf(x.y, qv[v].y, a1);
-              a2 = fmaf(x.z, qv[v].z, a2);
-              a3 = fmaf(x.w, qv[v].w, a3);
+              a01 = __ffma2_rn(make_float2(x.x, x.y), make_float2(qv[v].x, qv[v].y), a01);
+              a23 = __ffma2_rn(make_float2(x.z, x.w), make_float2(qv[v].z, qv[v].w), a23);
             }
           }
-          acc[i] = (a0 + a1) + (a2 + a3);
+          acc[i] = (a01.x + a01.y) + (a23.x + a23.y);
         }
       }
 #pragma unroll
