@@ -23,7 +23,7 @@ SEARCH_DIMS = [32, 64, 96, 128, 192, 256, 384, 512, 768, 1024]
 SOURCES = (["capi.cu", "search.cu", "kmeans.cu", "arena.cu", "update.cu", "maintain.cu", "quant.cu", "tc_score.cu",
             "noalloc.cu", "batch.cu", "aps_batch.cu", "tc_grouped.cu", "server.cu", "profile.cu", "checkpoint.cu",
             "views.cu"] + [f"search_d{d}.cu" for d in SEARCH_DIMS])
-HEADERS = ["common.cuh", "capvol.cuh", "index.cuh", "trace.h", "search_impl.cuh", "devmem.h", "grouped.cuh", "tc_common.cuh"]
+HEADERS = ["common.cuh", "capvol.cuh", "index.cuh", "trace.h", "search_impl.cuh", "devmem.h", "grouped.cuh", "tc_common.cuh", "aps_prepare.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMPILE_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -38,6 +38,7 @@
 
 #include "capvol.cuh"
 #include "common.cuh"
+#include "aps_prepare.cuh"
 #include "grouped.cuh"
 #include "index.cuh"
 #include "trace.h"
@@ -584,7 +585,10 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   sa.xs_cand = b->st.cand;
   sa.xs_t = b->st.t;
   sa.xs_mcap = mcap;
-  QK_TRY(launch_search(sa, s));
+  if (ap::fits(sa))   // one warp per query; the per-query kernel where the warp's buffers are too small
+    QK_TRY(ap::launch_prepare(sa, s));
+  else
+    QK_TRY(launch_search(sa, s));
   tr.mark("prepare");
   QK_TRY(mark(1));
   if (b->rstats) QK_CUDA(cudaMemsetAsync(b->rstats, 0, sizeof(unsigned long long) * (2 * (ab::kMaxRounds + 1) + 1), s));
