@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "capvol.cuh"
 #include "common.cuh"
 #include "grouped.cuh"
@@ -22,9 +24,9 @@ namespace qk {
 namespace ap {
 
 constexpr int kWarps = 4;     // queries per block
-constexpr int kRCap = 224;    // result set R of a level (K <= kRCap)
+constexpr int kRCap = 224;    // the largest result set R of a level (K <= kRCap)
 constexpr int kBuf = 32;      // survivors waiting for a merge
-constexpr int kMCap = 256;    // candidates of the level searched by Algorithm 1
+constexpr int kMCap = 256;    // the most candidates of a level searched by Algorithm 1
 
 // Shared memory of one warp.
 struct Ws {
@@ -42,11 +44,15 @@ struct Ws {
   uint8_t* csc;     // kMCap: scanned
 };
 
-__host__ __device__ constexpr size_t warp_bytes(int D) {
-  return (size_t)D * 4 + (size_t)kRCap * 12 * 2 + (size_t)kBuf * 12 + (size_t)kMCap * (4 + 4 + 8 + 8 + 1) + 64;
+// Bytes of one warp's buffers for results of up to rcap and mcap candidates
+// (every piece rounded to 16 bytes).
+__host__ __device__ inline size_t warp_bytes(int D, int rcap, int mcap) {
+  auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+  return r16(8 * (size_t)rcap) * 2 + r16(8 * (size_t)kBuf) + r16(8 * (size_t)mcap) * 2 + r16(4 * (size_t)D) +
+         r16(4 * (size_t)rcap) * 2 + r16(4 * (size_t)kBuf) + r16(4 * (size_t)mcap) * 2 + r16(mcap);
 }
 
-__device__ inline Ws carve(unsigned char* base, int D) {
+__device__ inline Ws carve(unsigned char* base, int D, int rcap, int mcap) {
   Ws w;
   unsigned char* p = base;
   auto take = [&](size_t bytes) {
@@ -54,18 +60,18 @@ __device__ inline Ws carve(unsigned char* base, int D) {
     p += (bytes + 15) & ~size_t(15);
     return r;
   };
-  w.ri = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * kRCap));
-  w.oi = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * kRCap));
+  w.ri = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * rcap));
+  w.oi = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * rcap));
   w.bi = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * kBuf));
-  w.ct = reinterpret_cast<double*>(take(sizeof(double) * kMCap));
-  w.cp = reinterpret_cast<double*>(take(sizeof(double) * kMCap));
+  w.ct = reinterpret_cast<double*>(take(sizeof(double) * mcap));
+  w.cp = reinterpret_cast<double*>(take(sizeof(double) * mcap));
   w.sq = reinterpret_cast<float*>(take(sizeof(float) * D));
-  w.rd = reinterpret_cast<float*>(take(sizeof(float) * kRCap));
-  w.od = reinterpret_cast<float*>(take(sizeof(float) * kRCap));
+  w.rd = reinterpret_cast<float*>(take(sizeof(float) * rcap));
+  w.od = reinterpret_cast<float*>(take(sizeof(float) * rcap));
   w.bd = reinterpret_cast<float*>(take(sizeof(float) * kBuf));
-  w.cpart = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kMCap));
-  w.cD = reinterpret_cast<float*>(take(sizeof(float) * kMCap));
-  w.csc = reinterpret_cast<uint8_t*>(take(kMCap));
+  w.cpart = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * mcap));
+  w.cD = reinterpret_cast<float*>(take(sizeof(float) * mcap));
+  w.csc = reinterpret_cast<uint8_t*>(take(mcap));
   return w;
 }
 
@@ -320,8 +326,14 @@ struct Warp {
   }
 };
 
+// Buffer sizes of a search: R holds the root's M_root and the upper level's
+// k1 results; the candidates of a level are the root's M_root (with one
+// level, the leaves exported from the root scan).
+inline int rcap_of(const SearchArgs& a) { return ((std::max(a.M_root, a.L == 2 ? a.k1 : 0) + 31) / 32) * 32; }
+inline int mcap_of(const SearchArgs& a) { return std::max(1, std::max(a.M_root, a.L == 2 ? a.k1 : 0)); }
+
 template <int TPR, int NV>
-__global__ void __launch_bounds__(kWarps * 32) aps_prepare_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(kWarps * 32) aps_prepare_kernel(SearchArgs a, int rcap, int mcap) {
   using W = Warp<TPR, NV>;
   constexpr int D = W::D;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -329,7 +341,7 @@ __global__ void __launch_bounds__(kWarps * 32) aps_prepare_kernel(SearchArgs a) 
   const int64_t qi = blockIdx.x * (int64_t)kWarps + warp;
   if (qi >= a.nq) return;
   W b;
-  b.w = carve(smem + (size_t)warp * ((warp_bytes(D) + 15) & ~size_t(15)), D);
+  b.w = carve(smem + (size_t)warp * warp_bytes(D, rcap, mcap), D, rcap, mcap);
   b.lane = lane;
   const float* q = a.Q + qi * D;
   for (int i = lane; i < D; i += 32) b.w.sq[i] = q[i];
@@ -381,21 +393,22 @@ __global__ void __launch_bounds__(kWarps * 32) aps_prepare_kernel(SearchArgs a) 
 
 // Whether the warp layout holds this search's candidate counts.
 inline bool fits(const SearchArgs& a) {
-  return a.M_root <= kRCap && a.M_root <= kMCap && (a.L == 1 || a.k1 <= kRCap) && a.xs_mcap >= 1;
+  return a.M_root <= kRCap && (a.L == 1 || a.k1 <= kRCap) && mcap_of(a) <= kMCap && a.xs_mcap >= 1;
 }
 
 template <int TPR, int NV>
 qk_status launch_t(const SearchArgs& a, cudaStream_t s) {
   constexpr int D = NV * 4 * TPR;
-  const size_t per_warp = (warp_bytes(D) + 15) & ~size_t(15);
-  const size_t smem = per_warp * kWarps;
-  static bool attr = false;   // set once per instantiation, outside any capture
+  const int rcap = rcap_of(a), mcap = mcap_of(a);
+  const size_t smem = warp_bytes(D, rcap, mcap) * kWarps;
+  static bool attr = false;   // the largest size, set once per instantiation, outside any capture
   if (!attr) {
-    QK_CUDA(cudaFuncSetAttribute(aps_prepare_kernel<TPR, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QK_CUDA(cudaFuncSetAttribute(aps_prepare_kernel<TPR, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(warp_bytes(D, kRCap, kMCap) * kWarps)));
     attr = true;
   }
   const unsigned grid = (unsigned)((a.nq + kWarps - 1) / kWarps);
-  aps_prepare_kernel<TPR, NV><<<grid, kWarps * 32, smem, s>>>(a);
+  aps_prepare_kernel<TPR, NV><<<grid, kWarps * 32, smem, s>>>(a, rcap, mcap);
   QK_CUDA(cudaGetLastError());
   return QK_OK;
 }
