@@ -117,6 +117,7 @@ struct ReplayArgs {
   unsigned long long* rstats = nullptr;   // per round: items asked for, items taken in
   int32_t* status = nullptr;
   int64_t* diag = nullptr;
+  unsigned long long* next_q = nullptr;   // the next query a warp takes (zeroed per launch)
 };
 
 // p from Eq. 8-9 with the raw caps for p_0 (as the per-query kernel computes
@@ -208,12 +209,9 @@ __device__ int take_in(float* bd, int64_t* bi, int rn, int k, const float* cd, c
   return bt::warp_compact(bd, bi, cnt, k, lane);
 }
 
-__global__ void __launch_bounds__(kThreads) aps_replay_kernel(ReplayArgs a) {
-  __shared__ float s_bd[kWarps][64];
-  __shared__ int64_t s_bi[kWarps][64];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t q = blockIdx.x * (int64_t)kWarps + warp;
-  if (q >= a.nq) return;
+// Algorithm 1 of query q over the round just scanned, and its next requests
+// (one warp; bd / bi its 64-entry buffer in shared memory).
+__device__ void replay_query(const ReplayArgs& a, const int64_t q, float* bd, int64_t* bi, const int lane) {
   const State& S = a.st;
   const int M = S.M[q];
   const int k = a.k;
@@ -230,8 +228,6 @@ __global__ void __launch_bounds__(kThreads) aps_replay_kernel(ReplayArgs a) {
   const double* t = S.t + q * a.mcap;
   double* p = S.p + q * a.mcap;
   uint8_t* fl = S.flag + q * a.mcap;
-  float* bd = s_bd[warp];
-  int64_t* bi = s_bi[warp];
   int rn = 0, ns = 0;
   double rho = 0.0, r = 0.0;
   if (a.first) {
@@ -378,6 +374,22 @@ __global__ void __launch_bounds__(kThreads) aps_replay_kernel(ReplayArgs a) {
     // next float above it; L2 distances are >= 0, so bits order like values
     a.gtau[q] = rn == k ? __float_as_uint(nextafterf(bd[k - 1], INFINITY)) : 0x7f7f7f7fu;
     if (a.rstats) atomicAdd(&a.rstats[2 * (a.round + 1)], (unsigned long long)nreq);
+  }
+}
+
+// Persistent: each warp takes the next query from a counter (zeroed before the
+// launch), so queries with long walks do not hold a block's other warps.
+__global__ void __launch_bounds__(kThreads) aps_replay_kernel(ReplayArgs a) {
+  __shared__ float s_bd[kWarps][64];
+  __shared__ int64_t s_bi[kWarps][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long q = 0;
+    if (lane == 0) q = atomicAdd(a.next_q, 1ull);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= (unsigned long long)a.nq) break;
+    replay_query(a, (int64_t)q, s_bd[warp], s_bi[warp], lane);
+    __syncwarp();
   }
 }
 
@@ -624,11 +636,20 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   ra.cpos = b->cpos;
   ra.qcoff = b->qcoff;
   ra.qcnt = b->qcnt;
-  const unsigned rgrid = (unsigned)((nq + ab::kWarps - 1) / ab::kWarps);
+  // the replay is persistent: as many blocks as the SMs hold at once, at most one per kWarps queries
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ab::aps_replay_kernel, ab::kThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const unsigned rgrid = (unsigned)std::min<int64_t>((nq + ab::kWarps - 1) / ab::kWarps,
+                                                     (int64_t)b->n_sm * std::max(1, per_sm));
+  ra.next_q = b->work + 1;
   QK_CUDA(cudaMemsetAsync(b->pcount, 0, sizeof(int32_t) * K, s));
   ra.first = 1;
   ra.round = -1;
   ra.final_request = b->rounds == 1;
+  QK_CUDA(cudaMemsetAsync(b->work + 1, 0, sizeof(unsigned long long), s));
   ab::aps_replay_kernel<<<rgrid, ab::kThreads, 0, s>>>(ra);
   QK_CUDA(cudaGetLastError());
   QK_TRY(mark(2));
@@ -705,6 +726,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     QK_CUDA(cudaMemsetAsync(b->pcount, 0, sizeof(int32_t) * K, s));
     ra.round = rd;
     ra.final_request = rd + 1 == b->rounds - 1;
+    QK_CUDA(cudaMemsetAsync(b->work + 1, 0, sizeof(unsigned long long), s));
     ab::aps_replay_kernel<<<rgrid, ab::kThreads, 0, s>>>(ra);
     QK_CUDA(cudaGetLastError());
     QK_TRY(mark(5 + 3 * rd));
@@ -870,7 +892,7 @@ qk_status qk_aps_batch_create(qk_index* ix, int64_t max_nq, int32_t k, qk_aps_ba
   run(aalloc(&b->qcoff, nq + 1));
   run(aalloc(&b->qcnt, nq));
   run(aalloc(&b->gtau, nq));
-  run(aalloc(&b->work, 1));
+  run(aalloc(&b->work, 2));   // [0] the grouped scan's units, [1] the replay's queries
   run(aalloc(&b->rstats, 2 * (ab::kMaxRounds + 1) + 1));   // per round asked / taken, then the exact fallbacks
   if (st == QK_OK) st = refresh(b, 0);
   if (st != QK_OK) {
