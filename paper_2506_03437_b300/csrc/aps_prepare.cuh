@@ -333,16 +333,8 @@ inline int rcap_of(const SearchArgs& a) { return ((std::max(a.M_root, a.L == 2 ?
 inline int mcap_of(const SearchArgs& a) { return std::max(1, std::max(a.M_root, a.L == 2 ? a.k1 : 0)); }
 
 template <int TPR, int NV>
-__global__ void __launch_bounds__(kWarps * 32) aps_prepare_kernel(SearchArgs a, int rcap, int mcap) {
-  using W = Warp<TPR, NV>;
-  constexpr int D = W::D;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t qi = blockIdx.x * (int64_t)kWarps + warp;
-  if (qi >= a.nq) return;
-  W b;
-  b.w = carve(smem + (size_t)warp * warp_bytes(D, rcap, mcap), D, rcap, mcap);
-  b.lane = lane;
+__device__ void prepare_query(const SearchArgs& a, Warp<TPR, NV>& b, const int64_t qi, const int lane) {
+  constexpr int D = Warp<TPR, NV>::D;
   const float* q = a.Q + qi * D;
   for (int i = lane; i < D; i += 32) b.w.sq[i] = q[i];
   __syncwarp();
@@ -391,6 +383,26 @@ __global__ void __launch_bounds__(kWarps * 32) aps_prepare_kernel(SearchArgs a, 
   if (lane == 0) a.xs_M[qi] = M;
 }
 
+// Persistent: each warp takes the next query from a.work (zeroed before the
+// launch), so long upper-level walks do not hold a block's other warps.
+template <int TPR, int NV>
+__global__ void __launch_bounds__(kWarps * 32) aps_prepare_kernel(SearchArgs a, int rcap, int mcap) {
+  using W = Warp<TPR, NV>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  W b;
+  b.w = carve(smem + (size_t)warp * warp_bytes(W::D, rcap, mcap), W::D, rcap, mcap);
+  b.lane = lane;
+  for (;;) {
+    int qi = 0;
+    if (lane == 0) qi = atomicAdd(a.work, 1);
+    qi = __shfl_sync(0xffffffffu, qi, 0);
+    if ((int64_t)qi >= a.nq) break;
+    prepare_query<TPR, NV>(a, b, qi, lane);
+    __syncwarp();
+  }
+}
+
 // Whether the warp layout holds this search's candidate counts.
 inline bool fits(const SearchArgs& a) {
   return a.M_root <= kRCap && (a.L == 1 || a.k1 <= kRCap) && mcap_of(a) <= kMCap && a.xs_mcap >= 1;
@@ -407,7 +419,17 @@ qk_status launch_t(const SearchArgs& a, cudaStream_t s) {
                                  (int)(warp_bytes(D, kRCap, kMCap) * kWarps)));
     attr = true;
   }
-  const unsigned grid = (unsigned)((a.nq + kWarps - 1) / kWarps);
+  int per_sm = 1, dev = 0, n_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, aps_prepare_kernel<TPR, NV>, kWarps * 32, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const unsigned grid =
+      (unsigned)std::min<int64_t>((a.nq + kWarps - 1) / kWarps, (int64_t)n_sm * std::max(1, per_sm));
+  QK_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int32_t), s));
   aps_prepare_kernel<TPR, NV><<<grid, kWarps * 32, smem, s>>>(a, rcap, mcap);
   QK_CUDA(cudaGetLastError());
   return QK_OK;
