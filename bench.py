@@ -278,7 +278,11 @@ def run_ours(args):
     if batched:
         plan = I.ApsBatchPlan(ix, NQ, K, rounds=args.rounds)
         bout = plan.outputs(Qd)
-        tiles = plan.autotune(Qd, tau, out=bout, reps=2, stream=stream)
+        if args.tiles:
+            tiles = tuple(int(x) for x in args.tiles.split(","))
+            plan.set_tiles(*tiles)
+        else:
+            tiles = plan.autotune(Qd, tau, out=bout, reps=2, stream=stream)
 
         def step(q_):
             plan.search(q_, tau, out=bout, stream=stream)
@@ -375,7 +379,7 @@ def run_ours(args):
                        "path": (f"batched APS, {args.rounds} rounds (qk_aps_batch_search)" if plan else
                                 "per-query kernel (qk_search)"),
                        "tiles": ({"queries_per_warp": tiles[0], "tile_rows": tiles[1], "chunk_rows": tiles[2],
-                                  "chosen_by": "autotuner (qk_aps_batch_autotune)"} if tiles else None),
+                                  "chosen_by": "flag" if args.tiles else "autotuner (qk_aps_batch_autotune)"} if tiles else None),
                        "same_as_per_query_kernel": same,
                        "stage_ms": {k_: (round(v_, 4) if isinstance(v_, float) else [round(x, 4) for x in v_])
                                     for k_, v_ in stages.items()},
@@ -1094,8 +1098,8 @@ def main():
                     help="noise s of the precision mixture: x = normalize(mu + s g / sqrt(d))")
     ap.add_argument("--prec-forms", default="f32,bf16,fp8", help="storage forms of the precision workload")
     ap.add_argument("--prec-fm", type=float, default=0.02, help="f_M of the leaf level (candidate fraction)")
-    ap.add_argument("--tiles", default="", help="queries_per_warp,tile_rows,chunk_rows for the batching "
-                                                 "workload instead of the autotuner's choice")
+    ap.add_argument("--tiles", default="", help="queries_per_warp,tile_rows,chunk_rows of the grouped scan "
+                                                 "(aps and batch workloads) instead of the autotuner's choice")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-workers", type=int, default=-1,
                     help="processes of the parallel oracle leg (-1: the host's cores, at most 64; 0 or 1: skip)")

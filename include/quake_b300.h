@@ -552,7 +552,7 @@ typedef struct qk_batch qk_batch;
 
 /* Tile shapes of the grouped scan. */
 typedef struct {
-  int32_t queries_per_warp;  /* 1, 2 or 4 (4 needs d <= 512): G = 8 x this queries per unit */
+  int32_t queries_per_warp;  /* 1, 2 or 4 (4 needs d <= 128 or d = 384, 512): G = 8 x this queries per unit */
   int32_t tile_rows;         /* rows per shared-memory tile (3 tiles in flight, <= 200 KB together) */
   int32_t chunk_rows;        /* rows per unit (>= tile_rows, >= 1024) */
 } qk_batch_tiles;
@@ -640,10 +640,10 @@ void qk_aps_batch_destroy(qk_aps_batch* plan);
 /* Number of rounds, 1 to 16 (default 4). */
 qk_status qk_aps_batch_set_rounds(qk_aps_batch* plan, int32_t rounds);
 /* Times the tile shapes (queries_per_warp x tile_rows x chunk_rows from
- * {1,2,4} x {16,32,64} x {1024,4096,16384}) that are valid here and keep the
- * grouped scan's arithmetic, hence the results, unchanged (the same lanes per
- * row as the current shape), reps batches each after one warm-up, keeps the
- * fastest in the plan and returns it.  Synchronises the stream. */
+ * {1,2,4} x {16,32,64} x {1024,4096,16384}) that are valid here, reps
+ * batches each after one warm-up, keeps the fastest in the plan and returns
+ * it.  Every shape sums each row in the per-query kernel's order, so the
+ * results do not depend on the choice.  Synchronises the stream. */
 qk_status qk_aps_batch_autotune(qk_aps_batch* plan, const float* q, int64_t nq, float recall_target,
                                 int64_t* out_ids, float* out_dist, int32_t reps, qk_batch_tiles* chosen,
                                 void* stream);

@@ -947,22 +947,9 @@ qk_status qk_aps_batch_set_scan(qk_aps_batch* b, int32_t mode) {
 namespace {
 bool aps_tiles_valid(int d, const qk_batch_tiles& t) {
   return (t.queries_per_warp == 1 || t.queries_per_warp == 2 || t.queries_per_warp == 4) &&
-         !(t.queries_per_warp == 4 && d > 512) && t.tile_rows >= 1 &&
+         bt::tpr_for(d, t.queries_per_warp) > 0 && t.tile_rows >= 1 &&
          (size_t)bt::kStages * t.tile_rows * d * 4 <= 200 * 1024 && t.chunk_rows >= t.tile_rows &&
          t.chunk_rows >= 1024;
-}
-
-// Lanes that sum one row in the grouped scan for queries_per_warp qw; shapes
-// with the same count give bitwise the same distances.
-int scan_lanes(int d, int qw) {
-  switch (d) {
-#define QK_LANES(D) \
-  case D: return qw == 1 ? bt::tpr_for(D, 1) : qw == 2 ? bt::tpr_for(D, 2) : bt::tpr_for(D, 4);
-    QK_LANES(32) QK_LANES(64) QK_LANES(96) QK_LANES(128) QK_LANES(192) QK_LANES(256) QK_LANES(384)
-    QK_LANES(512) QK_LANES(768) QK_LANES(1024)
-#undef QK_LANES
-    default: return 0;
-  }
 }
 }  // namespace
 
@@ -994,14 +981,13 @@ qk_status qk_aps_batch_autotune(qk_aps_batch* b, const float* q, int64_t nq, flo
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int d = b->ix->cfg.d;
-  const int lanes = scan_lanes(d, b->tiles.queries_per_warp);
   reps = std::max(1, reps);
   std::vector<qk_batch_tiles> cands;
   for (int qw : {1, 2, 4})
     for (int tr : {16, 32, 64})
       for (int ch : {1024, 4096, 16384}) {
         const qk_batch_tiles t{qw, tr, ch};
-        if (aps_tiles_valid(d, t) && scan_lanes(d, qw) == lanes) cands.push_back(t);
+        if (aps_tiles_valid(d, t)) cands.push_back(t);   // every shape gives the same results
       }
   cudaEvent_t e0, e1;
   QK_CUDA(cudaEventCreate(&e0));

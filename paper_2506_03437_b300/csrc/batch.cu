@@ -452,8 +452,8 @@ bool tiles_valid(const qk_batch* b, const qk_batch_tiles& t, std::string* why) {
     *why = "queries_per_warp must be 1, 2 or 4";
     return false;
   }
-  if (t.queries_per_warp == 4 && (d == 768 || d == 1024)) {
-    *why = "queries_per_warp 4 needs d <= 512";
+  if (bt::tpr_for(d, t.queries_per_warp) == 0) {
+    *why = "queries_per_warp " + std::to_string(t.queries_per_warp) + " is not available for d = " + std::to_string(d);
     return false;
   }
   if (t.tile_rows < 1 || (size_t)bt::kStages * t.tile_rows * d * 4 > 200 * 1024) {

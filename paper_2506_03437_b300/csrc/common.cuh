@@ -45,6 +45,13 @@ qk_status cuda_status(cudaError_t e, const char* what);
     if (s__ != QK_OK) return s__;            \
   } while (0)
 
+// Lanes that sum one row in the per-query search kernel (TPR of the launch
+// table in search.cu).  A row's float4 chunk c belongs to lane c % lanes, which
+// keeps two packed FMA chains over its chunks in order; the lanes' sums are
+// added by a butterfly.  The grouped scans sum every row in exactly this
+// order, so a row's distance is bitwise the same whichever kernel scans it.
+constexpr int row_lanes(int d) { return d <= 256 ? 8 : 32; }
+
 // Device-side error codes written to the index's status word.
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_ARG = 2, DEV_BAD_INDEX = 3 };
 

@@ -144,12 +144,15 @@ __device__ __forceinline__ int warp_compact(float* bd, I* bi, int n, int k, int 
   return keep;
 }
 
-// Lanes per row: the smallest power of two t with (D/4) % t == 0 and D/t at
-// most 32 floats (16 when a warp holds four queries) per lane and query.
+// Lanes per row of the grouped scan: the smallest power of two t dividing
+// row_lanes(D) with at most 32 query floats per lane (16 when a warp holds
+// four queries) and at most 8 (query, per-query-kernel lane) chain pairs per
+// lane.  Each lane stands in for row_lanes(D) / t lanes of the per-query
+// kernel, so every shape sums a row in that kernel's order.  0: no such t.
 constexpr int tpr_for(int D, int QW) {
-  const int fmax = QW > 2 ? 16 : 32;
-  for (int t = 1; t <= 32; t <<= 1)
-    if ((D / 4) % t == 0 && D / t <= fmax) return t;
+  const int tp = row_lanes(D), fmax = QW > 2 ? 16 : 32;
+  for (int t = 1; t <= tp; t <<= 1)
+    if (tp % t == 0 && D / t <= fmax && QW * (tp / t) <= 8) return t;
   return 0;
 }
 
@@ -197,7 +200,10 @@ template <int D, int QW>
 __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
   constexpr int TPR = tpr_for(D, QW);
   static_assert(TPR > 0, "unsupported dimension for this query count");
-  constexpr int F4 = D / 4 / TPR;    // float4 chunks per lane, row and query
+  constexpr int TP = row_lanes(D);   // lanes per row of the per-query kernel
+  constexpr int V = TP / TPR;        // of those, the lanes this lane stands in for
+  constexpr int NV = D / 4 / TP;     // float4 chunks of one per-query-kernel lane
+  constexpr int F4 = V * NV;         // float4 chunks per lane, row and query
   constexpr int RS = 32 / TPR;       // rows per warp step
   constexpr int G = kWarps * QW;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -288,9 +294,15 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
       const int slot = qg * QW + j;
       qid[j] = busy && slot < u.nq ? a.qlist[u.qb + slot] : -1;
       qp[j] = a.qpos && qid[j] >= 0 ? a.qpos[u.qb + slot] : 0;
+      // negated: a row element minus the query element is one packed add
       const float4* q4 = reinterpret_cast<const float4*>(a.Q + (qid[j] < 0 ? 0 : qid[j]) * D);
 #pragma unroll
-      for (int f = 0; f < F4; ++f) qv[j][f] = q4[part + TPR * f];
+      for (int i = 0; i < V; ++i)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float4 e = q4[part + TPR * i + TP * v];
+          qv[j][i * NV + v] = make_float4(-e.x, -e.y, -e.z, -e.w);
+        }
       tau[j] = qid[j] < 0 ? -INFINITY : __uint_as_float(a.gtau[qid[j]]);
       cnt[j] = 0;
       any |= qid[j] >= 0;
@@ -323,28 +335,40 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
           const int rr = r0 + rsub;
           const bool rv = rr < rows_t;
           const float4* x4 = reinterpret_cast<const float4*>(tile + (rv ? rr : 0) * D);
-          // two independent FMA chains per query (elements x, z and y, w of each
-          // float4), as packed pairs: one FADD2 and one FFMA2 per two elements
-          float2 ch[QW];
+          // per-query-kernel lane s = part + TPR * i sums chunks s, s + TP, ...
+          // in two packed chains (elements x, y and z, w of each float4), one
+          // such lane after the other
+          float val[QW][V];
 #pragma unroll
-          for (int j = 0; j < QW; ++j) ch[j] = make_float2(0.f, 0.f);
+          for (int i = 0; i < V; ++i) {
+            float2 c01[QW], c23[QW];
 #pragma unroll
-          for (int f = 0; f < F4; ++f) {
-            const float4 x = x4[part + TPR * f];
-            const float2 nxa = make_float2(-x.x, -x.y), nxb = make_float2(-x.z, -x.w);
+            for (int j = 0; j < QW; ++j) c01[j] = c23[j] = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < QW; ++j) {
-              const float2 ea = __fadd2_rn(make_float2(qv[j][f].x, qv[j][f].y), nxa);
-              ch[j] = __ffma2_rn(ea, ea, ch[j]);
-              const float2 eb = __fadd2_rn(make_float2(qv[j][f].z, qv[j][f].w), nxb);
-              ch[j] = __ffma2_rn(eb, eb, ch[j]);
+            for (int v = 0; v < NV; ++v) {
+              const float4 x = x4[part + TPR * i + TP * v];
+#pragma unroll
+              for (int j = 0; j < QW; ++j) {
+                const float4 nq = qv[j][i * NV + v];
+                const float2 d01 = __fadd2_rn(make_float2(x.x, x.y), make_float2(nq.x, nq.y));
+                const float2 d23 = __fadd2_rn(make_float2(x.z, x.w), make_float2(nq.z, nq.w));
+                c01[j] = __ffma2_rn(d01, d01, c01[j]);
+                c23[j] = __ffma2_rn(d23, d23, c23[j]);
+              }
             }
+#pragma unroll
+            for (int j = 0; j < QW; ++j) val[j][i] = (c01[j].x + c01[j].y) + (c23[j].x + c23[j].y);
           }
+          // the per-query kernel's butterfly: its levels TP/2 .. TPR pair
+          // lanes this lane holds, the levels below pair lanes of the row
           float acc[QW];
 #pragma unroll
-          for (int j = 0; j < QW; ++j) acc[j] = ch[j].x + ch[j].y;
-#pragma unroll
           for (int j = 0; j < QW; ++j) {
+#pragma unroll
+            for (int h = V >> 1; h > 0; h >>= 1)
+#pragma unroll
+              for (int i = 0; i < h; ++i) val[j][i] += val[j][i + h];
+            acc[j] = val[j][0];
 #pragma unroll
             for (int o = TPR >> 1; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
           }

@@ -122,6 +122,7 @@ struct ElemFP8 {
 template <int TPR, int NV>
 struct Block {
   static constexpr int D = NV * 4 * TPR;
+  static_assert(TPR == row_lanes(D), "the grouped scans follow this kernel's summation order");
   static constexpr int ROWS = kThreads / TPR;
   static constexpr int TILE = ROWS * D;
   static constexpr int STAGES = stages_for(TILE);

@@ -433,7 +433,7 @@ class ApsBatchPlan:
         L.check(L.lib.qk_aps_batch_set_tiles(self._h, C.byref(t)))
 
     def autotune(self, q, recall_target=0.9, out=None, reps=3, stream=None):
-        """Times the tile shapes that keep the results unchanged on this batch and keeps
+        """Times the valid tile shapes on this batch (all give the same results) and keeps
         the fastest; returns (queries_per_warp, tile_rows, chunk_rows)."""
         q = _as(q, np.float32)
         out = self.outputs(q) if out is None else out

@@ -91,11 +91,34 @@ def test_batched_aps_one_level_matches_oracle_and_per_query_kernel(I, mode):
     orc = aps.search(levels, Q, aps.Params(k=10, recall_target=0.9, f_M=(0.2,), beta_mode=mode))
     compare_search(out[:4] + (out[4], None), orc, 10, label=f"batched APS, one level, {mode} beta")
     assert out[2].max() > 1
-    # the per-query kernel takes the same decisions (distances may differ in the last bit:
-    # the two kernels sum a row's squared differences in different orders)
+    # the grouped scan sums every row in the per-query kernel's order, so the batch takes
+    # the per-query kernel's decisions and returns its distances bit for bit
     pi, pd, pn, pr = ix.search(Q, 10, recall_target=0.9)
-    same = sum(int(pn[j]) == int(out[2][j]) and same_topk(out[0][j], out[1][j], pi[j], pd[j]) for j in range(150))
-    assert same >= 149
+    assert np.array_equal(pn, out[2]) and np.array_equal(pi, out[0])
+    assert np.array_equal(pd.view(np.uint32), out[1].view(np.uint32))
+
+
+@pytest.mark.parametrize("d", [32, 128, 384])
+def test_every_tile_shape_gives_the_per_query_kernels_results(I, d):
+    """Each tile shape splits a row over a different number of lanes (1 to 32 per row, one
+    to eight of the per-query kernel's lanes per lane); all of them must return the per-query
+    kernel's ids, distances and nprobe bit for bit."""
+    import torch
+    X, ids, Q = synth.aps_search(seed=80 + d, n=12_000, d=d, n_comp=30, sigma=1.0, nq=200)
+    levels = kmeans.build_index(X, ids, 80, 0, iters=4, seed=5)
+    ix = make_index(I, X, ids, levels, f_M_leaf=0.2)
+    pi, pd, pn, _ = ix.search(Q, 10, recall_target=0.9)
+    plan = I.ApsBatchPlan(ix, Q.shape[0], 10)
+    Qd = torch.from_numpy(Q).cuda()
+    shapes = [(qw, tr, ch) for qw in (1, 2, 4) for tr, ch in ((16, 1024), (32, 4096))
+              if (qw, d) not in ((4, 192), (4, 256), (4, 768), (4, 1024))]
+    for shape in shapes:
+        plan.set_tiles(*shape)
+        gi, gd, gn = cpu(plan.search(Qd, 0.9))[:3]
+        assert np.array_equal(gn, pn), shape
+        assert np.array_equal(gi, pi), shape
+        assert np.array_equal(gd.view(np.uint32), pd.view(np.uint32)), shape
+    plan.close()
 
 
 def test_batched_aps_many_queries_long_partitions_and_graph(I):
@@ -153,8 +176,8 @@ def test_batched_aps_refuses_bad_queries_and_answers_the_rest(I, two_level):
 
 
 def test_autotune_keeps_results():
-    """qk_aps_batch_autotune times only shapes that keep the grouped scan's arithmetic: the
-    batch after tuning equals the batch before it, bit for bit."""
+    """Every shape qk_aps_batch_autotune times sums a row in the same order: the batch
+    after tuning equals the batch before it, bit for bit."""
     import torch
     from paper_2506_03437_b300 import index as I, synth
     X, ids, Q = synth.aps_search(seed=71, n=60_000, d=128, n_comp=60, sigma=1.2, nq=1500)
