@@ -379,7 +379,9 @@ def run_ours(args):
                        "path": (f"batched APS, {args.rounds} rounds (qk_aps_batch_search)" if plan else
                                 "per-query kernel (qk_search)"),
                        "tiles": ({"queries_per_warp": tiles[0], "tile_rows": tiles[1], "chunk_rows": tiles[2],
-                                  "chosen_by": "flag" if args.tiles else "autotuner (qk_aps_batch_autotune)"} if tiles else None),
+                                  "rows_per_thread": tiles[3] if len(tiles) > 3 else 0,
+                                  "chosen_by": "flag" if args.tiles else "autotuner (qk_aps_batch_autotune)"}
+                                 if tiles else None),
                        "same_as_per_query_kernel": same,
                        "stage_ms": {k_: (round(v_, 4) if isinstance(v_, float) else [round(x, 4) for x in v_])
                                     for k_, v_ in stages.items()},
@@ -721,7 +723,7 @@ def run_batch(args):
                    "n": n, "d": d, "partitions": n_part, "sizes_min_max": [int(sizes.min()), int(sizes.max())],
                    "queries": nq, "nprobe_mean": round(float(nprobe.mean()), 2), "k": k,
                    "tiles": {"queries_per_warp": tiles[0], "tile_rows": tiles[1], "chunk_rows": tiles[2],
-                             "chosen_by": "flag" if args.tiles else "autotuner"},
+                             "rows_per_thread": tiles[3], "chosen_by": "flag" if args.tiles else "autotuner"},
                    "stage_ms": stage_ms, "recall_at_10_vs_fp64": round(rec, 4),
                    "items": int(sum(min(int(x), n_part) for x in nprobe)), "rows_scanned": int(sel_rows),
                    "unique_partition_bytes": int(uniq_bytes),

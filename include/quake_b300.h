@@ -555,6 +555,11 @@ typedef struct {
   int32_t queries_per_warp;  /* 1, 2 or 4 (4 needs d <= 128 or d = 384, 512): G = 8 x this queries per unit */
   int32_t tile_rows;         /* rows per shared-memory tile (3 tiles in flight, <= 200 KB together) */
   int32_t chunk_rows;        /* rows per unit (>= tile_rows, >= 1024) */
+  int32_t rows_per_thread;   /* 0: each row is summed by 1-32 lanes holding the warp's queries in
+                                registers; 2: each thread sums 2 whole rows against its warp's 4
+                                queries, read from shared memory (needs queries_per_warp 4 and
+                                d <= 256; tiles of 64 rows; in the batched APS search it applies to
+                                the rounds after the first).  Both give the same results. */
 } qk_batch_tiles;
 
 /* Creates a plan for the (built or loaded) index.  max_nq >= 1, 1 <= k <= 32,

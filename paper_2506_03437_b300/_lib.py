@@ -62,7 +62,8 @@ class QkMaintAction(C.Structure):
 
 
 class QkBatchTiles(C.Structure):
-    _fields_ = [("queries_per_warp", C.c_int32), ("tile_rows", C.c_int32), ("chunk_rows", C.c_int32)]
+    _fields_ = [("queries_per_warp", C.c_int32), ("tile_rows", C.c_int32), ("chunk_rows", C.c_int32),
+                ("rows_per_thread", C.c_int32)]
 
 
 class QkServerConfig(C.Structure):

@@ -435,6 +435,7 @@ struct qk_aps_batch {
   unsigned long long* work = nullptr;
   unsigned long long* rstats = nullptr;
   int scan_blocks = 0;
+  int rows_blocks = 0;            // CTAs per SM of the whole-rows scan
   qk_batch_tiles scan_tiles{};
   // the scan of a round: 1 on the tensor cores (tc_grouped.cu), 0 on the CUDA cores
   int32_t scan_mode = 0;
@@ -573,8 +574,9 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   QK_CUDA(cudaStreamIsCapturing(s, &cs));
   const bool capturing = cs != cudaStreamCaptureStatusNone;
-  if (capturing && !(b->scan_tiles.queries_per_warp == tl.queries_per_warp && b->scan_tiles.tile_rows == tl.tile_rows))
-    b->scan_blocks = 0;
+  if (capturing && !(b->scan_tiles.queries_per_warp == tl.queries_per_warp && b->scan_tiles.tile_rows == tl.tile_rows &&
+                     b->scan_tiles.rows_per_thread == tl.rows_per_thread))
+    b->scan_blocks = b->rows_blocks = 0;
   Trace tr("aps_batch");
   const bool timing = b->timing && !capturing;
   auto mark = [&](int i) -> qk_status {
@@ -689,6 +691,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     QK_CUDA(cudaMemsetAsync(b->work, 0, sizeof(unsigned long long), s));
     bt::ScanArgs sc;
     sc.vec = ix->vec0;
+    sc.x_rows = ix->cap0;
     sc.ids = ix->ids0;
     sc.off = ix->off0;
     sc.size = ix->size0;
@@ -717,10 +720,12 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
       QK_TRY(tg_scan(q, nq, d, k, ix->vec0, ix->cap0, ix->ids0, sc, b->qpos, b->xn, b->xmax, b->Qg, b->qn,
                      b->qg_cap, b->cpos, b->rstats ? b->rstats + 2 * (ab::kMaxRounds + 1) : nullptr, b->cand_cap,
                      ix->diag, b->n_sm, s));
+    } else if (tl.rows_per_thread == 2 && rd > 0) {   // the first round's partitions hold few queries each
+      QK_TRY(bt::launch_scan_rows(sc, d, b->n_sm, capturing, &b->rows_blocks, s));
     } else {
       QK_TRY(launch_scan_rounds(sc, d, tl.queries_per_warp, b->n_sm, capturing, &b->scan_blocks, s));
-      b->scan_tiles = tl;
     }
+    if (!tensor) b->scan_tiles = tl;
     QK_TRY(mark(4 + 3 * rd));
     // 5. Algorithm 1 over the round, and the next requests
     QK_CUDA(cudaMemsetAsync(b->pcount, 0, sizeof(int32_t) * K, s));
@@ -949,7 +954,9 @@ bool aps_tiles_valid(int d, const qk_batch_tiles& t) {
   return (t.queries_per_warp == 1 || t.queries_per_warp == 2 || t.queries_per_warp == 4) &&
          bt::tpr_for(d, t.queries_per_warp) > 0 && t.tile_rows >= 1 &&
          (size_t)bt::kStages * t.tile_rows * d * 4 <= 200 * 1024 && t.chunk_rows >= t.tile_rows &&
-         t.chunk_rows >= 1024;
+         t.chunk_rows >= 1024 &&
+         (t.rows_per_thread == 0 ||
+          (t.rows_per_thread == 2 && t.queries_per_warp == 4 && bt::rows_layout_ok(d) && t.chunk_rows >= 64));
 }
 }  // namespace
 
@@ -960,7 +967,8 @@ qk_status qk_aps_batch_set_tiles(qk_aps_batch* b, const qk_batch_tiles* t) {
     return QK_ERR_ARG;
   }
   if (!aps_tiles_valid(b->ix->cfg.d, *t)) {
-    set_error("invalid tiles (queries_per_warp 1, 2 or 4; 3 tiles within 200 KB; chunk_rows >= 1024)");
+    set_error("invalid tiles (queries_per_warp 1, 2 or 4; 3 tiles within 200 KB; chunk_rows >= 1024; "
+              "rows_per_thread 0, or 2 with queries_per_warp 4 and d <= 256)");
     return QK_ERR_ARG;
   }
   b->tiles = *t;
@@ -983,12 +991,13 @@ qk_status qk_aps_batch_autotune(qk_aps_batch* b, const float* q, int64_t nq, flo
   const int d = b->ix->cfg.d;
   reps = std::max(1, reps);
   std::vector<qk_batch_tiles> cands;
-  for (int qw : {1, 2, 4})
-    for (int tr : {16, 32, 64})
-      for (int ch : {1024, 4096, 16384}) {
-        const qk_batch_tiles t{qw, tr, ch};
-        if (aps_tiles_valid(d, t)) cands.push_back(t);   // every shape gives the same results
-      }
+  for (int rpt : {0, 2})
+    for (int qw : {1, 2, 4})
+      for (int tr : {16, 32, 64})
+        for (int ch : {1024, 4096, 16384}) {
+          const qk_batch_tiles t{qw, tr, ch, rpt};
+          if (aps_tiles_valid(d, t)) cands.push_back(t);   // every shape gives the same results
+        }
   cudaEvent_t e0, e1;
   QK_CUDA(cudaEventCreate(&e0));
   QK_CUDA(cudaEventCreate(&e1));

@@ -464,6 +464,11 @@ bool tiles_valid(const qk_batch* b, const qk_batch_tiles& t, std::string* why) {
     *why = "chunk_rows must be >= tile_rows and >= 1024";
     return false;
   }
+  if (t.rows_per_thread != 0 &&
+      !(t.rows_per_thread == 2 && t.queries_per_warp == 4 && bt::rows_layout_ok(d))) {
+    *why = "rows_per_thread must be 0, or 2 with queries_per_warp 4 and d <= 256";
+    return false;
+  }
   return true;
 }
 
@@ -517,7 +522,8 @@ qk_status enqueue(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   QK_CUDA(cudaStreamIsCapturing(s, &cs));
   const bool capturing = cs != cudaStreamCaptureStatusNone;
-  if (capturing && !(b->scan_tiles.queries_per_warp == t.queries_per_warp && b->scan_tiles.tile_rows == t.tile_rows))
+  if (capturing && !(b->scan_tiles.queries_per_warp == t.queries_per_warp && b->scan_tiles.tile_rows == t.tile_rows &&
+                     b->scan_tiles.rows_per_thread == t.rows_per_thread))
     b->scan_blocks = 0;
   const bool timing = b->timing && !capturing;
   static const char* const kStage[6] = {"start", "scoring", "selection", "grouping", "scan", "merge"};
@@ -590,6 +596,7 @@ qk_status enqueue(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe
   QK_TRY(mark(3));
   bt::ScanArgs sc;
   sc.vec = ix->vec0;
+  sc.x_rows = ix->cap0;
   sc.ids = ix->ids0;
   sc.off = ix->off0;
   sc.size = ix->size0;
@@ -611,7 +618,10 @@ qk_status enqueue(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe
   sc.ci = b->ci;
   sc.work = b->work;
   sc.status = ix->status;
-  QK_TRY(launch_scan(sc, d, t.queries_per_warp, b->n_sm, capturing, &b->scan_blocks, s));
+  if (t.rows_per_thread == 2)
+    QK_TRY(bt::launch_scan_rows(sc, d, b->n_sm, capturing, &b->scan_blocks, s));
+  else
+    QK_TRY(launch_scan(sc, d, t.queries_per_warp, b->n_sm, capturing, &b->scan_blocks, s));
   b->scan_tiles = t;
   QK_TRY(mark(4));
   bt::merge_kernel<<<(unsigned)((nq + bt::kWarps - 1) / bt::kWarps), bt::kThreads, 0, s>>>(
@@ -873,13 +883,15 @@ qk_status qk_batch_autotune(qk_batch* b, const float* q, int64_t nq, const int32
   QK_TRY(refresh(b, s));
   reps = std::max(1, reps);
   std::vector<qk_batch_tiles> cands;
-  for (int qw : {1, 2, 4})
-    for (int tr : {16, 32, 64})
-      for (int ch : {1024, 4096, 16384}) {
-        qk_batch_tiles t{qw, tr, ch};
-        std::string why;
-        if (tiles_valid(b, t, &why)) cands.push_back(t);
-      }
+  for (int rpt : {0, 2})
+    for (int qw : {1, 2, 4})
+      for (int tr : {16, 32, 64})
+        for (int ch : {1024, 4096, 16384}) {
+          if (rpt == 2 && tr != 64) continue;   // the whole-rows scan has its own 64-row tiles
+          qk_batch_tiles t{qw, tr, ch, rpt};
+          std::string why;
+          if (tiles_valid(b, t, &why)) cands.push_back(t);
+        }
   cudaEvent_t e0, e1;
   QK_CUDA(cudaEventCreate(&e0));
   QK_CUDA(cudaEventCreate(&e1));

@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace qk {
 namespace bt {
@@ -187,6 +188,7 @@ struct ScanArgs {
   int aps = 0;
   const int32_t* qpos = nullptr;     // per query-list entry: the item's position
   int32_t* cpos = nullptr;           // per candidate: that position
+  int64_t x_rows = 0;                // rows of the arena vec points to (whole-rows scan)
 };
 
 struct UnitInfo {
@@ -459,6 +461,333 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
       __syncwarp();
     }
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------ whole rows per thread
+
+// The grouped scan with the contraction tiled in registers: every thread sums
+// two whole rows against the four queries of its warp, so no lane reduction
+// is needed and each shared-memory load feeds four (row loads) or eight
+// (query loads) packed FP32 operations.  The queries of the unit sit in
+// shared memory (read as warp-wide broadcasts).  The rows arrive by TMA tensor
+// copies, one per 32-float column block of a 64-row tile, with the 128-byte
+// swizzle: 16-byte chunk c of row r lands in chunk c ^ (r & 7) of the row's
+// 128-byte line, so the 32 rows a warp reads at once fall on distinct banks.
+// A unit holds G = 32 queries (8 warps x 4); warps without queries sit the
+// unit out.
+//
+// Each row is summed in the per-query kernel's order (row_lanes(D) = 8 lanes
+// with two packed chains each, then its butterfly), evaluated here lane by
+// lane in the order 0, 4, 2, 6, 1, 5, 3, 7 that completes the butterfly's
+// pairs as early as possible, so the distances equal the other kernels' bit
+// for bit.
+template <int D>
+struct RowsLayout {
+  static constexpr int kQ = 4;                 // queries per warp
+  static constexpr int kR = 2;                 // rows per lane
+  static constexpr int kTR = 32 * kR;          // rows per tile: one step of every warp
+  static constexpr int kStg = 2;               // tiles in flight
+  static constexpr int kG = kWarps * kQ;       // queries per unit
+  static constexpr int kBlock = kTR * 128;     // bytes of one 32-float column block of a tile
+  static constexpr int kTile = kBlock * (D / 32);
+  // offsets from the 1024-byte aligned start of the dynamic shared memory
+  static constexpr size_t tiles = 0;
+  static constexpr size_t sq = tiles + (size_t)kStg * kTile;
+  static constexpr size_t bars = sq + sizeof(float) * kG * D;
+  static constexpr size_t qbd = bars + sizeof(uint64_t) * kStg;
+  static constexpr size_t qbr = qbd + sizeof(float) * kG * kBuf;
+  static constexpr size_t unit = qbr + sizeof(int32_t) * kG * kBuf;
+  static constexpr size_t misc = unit + sizeof(UnitInfo);
+  static constexpr size_t total = misc + sizeof(int32_t) * (2 * kStg + 2) + 1024;   // + alignment slack
+};
+
+// Distances of rows lane and lane + 32 of a staged tile to the warp's four
+// (negated) queries in qn.
+template <int D>
+__device__ __forceinline__ void rows_distances(const unsigned char* tile, const float* qn, int lane,
+                                               float (&out)[2][4]) {
+  constexpr int TP = row_lanes(D), NV = D / 4 / TP, D4 = D / 4, BLK = RowsLayout<D>::kBlock;
+  static_assert(TP == 8, "the evaluation order below is that of an 8-lane butterfly");
+  const unsigned char* r0 = tile + lane * 128;
+  const unsigned char* r1 = tile + (lane + 32) * 128;
+  const float4* q4 = reinterpret_cast<const float4*>(qn);
+  float c0[2][4], b1[2][4], pv[2][4];
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const int s = ((kk & 1) << 2) | (kk & 2) | ((kk >> 2) & 1);   // 0, 4, 2, 6, 1, 5, 3, 7
+    const int coff = (s ^ (lane & 7)) << 4;                       // chunk s of rows lane, lane + 32
+    float2 c01[2][4], c23[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) c01[r][j] = c23[r][j] = make_float2(0.f, 0.f);
+#pragma unroll(NV <= 4 ? NV : 2)
+    for (int v = 0; v < NV; ++v) {
+      // float4 s + 8 v of the row: chunk s of column block v
+      const float4 xa = *reinterpret_cast<const float4*>(r0 + v * BLK + coff);
+      const float4 xb = *reinterpret_cast<const float4*>(r1 + v * BLK + coff);
+      const int f = s + TP * v;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 nq = q4[j * D4 + f];
+        const float2 n01 = make_float2(nq.x, nq.y), n23 = make_float2(nq.z, nq.w);
+        const float2 a01 = __fadd2_rn(make_float2(xa.x, xa.y), n01);
+        const float2 a23 = __fadd2_rn(make_float2(xa.z, xa.w), n23);
+        const float2 e01 = __fadd2_rn(make_float2(xb.x, xb.y), n01);
+        const float2 e23 = __fadd2_rn(make_float2(xb.z, xb.w), n23);
+        c01[0][j] = __ffma2_rn(a01, a01, c01[0][j]);
+        c23[0][j] = __ffma2_rn(a23, a23, c23[0][j]);
+        c01[1][j] = __ffma2_rn(e01, e01, c01[1][j]);
+        c23[1][j] = __ffma2_rn(e23, e23, c23[1][j]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float val = (c01[r][j].x + c01[r][j].y) + (c23[r][j].x + c23[r][j].y);
+        // butterfly: ((l0 + l4) + (l2 + l6)) + ((l1 + l5) + (l3 + l7))
+        if (kk == 0 || kk == 2 || kk == 4 || kk == 6) pv[r][j] = val;
+        if (kk == 1) c0[r][j] = pv[r][j] + val;
+        if (kk == 3) c0[r][j] = c0[r][j] + (pv[r][j] + val);
+        if (kk == 5) b1[r][j] = pv[r][j] + val;
+        if (kk == 7) out[r][j] = c0[r][j] + (b1[r][j] + (pv[r][j] + val));
+      }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 2)
+    grouped_scan_rows_kernel(const __grid_constant__ CUtensorMap xmap, ScanArgs a) {
+  using L = RowsLayout<D>;
+  constexpr int Q = L::kQ, TR = L::kTR, NS = L::kStg, G = L::kG;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // the swizzle pattern follows address bits 7-9: tiles start 1024-byte aligned
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* tiles = smem + L::tiles;
+  float* sq = reinterpret_cast<float*>(smem + L::sq);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::bars);
+  float* qbd = reinterpret_cast<float*>(smem + L::qbd);
+  int32_t* qbr = reinterpret_cast<int32_t*>(smem + L::qbr);
+  UnitInfo* su = reinterpret_cast<UnitInfo*>(smem + L::unit);
+  int32_t* s_done = reinterpret_cast<int32_t*>(smem + L::misc);   // per stage: busy warps done with its tile
+  uint32_t* s_fills = reinterpret_cast<uint32_t*>(s_done + NS);    // per stage: fills issued so far
+  uint32_t* s_pending = s_fills + NS;                              // stages with a fill in flight
+  int32_t* s_abort = reinterpret_cast<int32_t*>(s_pending + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      s_done[s] = 0;
+      s_fills[s] = 0;
+    }
+    *s_pending = 0;
+    *s_abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) phase[s] = 0u;
+  const int64_t n_units = *a.n_units;
+
+  for (;;) {
+    if (tid == 0) {
+      UnitInfo u;
+      u.unit = (int64_t)atomicAdd(a.work, 1ull);
+      if (u.unit < n_units) {
+        int lo = 0, hi = a.K;   // rank: the last with ustart[rank] <= unit
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (a.ustart[mid] <= u.unit) lo = mid; else hi = mid;
+        }
+        const int p = a.order[lo];
+        const int64_t local = u.unit - a.ustart[lo];
+        const int32_t sp = a.size[p];
+        const int32_t nch = (sp + a.CH - 1) / a.CH;
+        const int32_t g = (int32_t)(local / nch), c = (int32_t)(local % nch);
+        u.p = p;
+        u.qb = a.pstart[p] + g * G;
+        u.nq = min(G, a.pcount[p] - g * G);
+        u.row0 = c * a.CH;
+        u.rows = min(a.CH, sp - u.row0);
+        u.base = a.off[p] + u.row0;
+        u.nw = (u.nq + Q - 1) / Q;
+        u.rep = 1;
+      }
+      *su = u;
+    }
+    __syncthreads();
+    const UnitInfo& u = *su;   // read in place: stable until the unit's last barrier
+    if (u.unit >= n_units) break;
+    const int ntiles = (u.rows + TR - 1) / TR;
+
+    // Tile t into stage t % NS (one thread): a TMA copy of 64 rows per
+    // 32-float column block.  Rows past the chunk are copied too (rows past
+    // the arena read as zeros) and never scored.
+    auto fill = [&](int t) {
+      const int st = t % NS;
+      mbar_arrive_expect_tx(&full[st], (uint32_t)L::kTile);
+      ++s_fills[st];
+      atomicOr(s_pending, 1u << st);
+      const int y = (int)(u.base + (int64_t)t * TR);
+#pragma unroll
+      for (int b = 0; b < D / 32; ++b)
+        tc::tma_load_2d(smem_u32(tiles + (size_t)st * L::kTile + b * L::kBlock), &xmap, 32 * b, y, &full[st]);
+    };
+    if (tid == 0)
+      for (int t = 0; t < NS && t < ntiles; ++t) fill(t);
+
+    // the unit's queries, negated, into slots warp * Q + j (zeros past nq)
+    for (int i = tid; i < G * (D / 4); i += kThreads) {
+      const int slot = i / (D / 4), f = i % (D / 4);
+      float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (slot < u.nq) e = reinterpret_cast<const float4*>(a.Q + (int64_t)a.qlist[u.qb + slot] * D)[f];
+      reinterpret_cast<float4*>(sq)[i] = make_float4(-e.x, -e.y, -e.z, -e.w);
+    }
+    const bool busy = warp < u.nw;
+    float tau[Q];
+    int cnt[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const int slot = warp * Q + j;
+      const int64_t qi = busy && slot < u.nq ? a.qlist[u.qb + slot] : -1;
+      tau[j] = qi < 0 ? -INFINITY : __uint_as_float(a.gtau[qi]);
+      cnt[j] = 0;
+    }
+    __syncthreads();   // the queries are in place
+
+    const int nbusy = u.nw;
+    for (int t = 0; t < ntiles; ++t) {
+      const int st = t % NS;
+      if (!busy) {
+        phase[st] ^= 1u;
+        continue;
+      }
+      const bool arrived = mbar_wait_bounded(&full[st], phase[st]);
+      phase[st] ^= 1u;
+      if (!__all_sync(0xffffffffu, arrived)) {   // the warp gives up together
+        if (lane == 0) {
+          atomicExch(a.status, DEV_TIMEOUT);
+          atomicExch(s_abort, 1);
+        }
+        break;
+      }
+      if (lane == 0) atomicAnd(s_pending, ~(1u << st));
+      const int rows_t = min(TR, u.rows - t * TR);
+      float dist[2][4];
+      rows_distances<D>(tiles + (size_t)st * L::kTile, sq + warp * Q * D, lane, dist);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        float* bd = qbd + (warp * Q + j) * kBuf;
+        int32_t* br = qbr + (warp * Q + j) * kBuf;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int rr = lane + 32 * r;
+          const bool s = rr < rows_t && dist[r][j] < tau[j];
+          const unsigned m = __ballot_sync(0xffffffffu, s);
+          if (m) {
+            if (s) {
+              const int pos = cnt[j] + __popc(m & ((1u << lane) - 1u));
+              bd[pos] = dist[r][j];
+              br[pos] = u.row0 + t * TR + rr;
+            }
+            cnt[j] += __popc(m);
+            __syncwarp();
+            if (cnt[j] > kBuf - 32) {
+              cnt[j] = warp_compact(bd, br, cnt[j], a.k, lane);
+              if (cnt[j] == a.k) tau[j] = fminf(tau[j], bd[a.k - 1]);
+            }
+          }
+        }
+      }
+      __syncwarp();
+      int last = 0;
+      if (lane == 0) {
+        __threadfence_block();   // this warp's reads of the stage come before its count
+        last = atomicAdd(&s_done[st], 1) == nbusy - 1;
+        if (last) s_done[st] = 0;
+      }
+      if (last && t + NS < ntiles && !*(volatile int32_t*)s_abort) fill(t + NS);   // the stage is free
+    }
+    __syncthreads();   // every warp is done with the unit's tiles
+    if (*s_abort) {
+      // fills still in flight: wait for them (bounded) before the CTA leaves;
+      // the n-th fill of a stage completes the phase of parity (n - 1) & 1
+      if (tid == 0)
+        for (int s2 = 0; s2 < NS; ++s2)
+          if (*s_pending & (1u << s2)) mbar_wait_bounded(&full[s2], (s_fills[s2] - 1u) & 1u);
+      break;
+    }
+    if (busy) {
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        const int slot = warp * Q + j;
+        if (slot >= u.nq) continue;
+        const int64_t qi = a.qlist[u.qb + slot];
+        float* bd = qbd + (warp * Q + j) * kBuf;
+        int32_t* br = qbr + (warp * Q + j) * kBuf;
+        const int n = warp_compact(bd, br, cnt[j], a.k, lane);
+        int64_t at = 0;
+        if (lane == 0) at = a.qcoff[qi] + atomicAdd(&a.qcnt[qi], a.k);
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (lane < a.k) {
+          const int64_t row = a.off[u.p] + br[lane];
+          a.cd[at + lane] = lane < n ? bd[lane] : INFINITY;
+          a.ci[at + lane] = lane < n ? a.ids[row] : -1;
+          if (a.cpos) a.cpos[at + lane] = a.qpos[u.qb + slot];
+        }
+        // L2 distances are >= 0, so their bit patterns order like the values
+        if (lane == 0 && n == a.k && !a.aps) atomicMin(&a.gtau[qi], __float_as_uint(bd[a.k - 1]));
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Launches grouped_scan_rows_kernel with (SMs x CTAs an SM holds) CTAs.  The
+// attribute and occupancy queries run outside stream capture and are cached
+// in *per_sm; a captured launch reuses the cached value.
+template <int D>
+qk_status launch_rows_t(const ScanArgs& a, int n_sm, bool capturing, int* per_sm, cudaStream_t s) {
+  const size_t smem = RowsLayout<D>::total;
+  if (a.x_rows <= 0 || a.x_rows >= (int64_t)1 << 31) {
+    set_error("whole-rows scan: the arena must hold 1 to 2^31 - 1 rows");
+    return QK_ERR_ARG;
+  }
+  CUtensorMap xmap;
+  QK_TRY(make_map(&xmap, a.vec, a.x_rows, D, RowsLayout<D>::kTR));
+  if (!capturing) {
+    QK_CUDA(cudaFuncSetAttribute(grouped_scan_rows_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int n = 0;
+    QK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grouped_scan_rows_kernel<D>, kThreads, smem));
+    *per_sm = n > 0 ? n : 1;
+  } else if (*per_sm < 1) {
+    set_error("capture without a prior run of the same tiles");
+    return QK_ERR_STATE;
+  }
+  grouped_scan_rows_kernel<D><<<n_sm * *per_sm, kThreads, smem, s>>>(xmap, a);
+  QK_CUDA(cudaGetLastError());
+  return QK_OK;
+}
+
+// Whole rows per thread: dimensions with an 8-lane summation order (d <= 256).
+inline bool rows_layout_ok(int d) {
+  return d == 32 || d == 64 || d == 96 || d == 128 || d == 192 || d == 256;
+}
+
+inline qk_status launch_scan_rows(const ScanArgs& a, int d, int n_sm, bool capturing, int* per_sm, cudaStream_t s) {
+  switch (d) {
+    case 32: return launch_rows_t<32>(a, n_sm, capturing, per_sm, s);
+    case 64: return launch_rows_t<64>(a, n_sm, capturing, per_sm, s);
+    case 96: return launch_rows_t<96>(a, n_sm, capturing, per_sm, s);
+    case 128: return launch_rows_t<128>(a, n_sm, capturing, per_sm, s);
+    case 192: return launch_rows_t<192>(a, n_sm, capturing, per_sm, s);
+    case 256: return launch_rows_t<256>(a, n_sm, capturing, per_sm, s);
+    default: set_error("rows_per_thread 2 needs d <= 256"); return QK_ERR_ARG;
   }
 }
 

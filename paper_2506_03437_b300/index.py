@@ -347,7 +347,7 @@ class BatchPlan:
     def tiles(self):
         t = L.QkBatchTiles()
         L.check(L.lib.qk_batch_get_tiles(self._h, C.byref(t)))
-        return (t.queries_per_warp, t.tile_rows, t.chunk_rows)
+        return (t.queries_per_warp, t.tile_rows, t.chunk_rows, t.rows_per_thread)
 
     @tiles.setter
     def tiles(self, v):
@@ -397,7 +397,7 @@ class BatchPlan:
         t = L.QkBatchTiles()
         L.check(L.lib.qk_batch_autotune(self._h, L.ptr(q), int(q.shape[0]), L.ptr(nprobe), L.ptr(out[0]),
                                         L.ptr(out[1]), int(reps), C.byref(t), L.stream_ptr(stream)))
-        return (t.queries_per_warp, t.tile_rows, t.chunk_rows)
+        return (t.queries_per_warp, t.tile_rows, t.chunk_rows, t.rows_per_thread)
 
 
 class ApsBatchPlan:
@@ -428,20 +428,20 @@ class ApsBatchPlan:
         L.check(L.lib.qk_aps_batch_set_rounds(self._h, int(rounds)))
         self.rounds = int(rounds)
 
-    def set_tiles(self, queries_per_warp, tile_rows, chunk_rows):
-        t = L.QkBatchTiles(int(queries_per_warp), int(tile_rows), int(chunk_rows))
+    def set_tiles(self, queries_per_warp, tile_rows, chunk_rows, rows_per_thread=0):
+        t = L.QkBatchTiles(int(queries_per_warp), int(tile_rows), int(chunk_rows), int(rows_per_thread))
         L.check(L.lib.qk_aps_batch_set_tiles(self._h, C.byref(t)))
 
     def autotune(self, q, recall_target=0.9, out=None, reps=3, stream=None):
         """Times the valid tile shapes on this batch (all give the same results) and keeps
-        the fastest; returns (queries_per_warp, tile_rows, chunk_rows)."""
+        the fastest; returns (queries_per_warp, tile_rows, chunk_rows, rows_per_thread)."""
         q = _as(q, np.float32)
         out = self.outputs(q) if out is None else out
         t = L.QkBatchTiles()
         L.check(L.lib.qk_aps_batch_autotune(self._h, L.ptr(q), int(q.shape[0]), float(recall_target),
                                             L.ptr(out[0]), L.ptr(out[1]), int(reps), C.byref(t),
                                             L.stream_ptr(stream)))
-        return (t.queries_per_warp, t.tile_rows, t.chunk_rows)
+        return (t.queries_per_warp, t.tile_rows, t.chunk_rows, t.rows_per_thread)
 
     def set_scan(self, mode):
         """1: the rounds scan on the tensor cores (TF32 + exact re-score); 0: on the CUDA cores."""

@@ -101,8 +101,8 @@ def test_batched_aps_one_level_matches_oracle_and_per_query_kernel(I, mode):
 @pytest.mark.parametrize("d", [32, 128, 384])
 def test_every_tile_shape_gives_the_per_query_kernels_results(I, d):
     """Each tile shape splits a row over a different number of lanes (1 to 32 per row, one
-    to eight of the per-query kernel's lanes per lane); all of them must return the per-query
-    kernel's ids, distances and nprobe bit for bit."""
+    to eight of the per-query kernel's lanes per lane, or whole rows per thread); all of them
+    must return the per-query kernel's ids, distances and nprobe bit for bit."""
     import torch
     X, ids, Q = synth.aps_search(seed=80 + d, n=12_000, d=d, n_comp=30, sigma=1.0, nq=200)
     levels = kmeans.build_index(X, ids, 80, 0, iters=4, seed=5)
@@ -112,6 +112,8 @@ def test_every_tile_shape_gives_the_per_query_kernels_results(I, d):
     Qd = torch.from_numpy(Q).cuda()
     shapes = [(qw, tr, ch) for qw in (1, 2, 4) for tr, ch in ((16, 1024), (32, 4096))
               if (qw, d) not in ((4, 192), (4, 256), (4, 768), (4, 1024))]
+    if d <= 256:   # whole rows per thread in the rounds after the first
+        shapes += [(4, 16, 1024, 2), (4, 32, 4096, 2)]
     for shape in shapes:
         plan.set_tiles(*shape)
         gi, gd, gn = cpu(plan.search(Qd, 0.9))[:3]

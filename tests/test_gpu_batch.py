@@ -67,14 +67,14 @@ def small():
     return zipf_index(seed=51, n=60_000, d=64, n_part=300, hi=5000, nq=400, np_hi=60, n_empty=4)
 
 
-@pytest.mark.parametrize("tiles", [(2, 32, 4096), (1, 16, 1024), (4, 64, 1024), (2, 64, 16384)])
+@pytest.mark.parametrize("tiles", [(2, 32, 4096), (1, 16, 1024), (4, 64, 1024), (2, 64, 16384), (4, 64, 1024, 2)])
 def test_batch_matches_oracle(I, small, tiles):
     import torch
     X, ids, Q, nprobe, levels = small
     ix = make(I, X, levels)
     plan = I.BatchPlan(ix, 512, 10, 64)
     plan.tiles = tiles
-    assert plan.tiles == tiles
+    assert plan.tiles == tuple(tiles) + (0,) * (4 - len(tiles))
     q, npd = torch.from_numpy(Q).cuda(), torch.from_numpy(nprobe).cuda()
     gi, gd = plan.search(q, npd)
     gi2, gd2 = plan.search(q, npd)
@@ -189,6 +189,10 @@ def test_invalid_arguments(I, small):
         plan.tiles = (3, 32, 4096)
     with pytest.raises(L.QkError):
         plan.tiles = (2, 32, 512)
+    with pytest.raises(L.QkError):
+        plan.tiles = (2, 64, 4096, 2)        # whole rows per thread need 4 queries per warp
+    with pytest.raises(L.QkError):
+        plan.tiles = (4, 64, 4096, 1)
     big = torch.from_numpy(np.repeat(Q[:1], 9, axis=0)).cuda()
     with pytest.raises(L.QkError):
         plan.search(big, torch.ones(9, dtype=torch.int32, device="cuda"))   # nq above max_nq
