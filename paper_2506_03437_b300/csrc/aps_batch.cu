@@ -174,35 +174,43 @@ __device__ int warp_next(const double* p, const uint8_t* fl, int M, uint8_t skip
 }
 
 // Merges the round's candidates of the item at position `pos` into R
-// (bd/bi[0, rn), sorted); returns the new size (<= k).
+// (bd/bi[0, rn), sorted); returns the new size (<= k).  The scans write a
+// query's candidates in blocks of k, one per scanned unit, every entry of a
+// block tagged with its item's position, so only the blocks whose first tag
+// matches are read.
 __device__ int take_in(float* bd, int64_t* bi, int rn, int k, const float* cd, const int64_t* ci,
                        const int32_t* cpos, int cn, int pos, int lane) {
   int cnt = rn;
   float kd = rn == k ? bd[k - 1] : INFINITY;
   int64_t kid = rn == k ? bi[k - 1] : INT64_MAX;
-  for (int b = 0; b < cn; b += 32) {
-    const int i = b + lane;
-    bool s = false;
-    float d = 0.f;
-    int64_t id = -1;
-    if (i < cn && cpos[i] == pos) {
-      d = cd[i];
-      id = ci[i];
-      s = id >= 0 && bt::pair_less(d, id, kd, kid);
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, s);
-    if (s) {
-      const int at = cnt + __popc(m & ((1u << lane) - 1u));
-      bd[at] = d;
-      bi[at] = id;
-    }
-    cnt += __popc(m);
-    __syncwarp();
-    if (cnt > 32) {
-      cnt = bt::warp_compact(bd, bi, cnt, k, lane);
-      if (cnt == k) {
-        kd = bd[k - 1];
-        kid = bi[k - 1];
+  const int nb = cn / k;
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    unsigned mb = __ballot_sync(0xffffffffu, b0 + lane < nb && cpos[(b0 + lane) * k] == pos);
+    while (mb) {
+      const int i = (b0 + __ffs(mb) - 1) * k + lane;
+      mb &= mb - 1;
+      bool s = false;
+      float d = 0.f;
+      int64_t id = -1;
+      if (lane < k) {
+        d = cd[i];
+        id = ci[i];
+        s = id >= 0 && bt::pair_less(d, id, kd, kid);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, s);
+      if (s) {
+        const int at = cnt + __popc(m & ((1u << lane) - 1u));
+        bd[at] = d;
+        bi[at] = id;
+      }
+      cnt += __popc(m);
+      __syncwarp();
+      if (cnt > 32) {
+        cnt = bt::warp_compact(bd, bi, cnt, k, lane);
+        if (cnt == k) {
+          kd = bd[k - 1];
+          kid = bi[k - 1];
+        }
       }
     }
   }
@@ -487,6 +495,14 @@ void free_all(qk_aps_batch* b) {
 // tensor scan is full and a share of them would need the exact fallback: the
 // CUDA cores take that round.
 bool tensor_round(const qk_aps_batch* b, int rd) { return b->scan_mode && rd > 0; }
+
+// Rows per unit in round rd.  The first round asks each query's nearest
+// partition only, so its units are few and the largest partitions bound its
+// time; they are cut finer there.
+constexpr int kFirstRoundChunk = 1024;
+int round_chunk(const qk_batch_tiles& t, int rd) {
+  return rd == 0 ? std::min(t.chunk_rows, kFirstRoundChunk) : t.chunk_rows;
+}
 // Entries of the candidate buffer per (query, unit) and queries per unit.
 int slot_size(const qk_aps_batch* b, bool tensor) { return tensor ? tg_slot() : b->k; }
 int unit_queries(const qk_aps_batch* b, bool tensor) {
@@ -502,7 +518,7 @@ qk_status refresh(qk_aps_batch* b, cudaStream_t s) {
   QK_CUDA(cudaStreamSynchronize(s));
   const int32_t K = ix->n_leaf;
   const int32_t mcap = n_candidates(ix->cfg.f_M_leaf, K);
-  const int CH = b->tiles.chunk_rows;
+  const int CH = std::min(round_chunk(b->tiles, 0), round_chunk(b->tiles, 1));   // the finest chunking of a round
   int64_t extra = 0;
   for (int32_t sz : ix->h_size0) extra += std::max<int64_t>(0, ((int64_t)sz + CH - 1) / CH - 1);
   const int64_t need_cand =
@@ -619,7 +635,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   ra.beta_a = ix->beta_a;
   ra.beta_lnB = ix->beta_lnB;
   ra.size = ix->size0;
-  ra.CH = tl.chunk_rows;
+  ra.CH = round_chunk(tl, 0);   // the replay after the prepare step asks for round 0's items
   ra.pcount = b->pcount;
   ra.qslots = b->qslots;
   ra.gtau = b->gtau;
@@ -663,7 +679,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     ga.K = K;
     ga.nq = nq;
     ga.G = unit_queries(b, tensor);
-    ga.CH = tl.chunk_rows;
+    ga.CH = round_chunk(tl, rd);
     ga.k = slot_size(b, tensor);
     ga.size = ix->size0;
     ga.order = b->order;
@@ -697,7 +713,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     sc.size = ix->size0;
     sc.Q = q;
     sc.k = k;
-    sc.CH = tl.chunk_rows;
+    sc.CH = round_chunk(tl, rd);
     sc.TR = tl.tile_rows;
     sc.order = b->order;
     sc.ustart = b->ustart;
@@ -731,6 +747,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     QK_CUDA(cudaMemsetAsync(b->pcount, 0, sizeof(int32_t) * K, s));
     ra.round = rd;
     ra.final_request = rd + 1 == b->rounds - 1;
+    ra.CH = round_chunk(tl, rd + 1);   // its requests are the next round's items
     QK_CUDA(cudaMemsetAsync(b->work + 1, 0, sizeof(unsigned long long), s));
     ab::aps_replay_kernel<<<rgrid, ab::kThreads, 0, s>>>(ra);
     QK_CUDA(cudaGetLastError());
