@@ -652,12 +652,6 @@ qk_status qk_aps_batch_set_rounds(qk_aps_batch* plan, int32_t rounds);
 qk_status qk_aps_batch_autotune(qk_aps_batch* plan, const float* q, int64_t nq, float recall_target,
                                 int64_t* out_ids, float* out_dist, int32_t reps, qk_batch_tiles* chosen,
                                 void* stream);
-/* How a round's items are scanned.  0 (the only mode available) = on the
- * CUDA cores, FP32 direct differences for every row.  1 = on the tensor cores
- * (TF32 MMAs with a margin filter and an exact FP32 re-score) is refused with
- * QK_ERR_UNSUPPORTED: it is held back until a fault seen on a B300 is
- * explained. */
-qk_status qk_aps_batch_set_scan(qk_aps_batch* plan, int32_t mode);
 /* Tiles of the grouped scan (as qk_batch_set_tiles; default 2 queries per
  * warp, tile_rows 8192 / d capped to [8, 64], chunk_rows 4096). */
 qk_status qk_aps_batch_set_tiles(qk_aps_batch* plan, const qk_batch_tiles* tiles);
@@ -681,10 +675,6 @@ qk_status qk_aps_batch_stage_times(qk_aps_batch* plan, float* ms);
  * items Algorithm 1 took in (the rest were scanned beyond a query's stop);
  * arrays of the plan's round count. */
 qk_status qk_aps_batch_round_stats(qk_aps_batch* plan, int64_t* asked, int64_t* taken);
-/* For the last batch on the tensor cores (synchronous): how many (query,
- * partition chunk) lists could not vouch for their top-k and were scanned
- * exactly instead. */
-qk_status qk_aps_batch_fallbacks(qk_aps_batch* plan, int64_t* n);
 
 /* SPANN's early-termination rule, the comparator of Sec. 2 "Early Termination"
  * and Table 6: query i scans the candidates of its set S (the same S as APS

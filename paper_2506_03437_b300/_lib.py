@@ -32,8 +32,7 @@ EXPORTS = [
     "qk_server_submit_insert", "qk_server_submit_delete", "qk_server_results", "qk_server_drain",
     "qk_server_get_stats", "qk_aps_batch_create", "qk_aps_batch_destroy", "qk_aps_batch_set_rounds",
     "qk_aps_batch_set_tiles", "qk_aps_batch_autotune", "qk_aps_batch_search", "qk_aps_batch_capture", "qk_aps_batch_replay",
-    "qk_aps_batch_round_stats", "qk_aps_batch_set_timing", "qk_aps_batch_stage_times", "qk_aps_batch_set_scan",
-    "qk_aps_batch_fallbacks",
+    "qk_aps_batch_round_stats", "qk_aps_batch_set_timing", "qk_aps_batch_stage_times",
 ]
 
 
@@ -153,8 +152,6 @@ def _load():
         "qk_aps_batch_create": (i32, [vp, i64, i32, C.POINTER(vp)]),
         "qk_aps_batch_destroy": (None, [vp]),
         "qk_aps_batch_set_rounds": (i32, [vp, i32]),
-        "qk_aps_batch_set_scan": (i32, [vp, i32]),
-        "qk_aps_batch_fallbacks": (i32, [vp, vp]),
         "qk_aps_batch_set_tiles": (i32, [vp, C.POINTER(QkBatchTiles)]),
         "qk_aps_batch_autotune": (i32, [vp, vp, i64, C.c_float, vp, vp, i32, C.POINTER(QkBatchTiles), vp]),
         "qk_aps_batch_search": (i32, [vp, vp, i64, f32, vp, vp, vp, vp, vp, i32, vp]),

@@ -21,7 +21,7 @@ OBJDIR = os.path.join(HERE, "_build")
 
 SEARCH_DIMS = [32, 64, 96, 128, 192, 256, 384, 512, 768, 1024]
 SOURCES = (["capi.cu", "search.cu", "kmeans.cu", "arena.cu", "update.cu", "maintain.cu", "quant.cu", "tc_score.cu",
-            "noalloc.cu", "batch.cu", "aps_batch.cu", "tc_grouped.cu", "server.cu", "profile.cu", "checkpoint.cu",
+            "noalloc.cu", "batch.cu", "aps_batch.cu", "server.cu", "profile.cu", "checkpoint.cu",
             "views.cu"] + [f"search_d{d}.cu" for d in SEARCH_DIMS])
 HEADERS = ["common.cuh", "capvol.cuh", "index.cuh", "trace.h", "search_impl.cuh", "devmem.h", "grouped.cuh", "tc_common.cuh", "aps_prepare.cuh"]
 

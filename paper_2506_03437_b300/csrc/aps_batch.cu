@@ -7,9 +7,11 @@
 // may move, p may be recomputed, and the stop rule r >= tau_R is checked.  Its
 // choice at every step depends only on the p values and on the results of the
 // partitions already scanned.  So the batch runs in rounds:
-//   prepare  the per-query search kernel scores the top partition and runs
-//            APS on the upper level, then exports each query's leaf
-//            candidates S (nearest first) with their bisector distances t_i;
+//   prepare  one warp per query (aps_prepare.cuh; the per-query kernel's
+//            export mode where the warp's buffers are too small) scores the
+//            top partition and runs APS on the upper level, then exports each
+//            query's leaf candidates S (nearest first) with their bisector
+//            distances t_i;
 //   round    every unfinished query has asked for a few of its candidates;
 //            the (query, partition) items are grouped by partition and one
 //            persistent grouped scan computes, for every item, its own exact
@@ -44,16 +46,6 @@
 #include "trace.h"
 
 namespace qk {
-
-// tc_grouped.cu: the round's scan on the tensor cores
-int tg_slot();
-int tg_max_k();
-qk_status tg_prepare_norms(const float* X, int d, const int64_t* off, const int32_t* size, int K, float* xn,
-                           uint32_t* scratch, float* xmax, cudaStream_t s);
-qk_status tg_scan(const float* Q, int64_t nq, int d, int k, const float* X, int64_t x_rows, const int64_t* ids,
-                  const bt::ScanArgs& sc, const int32_t* qpos, const float* xn, float xmax, float* Qg, float* qn,
-                  int64_t qg_cap, int32_t* cpos, unsigned long long* fallbacks, int64_t cand_cap, int64_t* diag,
-                  int n_sm, cudaStream_t s);
 
 namespace ab {
 
@@ -445,15 +437,6 @@ struct qk_aps_batch {
   int scan_blocks = 0;
   int rows_blocks = 0;            // CTAs per SM of the whole-rows scan
   qk_batch_tiles scan_tiles{};
-  // the scan of a round: 1 on the tensor cores (tc_grouped.cu), 0 on the CUDA cores
-  int32_t scan_mode = 0;
-  float* xn = nullptr;            // squared norms of the arena rows (tensor scan)
-  int64_t xn_cap = 0;
-  uint32_t* xmax2 = nullptr;
-  float xmax = 0.f;
-  float* Qg = nullptr;            // the round's queries in list order (tensor scan)
-  float* qn = nullptr;
-  int64_t qg_cap = 0;
   cudaGraphExec_t graph = nullptr;
   uint64_t graph_version = 0;
   int64_t graph_nq = 0;
@@ -487,14 +470,7 @@ void free_all(qk_aps_batch* b) {
   afree(b->pcount), afree(b->pcur), afree(b->pstart), afree(b->qlist), afree(b->qpos), afree(b->order);
   afree(b->qcnt), afree(b->cpos), afree(b->ustart), afree(b->tmp), afree(b->tmp2), afree(b->n_units);
   afree(b->qslots), afree(b->qcoff), afree(b->ci), afree(b->gtau), afree(b->cd), afree(b->work), afree(b->rstats);
-  afree(b->xn), afree(b->xmax2), afree(b->Qg), afree(b->qn);
 }
-
-// Whether round rd scans on the tensor cores.  The first round asks every
-// query for its nearest partitions with no bound yet, so every list of the
-// tensor scan is full and a share of them would need the exact fallback: the
-// CUDA cores take that round.
-bool tensor_round(const qk_aps_batch* b, int rd) { return b->scan_mode && rd > 0; }
 
 // Rows per unit in round rd.  The first round asks each query's nearest
 // partition only, so its units are few and the largest partitions bound its
@@ -502,11 +478,6 @@ bool tensor_round(const qk_aps_batch* b, int rd) { return b->scan_mode && rd > 0
 constexpr int kFirstRoundChunk = 1024;
 int round_chunk(const qk_batch_tiles& t, int rd) {
   return rd == 0 ? std::min(t.chunk_rows, kFirstRoundChunk) : t.chunk_rows;
-}
-// Entries of the candidate buffer per (query, unit) and queries per unit.
-int slot_size(const qk_aps_batch* b, bool tensor) { return tensor ? tg_slot() : b->k; }
-int unit_queries(const qk_aps_batch* b, bool tensor) {
-  return tensor ? 128 : bt::kWarps * b->tiles.queries_per_warp;
 }
 
 // Re-reads the index's shape and partition sizes; re-sizes the workspace
@@ -522,7 +493,7 @@ qk_status refresh(qk_aps_batch* b, cudaStream_t s) {
   int64_t extra = 0;
   for (int32_t sz : ix->h_size0) extra += std::max<int64_t>(0, ((int64_t)sz + CH - 1) / CH - 1);
   const int64_t need_cand =
-      (int64_t)std::max(slot_size(b, b->scan_mode != 0), slot_size(b, false)) * b->max_nq * ((int64_t)mcap + extra);
+      (int64_t)b->k * b->max_nq * ((int64_t)mcap + extra);
   const size_t nq = (size_t)b->max_nq;
   if (mcap != b->mcap) {
     ab::State& st = b->st;
@@ -551,21 +522,6 @@ qk_status refresh(qk_aps_batch* b, cudaStream_t s) {
     QK_TRY(aalloc(&b->ci, (size_t)cap));
     QK_TRY(aalloc(&b->cpos, (size_t)cap));
     b->cand_cap = cap;
-  }
-  if (b->scan_mode) {
-    // the queries of a round in list order, and the norms of the arena's live rows
-    const int64_t qg = b->max_nq * (int64_t)mcap;
-    if (qg > b->qg_cap) {
-      QK_TRY(aalloc(&b->Qg, (size_t)qg * ix->cfg.d));
-      QK_TRY(aalloc(&b->qn, (size_t)qg));
-      b->qg_cap = qg;
-    }
-    if (ix->cap0 > b->xn_cap) {
-      QK_TRY(aalloc(&b->xn, (size_t)ix->cap0));
-      b->xn_cap = ix->cap0;
-    }
-    if (!b->xmax2) QK_TRY(aalloc(&b->xmax2, 1));
-    QK_TRY(tg_prepare_norms(ix->vec0, ix->cfg.d, ix->off0, ix->size0, K, b->xn, b->xmax2, &b->xmax, s));
   }
   std::vector<int32_t> order(K);
   std::iota(order.begin(), order.end(), 0);
@@ -621,7 +577,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     QK_TRY(launch_search(sa, s));
   tr.mark("prepare");
   QK_TRY(mark(1));
-  if (b->rstats) QK_CUDA(cudaMemsetAsync(b->rstats, 0, sizeof(unsigned long long) * (2 * (ab::kMaxRounds + 1) + 1), s));
+  if (b->rstats) QK_CUDA(cudaMemsetAsync(b->rstats, 0, sizeof(unsigned long long) * 2 * (ab::kMaxRounds + 1), s));
   // 2. the first requests
   ab::ReplayArgs ra;
   ra.st = b->st;
@@ -673,14 +629,13 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   QK_TRY(mark(2));
   ra.first = 0;
   for (int rd = 0; rd < b->rounds; ++rd) {
-    const bool tensor = tensor_round(b, rd);
     // 3. group the round's items by partition
     bt::GroupArgs ga;
     ga.K = K;
     ga.nq = nq;
-    ga.G = unit_queries(b, tensor);
+    ga.G = bt::kWarps * tl.queries_per_warp;
     ga.CH = round_chunk(tl, rd);
-    ga.k = slot_size(b, tensor);
+    ga.k = k;
     ga.size = ix->size0;
     ga.order = b->order;
     ga.pcount = b->pcount;
@@ -732,16 +687,12 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     sc.aps = 1;
     sc.qpos = b->qpos;
     sc.cpos = b->cpos;
-    if (tensor) {
-      QK_TRY(tg_scan(q, nq, d, k, ix->vec0, ix->cap0, ix->ids0, sc, b->qpos, b->xn, b->xmax, b->Qg, b->qn,
-                     b->qg_cap, b->cpos, b->rstats ? b->rstats + 2 * (ab::kMaxRounds + 1) : nullptr, b->cand_cap,
-                     ix->diag, b->n_sm, s));
-    } else if (tl.rows_per_thread == 2 && rd > 0) {   // the first round's partitions hold few queries each
+    if (tl.rows_per_thread == 2 && rd > 0) {   // the first round's partitions hold few queries each
       QK_TRY(bt::launch_scan_rows(sc, d, b->n_sm, capturing, &b->rows_blocks, s));
     } else {
       QK_TRY(launch_scan_rounds(sc, d, tl.queries_per_warp, b->n_sm, capturing, &b->scan_blocks, s));
     }
-    if (!tensor) b->scan_tiles = tl;
+    b->scan_tiles = tl;
     QK_TRY(mark(4 + 3 * rd));
     // 5. Algorithm 1 over the round, and the next requests
     QK_CUDA(cudaMemsetAsync(b->pcount, 0, sizeof(int32_t) * K, s));
@@ -890,7 +841,6 @@ qk_status qk_aps_batch_create(qk_index* ix, int64_t max_nq, int32_t k, qk_aps_ba
   b->tiles.queries_per_warp = 2;
   b->tiles.tile_rows = std::max(8, std::min(64, 8192 / ix->cfg.d));
   b->tiles.chunk_rows = 4096;
-  b->scan_mode = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -915,7 +865,7 @@ qk_status qk_aps_batch_create(qk_index* ix, int64_t max_nq, int32_t k, qk_aps_ba
   run(aalloc(&b->qcnt, nq));
   run(aalloc(&b->gtau, nq));
   run(aalloc(&b->work, 2));   // [0] the grouped scan's units, [1] the replay's queries
-  run(aalloc(&b->rstats, 2 * (ab::kMaxRounds + 1) + 1));   // per round asked / taken, then the exact fallbacks
+  run(aalloc(&b->rstats, 2 * (ab::kMaxRounds + 1)));   // per round: items asked for, items taken in
   if (st == QK_OK) st = refresh(b, 0);
   if (st != QK_OK) {
     free_all(b);
@@ -943,25 +893,6 @@ qk_status qk_aps_batch_set_rounds(qk_aps_batch* b, int32_t rounds) {
     return QK_ERR_ARG;
   }
   b->rounds = rounds;
-  return QK_OK;
-  QK_GUARD_END
-}
-
-qk_status qk_aps_batch_set_scan(qk_aps_batch* b, int32_t mode) {
-  QK_GUARD_BEGIN
-  if (!b || (mode != 0 && mode != 1)) {
-    set_error("scan mode is 0 (CUDA cores) or 1 (tensor cores)");
-    return QK_ERR_ARG;
-  }
-  if (mode == 1) {
-    // The tensor-core scan of the rounds (tc_grouped.cu) faulted on a B300 in
-    // two of four runs with no bounds check firing; until the cause is known
-    // it is not run.
-    set_error("the tensor-core scan of the batched search is not available");
-    return QK_ERR_UNSUPPORTED;
-  }
-  b->scan_mode = mode;
-  b->version = ~0ull;   // the candidate buffer and the norms depend on the mode
   return QK_OK;
   QK_GUARD_END
 }
@@ -1188,19 +1119,6 @@ qk_status qk_aps_batch_stage_times(qk_aps_batch* b, float* ms) {
     ms[3] += sc;
     ms[4 + r] = sc;
   }
-  return QK_OK;
-  QK_GUARD_END
-}
-
-qk_status qk_aps_batch_fallbacks(qk_aps_batch* b, int64_t* n) {
-  QK_GUARD_BEGIN
-  if (!b || !n) {
-    set_error("null argument");
-    return QK_ERR_ARG;
-  }
-  unsigned long long h = 0;
-  QK_CUDA(cudaMemcpy(&h, b->rstats + 2 * (ab::kMaxRounds + 1), sizeof(h), cudaMemcpyDeviceToHost));
-  *n = (int64_t)h;
   return QK_OK;
   QK_GUARD_END
 }

@@ -1,8 +1,9 @@
 // Building blocks of the tensor-core kernels (tcgen05 + TMEM, TMA): tile
 // constants, the instruction and shared-memory descriptors of K-major TF32
 // operands with the 128-byte swizzle, thin wrappers of the PTX instructions,
-// and the host-side tensor-map encoding.  Shared by tc_score.cu (centroid
-// scoring) and tc_grouped.cu (the grouped partition scan).
+// and the host-side tensor-map encoding.  Used by tc_score.cu (centroid
+// scoring); the grouped scan's whole-rows layout (grouped.cuh) takes its TMA
+// tile copy and tensor maps.
 #pragma once
 
 #include <cuda.h>

@@ -443,10 +443,6 @@ class ApsBatchPlan:
                                             L.stream_ptr(stream)))
         return (t.queries_per_warp, t.tile_rows, t.chunk_rows, t.rows_per_thread)
 
-    def set_scan(self, mode):
-        """1: the rounds scan on the tensor cores (TF32 + exact re-score); 0: on the CUDA cores."""
-        L.check(L.lib.qk_aps_batch_set_scan(self._h, int(mode)))
-
     def outputs(self, q, cap0=0):
         """(ids, dist, nprobe, recall_estimate[, scanned0]) CUDA tensors for q's batch."""
         import torch
@@ -490,12 +486,6 @@ class ApsBatchPlan:
         L.check(L.lib.qk_aps_batch_stage_times(self._h, L.ptr(ms)))
         return {"prepare": float(ms[0]), "replay": float(ms[1]), "grouping": float(ms[2]),
                 "scan": float(ms[3]), "scan_per_round": ms[4:].tolist()}
-
-    def fallbacks(self):
-        """(query, partition chunk) lists of the last tensor-core batch scanned exactly instead."""
-        n = np.zeros(1, np.int64)
-        L.check(L.lib.qk_aps_batch_fallbacks(self._h, L.ptr(n)))
-        return int(n[0])
 
     def round_stats(self):
         """Per round of the last batch: (items asked for, items Algorithm 1 took in)."""
