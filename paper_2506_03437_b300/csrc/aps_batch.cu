@@ -110,7 +110,13 @@ struct ReplayArgs {
   int32_t* status = nullptr;
   int64_t* diag = nullptr;
   unsigned long long* next_q = nullptr;   // the next query a warp takes (zeroed per launch)
+  int staged = 0;                         // the walk's state in shared memory (stage_bytes(mcap) per warp)
 };
+
+// Shared memory of one warp's staged walk state: t_i and p_i (FP64) and the
+// flags of mcap candidates, 16-byte aligned.
+__host__ __device__ inline size_t stage_bytes(int mcap) { return ((size_t)mcap * 17 + 15) & ~size_t(15); }
+constexpr int kStageMaxCap = 384;   // larger candidate sets walk in global memory
 
 // p from Eq. 8-9 with the raw caps for p_0 (as the per-query kernel computes
 // it, lane by lane in the same order), then r = p_0 + sum of the scanned p_i.
@@ -211,7 +217,11 @@ __device__ int take_in(float* bd, int64_t* bi, int rn, int k, const float* cd, c
 
 // Algorithm 1 of query q over the round just scanned, and its next requests
 // (one warp; bd / bi its 64-entry buffer in shared memory).
-__device__ void replay_query(const ReplayArgs& a, const int64_t q, float* bd, int64_t* bi, const int lane) {
+// With `stage`, the query's t_i, p_i and flags are worked on in shared memory
+// (stage: mcap doubles, mcap doubles, mcap bytes) and p and the flags written
+// back at the end; the walk reads them once per step.
+__device__ void replay_query(const ReplayArgs& a, const int64_t q, float* bd, int64_t* bi, const int lane,
+                             unsigned char* stage) {
   const State& S = a.st;
   const int M = S.M[q];
   const int k = a.k;
@@ -228,6 +238,22 @@ __device__ void replay_query(const ReplayArgs& a, const int64_t q, float* bd, in
   const double* t = S.t + q * a.mcap;
   double* p = S.p + q * a.mcap;
   uint8_t* fl = S.flag + q * a.mcap;
+  double* gp = p;
+  uint8_t* gfl = fl;
+  if (stage) {
+    double* st = reinterpret_cast<double*>(stage);
+    double* sp = st + a.mcap;
+    uint8_t* sf = reinterpret_cast<uint8_t*>(sp + a.mcap);
+    for (int i = lane; i < M; i += 32) {
+      st[i] = t[i];
+      sp[i] = p[i];
+      sf[i] = a.first ? 0 : fl[i];
+    }
+    t = st;
+    p = sp;
+    fl = sf;
+    __syncwarp();
+  }
   int rn = 0, ns = 0;
   double rho = 0.0, r = 0.0;
   if (a.first) {
@@ -357,6 +383,13 @@ __device__ void replay_query(const ReplayArgs& a, const int64_t q, float* bd, in
     slots += (a.size[part] + a.CH - 1) / a.CH;
   }
   for (int o = 16; o > 0; o >>= 1) slots += __shfl_xor_sync(0xffffffffu, slots, o);
+  if (stage) {   // the next replay of this query reads them from global memory
+    __syncwarp();
+    for (int i = lane; i < M; i += 32) {
+      gp[i] = p[i];
+      gfl[i] = fl[i];
+    }
+  }
   if (lane < rn) {
     S.Rd[q * k + lane] = bd[lane];
     S.Ri[q * k + lane] = bi[lane];
@@ -382,13 +415,15 @@ __device__ void replay_query(const ReplayArgs& a, const int64_t q, float* bd, in
 __global__ void __launch_bounds__(kThreads) aps_replay_kernel(ReplayArgs a) {
   __shared__ float s_bd[kWarps][64];
   __shared__ int64_t s_bi[kWarps][64];
+  extern __shared__ __align__(16) unsigned char s_stage[];   // per warp: stage_bytes(mcap), when staged
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* stage = a.staged ? s_stage + (size_t)warp * stage_bytes(a.mcap) : nullptr;
   for (;;) {
     unsigned long long q = 0;
     if (lane == 0) q = atomicAdd(a.next_q, 1ull);
     q = __shfl_sync(0xffffffffu, q, 0);
     if (q >= (unsigned long long)a.nq) break;
-    replay_query(a, (int64_t)q, s_bd[warp], s_bi[warp], lane);
+    replay_query(a, (int64_t)q, s_bd[warp], s_bi[warp], lane, stage);
     __syncwarp();
   }
 }
@@ -611,8 +646,12 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   ra.qcoff = b->qcoff;
   ra.qcnt = b->qcnt;
   // the replay is persistent: as many blocks as the SMs hold at once, at most one per kWarps queries
+  ra.staged = mcap <= ab::kStageMaxCap;
+  const size_t rsmem = ra.staged ? ab::kWarps * ab::stage_bytes(mcap) : 0;
+  if (rsmem > 48 * 1024 && !capturing)
+    QK_CUDA(cudaFuncSetAttribute(ab::aps_replay_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem));
   int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ab::aps_replay_kernel, ab::kThreads, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ab::aps_replay_kernel, ab::kThreads, rsmem) != cudaSuccess) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -624,7 +663,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
   ra.round = -1;
   ra.final_request = b->rounds == 1;
   QK_CUDA(cudaMemsetAsync(b->work + 1, 0, sizeof(unsigned long long), s));
-  ab::aps_replay_kernel<<<rgrid, ab::kThreads, 0, s>>>(ra);
+  ab::aps_replay_kernel<<<rgrid, ab::kThreads, rsmem, s>>>(ra);
   QK_CUDA(cudaGetLastError());
   QK_TRY(mark(2));
   ra.first = 0;
@@ -700,7 +739,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     ra.final_request = rd + 1 == b->rounds - 1;
     ra.CH = round_chunk(tl, rd + 1);   // its requests are the next round's items
     QK_CUDA(cudaMemsetAsync(b->work + 1, 0, sizeof(unsigned long long), s));
-    ab::aps_replay_kernel<<<rgrid, ab::kThreads, 0, s>>>(ra);
+    ab::aps_replay_kernel<<<rgrid, ab::kThreads, rsmem, s>>>(ra);
     QK_CUDA(cudaGetLastError());
     QK_TRY(mark(5 + 3 * rd));
   }

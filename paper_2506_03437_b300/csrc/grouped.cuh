@@ -795,24 +795,32 @@ inline qk_status launch_scan_rows(const ScanArgs& a, int d, int n_sm, bool captu
 
 // Exclusive scan of n int64 values by one CTA; the total goes to *total.
 static __device__ void block_scan(const int64_t* in, int64_t* out, int n, int64_t* total, int64_t* s_part) {
-  const int tid = threadIdx.x, T = blockDim.x;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = (T + 31) >> 5;
   const int per = (n + T - 1) / T;
   const int b = tid * per, e = min(n, b + per);
   int64_t sum = 0;
   for (int i = b; i < e; ++i) sum += in[i];
-  s_part[tid] = sum;
+  // the threads' sums scanned by warp shuffles, then the warps' totals by warp 0
+  int64_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_part[warp] = x;
   __syncthreads();
-  if (tid == 0) {
-    int64_t run = 0;
-    for (int i = 0; i < T; ++i) {
-      const int64_t v = s_part[i];
-      s_part[i] = run;
-      run += v;
+  if (warp == 0) {
+    int64_t v = lane < nw ? s_part[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
     }
-    *total = run;
+    if (lane < nw) s_part[lane] = v;   // inclusive totals of warps 0..lane
+    if (lane == nw - 1) *total = v;
   }
   __syncthreads();
-  int64_t run = s_part[tid];
+  int64_t run = x - sum + (warp > 0 ? s_part[warp - 1] : 0);
   for (int i = b; i < e; ++i) {
     const int64_t v = in[i];
     out[i] = run;
