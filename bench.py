@@ -332,6 +332,12 @@ def run_ours(args):
         dist.barrier()
     h0 = ix.hits(0)
     h1 = ix.hits(1)
+    pairs_first = None
+    if plan:   # (evaluation only, after the hit counts are read) the first round's pairs
+        s0 = plan.search(Qd, tau, cap0=1, stream=stream)[4]
+        torch.cuda.synchronize()
+        first = s0[:, 0].cpu().numpy()
+        pairs_first = int(sizes0[first[first >= 0]].sum())
     eb = {"f32": 4, "bf16": 2, "fp8": 1}[args.storage]
     bytes_unique, bytes_items = algorithmic_bytes(h0, h1, sizes0, sizes1, eb, args.steps, 0)
     avg_step_s = dev_s / args.steps
@@ -386,6 +392,7 @@ def run_ours(args):
                        "stage_ms": {k_: (round(v_, 4) if isinstance(v_, float) else [round(x, 4) for x in v_])
                                     for k_, v_ in stages.items()},
                        "items_asked_per_round": a_items.tolist(), "items_taken_per_round": t_items.tolist(),
+                       "pairs_first_round": pairs_first,
                        "mean_nprobe": round(mean_nprobe, 2), "f_M": [F_M_LEAF, F_M_PARENT],
                        "tau_rho": 0.01, "upper_recall": 0.99, "beta": "table", "build_s": round(build_s, 2),
                        "storage": args.storage, "rerank": args.rerank if args.storage != "f32" else None,
