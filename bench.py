@@ -68,11 +68,12 @@ TRAFFIC_BYTES = 120.52e9 + 0.411e9
 TRAFFIC_KERNEL_HASH = "bfca0f4e553054f7"
 KERNEL_SOURCES = ["search_impl.cuh", "common.cuh", "capvol.cuh", "index.cuh"]
 # DRAM traffic of the grouped scans of one batched APS step on the full workload
-# (its four launches, one per round, summed), from the single-pass ncu capture
-# summarised in profiles/aps_batch_launches_1Mx128.md; it belongs to these
-# sources with this hash.
-SCAN_TRAFFIC_BYTES = (461.61 + 5.95 + 530.17 + 33.22 + 0.142 + 0.142) * 1e6
-SCAN_TRAFFIC_HASH = "564a749f5048bd10"
+# (its four launches, one per round, summed: the lane-split layout in round 1,
+# whole rows after it), from the single-pass ncu capture summarised in
+# profiles/aps_batch_launches_1Mx128.md, with tiles (4, 32, 4096, 2) as the
+# autotuner picks them; it belongs to these sources with this hash.
+SCAN_TRAFFIC_BYTES = (458.28 + 9.26 + 547.06 + 33.83 + 0.219 + 0.217) * 1e6
+SCAN_TRAFFIC_HASH = "62795b5052439e5b"
 SCAN_SOURCES = ["grouped.cuh", "common.cuh", "index.cuh", "aps_batch.cu"]
 
 
@@ -463,7 +464,8 @@ def scan_roofline(pairs, scan_s, peak_ops, bytes_unique, bytes_items, step_s, hb
         extra = {"dram_gbs": round(traffic / scan_s / 1e9, 1), "dram_frac": round(traffic / scan_s / 1e9 / hbm_peak, 4),
                  "reread_factor": round(traffic / bytes_unique, 2),
                  "traffic_note": "ncu DRAM read + write bytes of the step's grouped-scan launches, summed"}
-    return {"bound": "alu", "kernel": "grouped_scan_kernel", "achieved": round(achieved, 2),
+    return {"bound": "alu", "kernel": "grouped_scan_rows_kernel + grouped_scan_kernel (the step's scans)",
+            "achieved": round(achieved, 2),
             "peak": round(peak_ops, 2), "unit": "Tops/s", "frac": round(achieved / peak_ops, 4),
             "traffic": traffic, **extra, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x max SM clock",
             "scan_ms_per_step": round(1e3 * scan_s, 4), "pairs_per_step": round(pairs),
