@@ -212,6 +212,7 @@ __device__ int take_in(float* bd, int64_t* bi, int rn, int k, const float* cd, c
       }
     }
   }
+  if (cnt == rn) return rn;   // nothing entered: R is sorted and within k already
   return bt::warp_compact(bd, bi, cnt, k, lane);
 }
 
