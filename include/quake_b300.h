@@ -557,9 +557,10 @@ typedef struct {
   int32_t chunk_rows;        /* rows per unit (>= tile_rows, >= 1024) */
   int32_t rows_per_thread;   /* 0: each row is summed by 1-32 lanes holding the warp's queries in
                                 registers; 2: each thread sums 2 whole rows against its warp's 4
-                                queries, read from shared memory (needs queries_per_warp 4 and
-                                d <= 256; tiles of 64 rows; in the batched APS search it applies to
-                                the rounds after the first).  Both give the same results. */
+                                queries, read from shared memory (d <= 256; units of 32 queries and
+                                tiles of 64 rows whatever queries_per_warp and tile_rows say; in the
+                                batched APS search it applies to the rounds after the first, which
+                                keeps the other fields).  Both give the same results. */
 } qk_batch_tiles;
 
 /* Creates a plan for the (built or loaded) index.  max_nq >= 1, 1 <= k <= 32,

@@ -673,7 +673,8 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     bt::GroupArgs ga;
     ga.K = K;
     ga.nq = nq;
-    ga.G = bt::kWarps * tl.queries_per_warp;
+    const bool rows_round = tl.rows_per_thread == 2 && rd > 0;   // the first round's partitions hold few queries
+    ga.G = rows_round ? bt::kRowsG : bt::kWarps * tl.queries_per_warp;
     ga.CH = round_chunk(tl, rd);
     ga.k = k;
     ga.size = ix->size0;
@@ -727,7 +728,7 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     sc.aps = 1;
     sc.qpos = b->qpos;
     sc.cpos = b->cpos;
-    if (tl.rows_per_thread == 2 && rd > 0) {   // the first round's partitions hold few queries each
+    if (rows_round) {
       QK_TRY(bt::launch_scan_rows(sc, d, b->n_sm, capturing, &b->rows_blocks, s));
     } else {
       QK_TRY(launch_scan_rounds(sc, d, tl.queries_per_warp, b->n_sm, capturing, &b->scan_blocks, s));
@@ -944,7 +945,7 @@ bool aps_tiles_valid(int d, const qk_batch_tiles& t) {
          (size_t)bt::kStages * t.tile_rows * d * 4 <= 200 * 1024 && t.chunk_rows >= t.tile_rows &&
          t.chunk_rows >= 1024 &&
          (t.rows_per_thread == 0 ||
-          (t.rows_per_thread == 2 && t.queries_per_warp == 4 && bt::rows_layout_ok(d) && t.chunk_rows >= 64));
+          (t.rows_per_thread == 2 && bt::rows_layout_ok(d)));
 }
 }  // namespace
 
@@ -956,7 +957,7 @@ qk_status qk_aps_batch_set_tiles(qk_aps_batch* b, const qk_batch_tiles* t) {
   }
   if (!aps_tiles_valid(b->ix->cfg.d, *t)) {
     set_error("invalid tiles (queries_per_warp 1, 2 or 4; 3 tiles within 200 KB; chunk_rows >= 1024; "
-              "rows_per_thread 0, or 2 with queries_per_warp 4 and d <= 256)");
+              "rows_per_thread 0, or 2 with d <= 256)");
     return QK_ERR_ARG;
   }
   b->tiles = *t;

@@ -465,8 +465,8 @@ bool tiles_valid(const qk_batch* b, const qk_batch_tiles& t, std::string* why) {
     return false;
   }
   if (t.rows_per_thread != 0 &&
-      !(t.rows_per_thread == 2 && t.queries_per_warp == 4 && bt::rows_layout_ok(d))) {
-    *why = "rows_per_thread must be 0, or 2 with queries_per_warp 4 and d <= 256";
+      !(t.rows_per_thread == 2 && bt::rows_layout_ok(d))) {
+    *why = "rows_per_thread must be 0, or 2 with d <= 256";
     return false;
   }
   return true;
@@ -518,7 +518,7 @@ qk_status enqueue(qk_batch* b, const float* q, int64_t nq, const int32_t* nprobe
   qk_index* ix = b->ix;
   const int d = ix->cfg.d, K = b->K;
   const qk_batch_tiles& t = b->tiles;
-  const int G = bt::kWarps * t.queries_per_warp;
+  const int G = t.rows_per_thread == 2 ? bt::kRowsG : bt::kWarps * t.queries_per_warp;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   QK_CUDA(cudaStreamIsCapturing(s, &cs));
   const bool capturing = cs != cudaStreamCaptureStatusNone;
@@ -887,7 +887,7 @@ qk_status qk_batch_autotune(qk_batch* b, const float* q, int64_t nq, const int32
     for (int qw : {1, 2, 4})
       for (int tr : {16, 32, 64})
         for (int ch : {1024, 4096, 16384}) {
-          if (rpt == 2 && tr != 64) continue;   // the whole-rows scan has its own 64-row tiles
+          if (rpt == 2 && (tr != 64 || qw != 2)) continue;   // the whole-rows scan has its own tiles and units
           qk_batch_tiles t{qw, tr, ch, rpt};
           std::string why;
           if (tiles_valid(b, t, &why)) cands.push_back(t);

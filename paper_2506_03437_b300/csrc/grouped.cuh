@@ -482,6 +482,8 @@ __global__ void __launch_bounds__(kThreads, 2) grouped_scan_kernel(ScanArgs a) {
 // lane in the order 0, 4, 2, 6, 1, 5, 3, 7 that completes the butterfly's
 // pairs as early as possible, so the distances equal the other kernels' bit
 // for bit.
+constexpr int kRowsG = kWarps * 4;   // queries per unit of the whole-rows layout
+
 template <int D>
 struct RowsLayout {
   static constexpr int kQ = 4;                 // queries per warp
@@ -489,6 +491,7 @@ struct RowsLayout {
   static constexpr int kTR = 32 * kR;          // rows per tile: one step of every warp
   static constexpr int kStg = 2;               // tiles in flight
   static constexpr int kG = kWarps * kQ;       // queries per unit
+  static_assert(kG == kRowsG, "the grouping sizes units by kRowsG");
   static constexpr int kBlock = kTR * 128;     // bytes of one 32-float column block of a tile
   static constexpr int kTile = kBlock * (D / 32);
   // offsets from the 1024-byte aligned start of the dynamic shared memory

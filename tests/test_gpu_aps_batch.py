@@ -98,7 +98,7 @@ def test_batched_aps_one_level_matches_oracle_and_per_query_kernel(I, mode):
     assert np.array_equal(pd.view(np.uint32), out[1].view(np.uint32))
 
 
-@pytest.mark.parametrize("d", [32, 128, 384])
+@pytest.mark.parametrize("d", [32, 64, 96, 128, 192, 256, 384])
 def test_every_tile_shape_gives_the_per_query_kernels_results(I, d):
     """Each tile shape splits a row over a different number of lanes (1 to 32 per row, one
     to eight of the per-query kernel's lanes per lane, or whole rows per thread); all of them
@@ -113,7 +113,7 @@ def test_every_tile_shape_gives_the_per_query_kernels_results(I, d):
     shapes = [(qw, tr, ch) for qw in (1, 2, 4) for tr, ch in ((16, 1024), (32, 4096))
               if (qw, d) not in ((4, 192), (4, 256), (4, 768), (4, 1024))]
     if d <= 256:   # whole rows per thread in the rounds after the first
-        shapes += [(4, 16, 1024, 2), (4, 32, 4096, 2)]
+        shapes += [(1, 16, 1024, 2), (2, 32, 4096, 2)]
     for shape in shapes:
         plan.set_tiles(*shape)
         gi, gd, gn = cpu(plan.search(Qd, 0.9))[:3]

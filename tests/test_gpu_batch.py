@@ -90,12 +90,14 @@ def test_per_query_kernel_matches_oracle(I, small):
     check_against_oracle(levels[0], Q[:200], nprobe[:200], gi, gd, 10)
 
 
-@pytest.mark.parametrize("d", [32, 128, 256])
-def test_batch_dims(I, d):
+@pytest.mark.parametrize("d,rows", [(32, 0), (128, 0), (256, 0), (256, 2), (192, 2)])
+def test_batch_dims(I, d, rows):
     import torch
     X, ids, Q, nprobe, levels = zipf_index(seed=52 + d, n=20_000, d=d, n_part=120, hi=3000, nq=150, np_hi=30)
     ix = make(I, X, levels)
     plan = I.BatchPlan(ix, 150, 16, 40)
+    if rows:
+        plan.tiles = (2, 32, 4096, 2)
     gi, gd = plan.search(torch.from_numpy(Q).cuda(), torch.from_numpy(nprobe).cuda())
     ix.check()
     check_against_oracle(levels[0], Q, nprobe, gi.cpu().numpy(), gd.cpu().numpy(), 16)
@@ -190,9 +192,7 @@ def test_invalid_arguments(I, small):
     with pytest.raises(L.QkError):
         plan.tiles = (2, 32, 512)
     with pytest.raises(L.QkError):
-        plan.tiles = (2, 64, 4096, 2)        # whole rows per thread need 4 queries per warp
-    with pytest.raises(L.QkError):
-        plan.tiles = (4, 64, 4096, 1)
+        plan.tiles = (4, 64, 4096, 1)        # rows_per_thread is 0 or 2
     big = torch.from_numpy(np.repeat(Q[:1], 9, axis=0)).cuda()
     with pytest.raises(L.QkError):
         plan.search(big, torch.ones(9, dtype=torch.int32, device="cuda"))   # nq above max_nq
