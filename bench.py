@@ -421,6 +421,14 @@ def run_ours(args):
                                "driver_lag_p99_ms": st["driver_lag_p99_ms"], "clocks": sclk,
                                "note": ("latency from each request's scheduled arrival to its completion, "
                                         "through the library's serving loop (qk_server_*)")}
+            if args.server == "native":   # the same sample with the slots' batched APS plans
+                st2, scfg2, sclk2 = serve_stream(args.serve_ops, args.serve_load, args.server, args.update_wait,
+                                                 args.start, maintain_every=args.serve_ops, batched_from=256)
+                line["serving"]["with_batched_plans"] = {
+                    "batched_from": 256, "saturation_qps": scfg2["saturation_qps"],
+                    "arrival_rate_ops": scfg2["arrival_rate_ops"], "search_qps": st2["search_qps"],
+                    "search": st2["search"], "insert": st2.get("insert"), "delete": st2.get("delete"),
+                    "driver_lag_p99_ms": st2["driver_lag_p99_ms"], "clocks": sclk2}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(X, ids, Q, tau, args.cpu_seconds, workers=cpu_workers(args))
         print(json.dumps(line), flush=True)
@@ -1024,16 +1032,22 @@ def run_sweep(args):
         "clocks": clk.summary()}), flush=True)
 
 
-def serve_stream(n_ops, load, server="native", update_wait=0.01, start=2_000_000, maintain_every=100_000):
+def serve_stream(n_ops, load, server="native", update_wait=0.01, start=2_000_000, maintain_every=100_000,
+                 batched_from=0):
     """The dynamic skewed stream of the serving workload (start 2M x 128 from 2,000
     components; 90% queries, 5% inserts, 5% deletes; Zipf(1.2) over a hot set of 100
     components rotating every 100,000 operations; maintenance every 100,000 operations),
     open-loop Poisson arrivals at `load` x the saturation rate measured by a closed burst.
-    Returns (latency summary, config, clocks)."""
+    batched_from > 0 (native server): batches of that many searches or more run through the
+    slots' batched APS plans.  Returns (latency summary, config, clocks)."""
     import torch
     from paper_2506_03437_b300 import index as I
     from paper_2506_03437_b300.serving import NativeServer, Server, skewed_stream
-    Srv = NativeServer if server == "native" else Server
+    if server == "native":
+        def Srv(*a, **kw):
+            return NativeServer(*a, batched_from=batched_from, **kw)
+    else:
+        Srv = Server
     n0, n_comp = start, 2000
     C = synth.mixture_centers(n_comp, D, 1240)
     X, _ = synth.mixture_samples(C, n0, SIGMA, 1241)
@@ -1061,7 +1075,8 @@ def serve_stream(n_ops, load, server="native", update_wait=0.01, start=2_000_000
     cfg = {"workload": f"serve_{n0}x{D}_{n_ops}ops", "start_vectors": n0, "ops": n_ops,
            "load": load, "saturation_qps": sat, "arrival_rate_ops": round(rate, 1),
            "update_wait_s": update_wait, "server": server, "maintain_every": maintain_every,
-           "n_leaf": n_leaf, "streams": 4, "max_batch": 2048}
+           "n_leaf": n_leaf, "streams": 4, "max_batch": 2048,
+           "batched_from": batched_from if server == "native" else None}
     del ix
     torch.cuda.empty_cache()
     return st, cfg, clk.summary()
@@ -1071,7 +1086,8 @@ def run_serve(args):
     """The serving workload on the whole stream: reports p50/p99 latency and QPS."""
     import torch
     torch.cuda.set_device(0)
-    st, cfg, clocks = serve_stream(args.ops, args.serve_load, args.server, args.update_wait, args.start)
+    st, cfg, clocks = serve_stream(args.ops, args.serve_load, args.server, args.update_wait, args.start,
+                                   batched_from=args.serve_batched_from)
     line = {"metric": "serving p50/p99 latency and QPS (dynamic skewed stream)",
             "value": st["search_qps"], "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": round(1e3 * st["wall_s"], 3), "higher_is_better": True, "scaling": "weak",
@@ -1096,6 +1112,8 @@ def main():
     ap.add_argument("--start", type=int, default=2_000_000, help="vectors in the index when the stream starts")
     ap.add_argument("--server", default="native", choices=["native", "python"],
                     help="the scheduler in the library (qk_server_*) or the Python loop of serving.py")
+    ap.add_argument("--serve-batched-from", type=int, default=0,
+                    help="serve workload: batches from this size run through batched APS plans (0: never)")
     ap.add_argument("--update-wait", type=float, default=0.01,
                     help="seconds the oldest pending update may wait before a group is applied")
     ap.add_argument("--n-batch", type=int, default=5_000_000, help="rows of the batching workload")

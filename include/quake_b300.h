@@ -654,7 +654,8 @@ qk_status qk_aps_batch_autotune(qk_aps_batch* plan, const float* q, int64_t nq, 
                                 int64_t* out_ids, float* out_dist, int32_t reps, qk_batch_tiles* chosen,
                                 void* stream);
 /* Tiles of the grouped scan (as qk_batch_set_tiles; default 2 queries per
- * warp, tile_rows 8192 / d capped to [8, 64], chunk_rows 4096). */
+ * warp, tile_rows 8192 / d capped to [8, 64], chunk_rows 4096, and whole rows
+ * per thread after the first round where d <= 256). */
 qk_status qk_aps_batch_set_tiles(qk_aps_batch* plan, const qk_batch_tiles* tiles);
 qk_status qk_aps_batch_search(qk_aps_batch* plan, const float* q, int64_t nq, float recall_target,
                               int64_t* out_ids, float* out_dist, int32_t* out_nprobe, float* out_recall,
@@ -737,6 +738,13 @@ typedef struct {
   double update_wait_s;            /* longest wait of a pending update before its group is applied */
   int32_t concurrent_maintenance;  /* 1: prepare passes beside the searches */
   const qk_maint_params* maint;    /* pass parameters (copied; required when maintain_every > 0) */
+  int32_t batched_from;            /* batches of at least this many searches run through each slot's
+                                      batched APS plan (qk_aps_batch_*; FP32 L2 indexes with k <= 32),
+                                      smaller ones through qk_search; 0 (default): always qk_search.
+                                      The two give the same results bit for bit.  The plan's persistent
+                                      kernels hold every SM for milliseconds, so update kernels wait
+                                      behind them: several times the search throughput, at tens of
+                                      milliseconds more update latency. */
 } qk_server_config;
 
 typedef struct {
@@ -761,6 +769,16 @@ void qk_server_destroy(qk_server* server);
 qk_status qk_server_submit_search(qk_server* server, const float* q, int64_t* ticket);
 qk_status qk_server_submit_insert(qk_server* server, const float* x, int64_t id, int64_t* ticket);
 qk_status qk_server_submit_delete(qk_server* server, int64_t id, int64_t* ticket);
+/* Open-loop playback of a request stream from the calling thread: request j
+ * (kind 0 search, 1 insert, 2 delete; ref the id of an insert or delete; vec
+ * n x d FP32, row j the query or the inserted vector) is submitted at t_s[j]
+ * seconds after the call starts (t_s non-decreasing), as the submit calls
+ * would, and its latency counts from that scheduled time.  lag_s (optional,
+ * n) receives how late each submission was.  Returns once every request is
+ * submitted (tickets continue from those already issued); errors as the
+ * submit calls, for the first request that fails. */
+qk_status qk_server_play(qk_server* server, int64_t n, const int8_t* kind, const int64_t* ref, const float* vec,
+                         const double* t_s, double* lag_s);
 /* Results of tickets [first, first + count): done flags, search results
  * (count x k ids and distances, -1 / +inf where not a search or not done) and
  * latencies in seconds (-1 where not done).  Any output may be NULL. */

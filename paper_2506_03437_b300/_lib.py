@@ -29,7 +29,7 @@ EXPORTS = [
     "qk_batch_search", "qk_batch_capture", "qk_batch_replay", "qk_batch_autotune", "qk_batch_set_timing",
     "qk_batch_stage_times", "qk_maintain_prepare", "qk_maintain_commit", "qk_profile_scan", "qk_save", "qk_restore",
     "qk_server_config_default", "qk_server_create", "qk_server_destroy", "qk_server_submit_search",
-    "qk_server_submit_insert", "qk_server_submit_delete", "qk_server_results", "qk_server_drain",
+    "qk_server_submit_insert", "qk_server_submit_delete", "qk_server_play", "qk_server_results", "qk_server_drain",
     "qk_server_get_stats", "qk_aps_batch_create", "qk_aps_batch_destroy", "qk_aps_batch_set_rounds",
     "qk_aps_batch_set_tiles", "qk_aps_batch_autotune", "qk_aps_batch_search", "qk_aps_batch_capture", "qk_aps_batch_replay",
     "qk_aps_batch_round_stats", "qk_aps_batch_set_timing", "qk_aps_batch_stage_times",
@@ -69,7 +69,7 @@ class QkServerConfig(C.Structure):
     _fields_ = [("k", C.c_int32), ("recall_target", C.c_float), ("max_batch", C.c_int32), ("streams", C.c_int32),
                 ("min_free_bytes", C.c_int64), ("maintain_every", C.c_int64), ("update_batch", C.c_int32),
                 ("update_wait_s", C.c_double), ("concurrent_maintenance", C.c_int32),
-                ("maint", C.POINTER(QkMaintParams))]
+                ("maint", C.POINTER(QkMaintParams)), ("batched_from", C.c_int32)]
 
 
 class QkIndexStats(C.Structure):
@@ -136,6 +136,7 @@ def _load():
         "qk_server_submit_search": (i32, [vp, vp, C.POINTER(C.c_int64)]),
         "qk_server_submit_insert": (i32, [vp, vp, i64, C.POINTER(C.c_int64)]),
         "qk_server_submit_delete": (i32, [vp, i64, C.POINTER(C.c_int64)]),
+        "qk_server_play": (i32, [vp, i64, vp, vp, vp, vp, vp]),
         "qk_server_results": (i32, [vp, i64, i64, vp, vp, vp, vp]),
         "qk_server_drain": (i32, [vp, f64]),
         "qk_server_get_stats": (i32, [vp, C.POINTER(QkServerStats)]),

@@ -482,6 +482,12 @@ struct qk_aps_batch {
   bool timing = false, timed = false;
   int timed_rounds = 0;
   cudaEvent_t ev[3 + 3 * ab::kMaxRounds] = {};
+  // pinned staging of the partition order (two, used in turn) and the events
+  // of their copies to the device
+  int32_t* h_order[2] = {};
+  int32_t h_order_cap[2] = {};
+  cudaEvent_t order_ev[2] = {};
+  int order_turn = 0;
 };
 
 namespace {
@@ -506,6 +512,14 @@ void free_all(qk_aps_batch* b) {
   afree(b->pcount), afree(b->pcur), afree(b->pstart), afree(b->qlist), afree(b->qpos), afree(b->order);
   afree(b->qcnt), afree(b->cpos), afree(b->ustart), afree(b->tmp), afree(b->tmp2), afree(b->n_units);
   afree(b->qslots), afree(b->qcoff), afree(b->ci), afree(b->gtau), afree(b->cd), afree(b->work), afree(b->rstats);
+  for (int t = 0; t < 2; ++t) {
+    if (b->order_ev[t]) cudaEventSynchronize(b->order_ev[t]);   // its copy has read the staging
+    if (b->h_order[t]) cudaFreeHost(b->h_order[t]);
+    if (b->order_ev[t]) cudaEventDestroy(b->order_ev[t]);
+    b->h_order[t] = nullptr;
+    b->order_ev[t] = nullptr;
+    b->h_order_cap[t] = 0;
+  }
 }
 
 // Rows per unit in round rd.  The first round asks each query's nearest
@@ -521,8 +535,6 @@ int round_chunk(const qk_batch_tiles& t, int rd) {
 qk_status refresh(qk_aps_batch* b, cudaStream_t s) {
   qk_index* ix = b->ix;
   if (b->version == ix->version && b->K == ix->n_leaf) return QK_OK;
-  // the plan's batches still in flight on s use the workspace re-sized below
-  QK_CUDA(cudaStreamSynchronize(s));
   const int32_t K = ix->n_leaf;
   const int32_t mcap = n_candidates(ix->cfg.f_M_leaf, K);
   const int CH = std::min(round_chunk(b->tiles, 0), round_chunk(b->tiles, 1));   // the finest chunking of a round
@@ -531,6 +543,9 @@ qk_status refresh(qk_aps_batch* b, cudaStream_t s) {
   const int64_t need_cand =
       (int64_t)b->k * b->max_nq * ((int64_t)mcap + extra);
   const size_t nq = (size_t)b->max_nq;
+  // the plan's batches still in flight on s use the workspace re-sized below;
+  // a new version of the same shape (inserts, deletes) needs no wait
+  if (mcap != b->mcap || K != b->K || need_cand > b->cand_cap) QK_CUDA(cudaStreamSynchronize(s));
   if (mcap != b->mcap) {
     ab::State& st = b->st;
     QK_TRY(aalloc(&st.cand, nq * mcap));
@@ -559,12 +574,24 @@ qk_status refresh(qk_aps_batch* b, cudaStream_t s) {
     QK_TRY(aalloc(&b->cpos, (size_t)cap));
     b->cand_cap = cap;
   }
-  std::vector<int32_t> order(K);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int32_t x, int32_t y) { return ix->h_size0[x] > ix->h_size0[y]; });
-  QK_CUDA(cudaMemcpyAsync(b->order, order.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
-  QK_CUDA(cudaStreamSynchronize(s));
+  // the partitions by decreasing size, copied in stream order from pinned
+  // staging the copy before the last has finished reading
+  const int tn = b->order_turn;
+  b->order_turn ^= 1;
+  if (!b->order_ev[tn]) QK_CUDA(cudaEventCreateWithFlags(&b->order_ev[tn], cudaEventDisableTiming));
+  QK_CUDA(cudaEventSynchronize(b->order_ev[tn]));
+  if (K > b->h_order_cap[tn]) {
+    if (b->h_order[tn]) cudaFreeHost(b->h_order[tn]);
+    b->h_order[tn] = nullptr;
+    b->h_order_cap[tn] = 0;
+    QK_CUDA(cudaMallocHost(reinterpret_cast<void**>(&b->h_order[tn]), sizeof(int32_t) * std::max(K, 1)));
+    b->h_order_cap[tn] = K;
+  }
+  int32_t* order = b->h_order[tn];
+  std::iota(order, order + K, 0);
+  std::stable_sort(order, order + K, [&](int32_t x, int32_t y) { return ix->h_size0[x] > ix->h_size0[y]; });
+  QK_CUDA(cudaMemcpyAsync(b->order, order, sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
+  QK_CUDA(cudaEventRecord(b->order_ev[tn], s));
   b->version = ix->version;
   return QK_OK;
 }
@@ -882,6 +909,7 @@ qk_status qk_aps_batch_create(qk_index* ix, int64_t max_nq, int32_t k, qk_aps_ba
   b->tiles.queries_per_warp = 2;
   b->tiles.tile_rows = std::max(8, std::min(64, 8192 / ix->cfg.d));
   b->tiles.chunk_rows = 4096;
+  b->tiles.rows_per_thread = bt::rows_layout_ok(ix->cfg.d) ? 2 : 0;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);

@@ -70,6 +70,7 @@ struct Slot {
   std::vector<int64_t> tickets;   // of the batch in flight
   std::vector<Clock::time_point> t0;
   bool busy = false;
+  qk_aps_batch* plan = nullptr;   // batched APS workspace of this slot (null: qk_search only)
 };
 
 }  // namespace
@@ -385,9 +386,13 @@ void scheduler_body(qk_server* sv) {
       cudaStream_t st = slot->stream;
       const int k = sv->cfg.k;
       cudaMemcpyAsync(slot->q_dev, slot->q_host, sizeof(float) * n * d, cudaMemcpyHostToDevice, st);
-      if (fail(sv, qk_search(sv->ix, slot->q_dev, n, k, sv->cfg.recall_target, 0, slot->ids_dev, slot->dist_dev,
-                             nullptr, nullptr, st),
-               "search")) {
+      const qk_status ss =
+          slot->plan && n >= sv->cfg.batched_from
+              ? qk_aps_batch_search(slot->plan, slot->q_dev, n, sv->cfg.recall_target, slot->ids_dev, slot->dist_dev,
+                                    nullptr, nullptr, nullptr, 0, st)
+              : qk_search(sv->ix, slot->q_dev, n, k, sv->cfg.recall_target, 0, slot->ids_dev, slot->dist_dev, nullptr,
+                          nullptr, st);
+      if (fail(sv, ss, "search")) {
         slot->tickets.clear();
         slot->t0.clear();
         break;
@@ -427,7 +432,10 @@ void scheduler_loop(qk_server* sv) {
   }
 }
 
-qk_status submit(qk_server* sv, int kind, const float* x, int64_t id, int64_t* ticket) {
+// A request whose latency counts from `at` (its arrival; now for the public
+// submit calls).
+qk_status submit(qk_server* sv, int kind, const float* x, int64_t id, int64_t* ticket,
+                 Clock::time_point at = Clock::time_point{}) {
   if (!sv || !ticket) {
     set_error("null argument");
     return QK_ERR_ARG;
@@ -464,7 +472,7 @@ qk_status submit(qk_server* sv, int kind, const float* x, int64_t id, int64_t* t
     sv->res_ids.resize((size_t)(t + 1) * k, -1);
     sv->res_dist.resize((size_t)(t + 1) * k, INFINITY);
   }
-  Op o{t, kind, id, Clock::now()};
+  Op o{t, kind, id, at == Clock::time_point{} ? Clock::now() : at};
   if (kind == 0) {
     sv->searches.push_back(o);
     sv->search_q.emplace_back(x, x + sv->d);
@@ -495,6 +503,7 @@ void qk_server_config_default(qk_server_config* c) {
   c->update_wait_s = 0.01;
   c->concurrent_maintenance = 1;
   c->maint = nullptr;
+  c->batched_from = 0;
 }
 
 qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server** out) {
@@ -510,7 +519,7 @@ qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server*
   }
   if (cfg->k < 1 || cfg->k > 1024 || cfg->max_batch < 1 || cfg->streams < 1 || cfg->streams > kWorkSlots ||
       cfg->update_batch < 1 || !(cfg->update_wait_s >= 0) || cfg->maintain_every < 0 ||
-      (cfg->maintain_every > 0 && !cfg->maint)) {
+      (cfg->maintain_every > 0 && !cfg->maint) || cfg->batched_from < 0) {
     set_error("invalid server configuration");
     return QK_ERR_ARG;
   }
@@ -551,6 +560,13 @@ qk_status qk_server_create(qk_index* ix, const qk_server_config* cfg, qk_server*
   }
   ck(cudaStreamCreateWithFlags(&sv->maint_stream, cudaStreamNonBlocking));
   ck(cudaStreamCreateWithPriority(&sv->update_stream, cudaStreamNonBlocking, prio_hi));
+  // a batched APS plan per slot where the index's form allows it; without one
+  // every batch runs through qk_search
+  if (st == QK_OK && cfg->batched_from > 0 && cfg->batched_from <= mb && ix->cfg.metric == QK_METRIC_L2 &&
+      ix->cfg.storage == QK_STORE_F32 && k <= 32) {
+    for (Slot& s : sv->slots)
+      if (qk_aps_batch_create(ix, mb, k, &s.plan) != QK_OK) s.plan = nullptr;
+  }
   if (st != QK_OK) {
     qk_server_destroy(sv);
     return st;
@@ -585,6 +601,34 @@ qk_status qk_server_submit_insert(qk_server* sv, const float* x, int64_t id, int
 qk_status qk_server_submit_delete(qk_server* sv, int64_t id, int64_t* ticket) {
   QK_GUARD_BEGIN
   return submit(sv, 2, nullptr, id, ticket);
+  QK_GUARD_END
+}
+
+qk_status qk_server_play(qk_server* sv, int64_t n, const int8_t* kind, const int64_t* ref, const float* vec,
+                         const double* t_s, double* lag_s) {
+  QK_GUARD_BEGIN
+  if (!sv || n < 0 || (n > 0 && (!kind || !ref || !t_s))) {
+    set_error("invalid arguments");
+    return QK_ERR_ARG;
+  }
+  const Clock::time_point t0 = Clock::now();
+  int64_t ticket = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const Clock::time_point due =
+        t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(t_s[j]));
+    Clock::time_point now = Clock::now();
+    if (due - now > std::chrono::microseconds(200)) std::this_thread::sleep_for(due - now - std::chrono::microseconds(100));
+    while ((now = Clock::now()) < due) {
+    }
+    if (lag_s) lag_s[j] = secs(due, now);
+    const int kd = kind[j];
+    if (kd < 0 || kd > 2 || (kd != 2 && !vec)) {
+      set_error("operation " + std::to_string(j) + ": invalid kind or missing vector");
+      return QK_ERR_ARG;
+    }
+    QK_TRY(submit(sv, kd, kd == 2 ? nullptr : vec + j * (int64_t)sv->d, kd == 0 ? -1 : ref[j], &ticket, due));
+  }
+  return QK_OK;
   QK_GUARD_END
 }
 
@@ -708,6 +752,7 @@ void qk_server_destroy(qk_server* sv) {
     if (s.q_dev) cudaFree(s.q_dev);
     if (s.ids_dev) cudaFree(s.ids_dev);
     if (s.dist_dev) cudaFree(s.dist_dev);
+    if (s.plan) qk_aps_batch_destroy(s.plan);
   }
   if (sv->maint_stream) cudaStreamDestroy(sv->maint_stream);
   if (sv->update_stream) cudaStreamDestroy(sv->update_stream);

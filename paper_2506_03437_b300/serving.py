@@ -318,19 +318,21 @@ def skewed_stream(centers, start_ids, n_ops, sigma, seed, hot=100, zipf=1.2, rot
 
 class NativeServer:
     """The same serving loop run by the library's scheduler thread (qk_server_* in
-    include/quake_b300.h): this class only drives the open-loop arrivals and reads the
-    results.  A request's latency counts from its scheduled arrival: the time between the
-    arrival and the submission (if the driver runs late) is added to the server's own."""
+    include/quake_b300.h), with the open-loop arrivals played by the library as well
+    (qk_server_play); this class only builds the configuration and reads the results.  A
+    request's latency counts from its scheduled arrival, so a late submission counts in it."""
 
     def __init__(self, index, d, k=10, recall_target=0.9, max_batch=2048, streams=4, min_free_bytes=1 << 30,
                  maintain_every=0, maint_args=None, update_batch=1024, update_wait_s=0.01,
-                 concurrent_maintenance=True):
+                 concurrent_maintenance=True, batched_from=None):
         import ctypes as C
         from . import _lib as L
         self.C, self.L = C, L
         self.ix, self.d, self.k = index, d, k
         cfg = L.QkServerConfig()
         L.lib.qk_server_config_default(C.byref(cfg))
+        if batched_from is not None:   # batches from this size run through the batched APS plan
+            cfg.batched_from = int(batched_from)
         cfg.k, cfg.recall_target, cfg.max_batch, cfg.streams = k, recall_target, max_batch, streams
         cfg.min_free_bytes, cfg.maintain_every = min_free_bytes, maintain_every
         cfg.update_batch, cfg.update_wait_s = update_batch, update_wait_s
@@ -363,29 +365,14 @@ class NativeServer:
         n = len(ops)
         lag = np.zeros(n)
         vec = np.ascontiguousarray(ops.vec, np.float32)
-        base, row = vec.ctypes.data, vec.shape[1] * 4
-        kinds, refs, ts = ops.kind.tolist(), ops.ref.tolist(), ops.t.tolist()
-        tk = C.c_int64()
-        sub_s, sub_i, sub_d = L.lib.qk_server_submit_search, L.lib.qk_server_submit_insert, L.lib.qk_server_submit_delete
+        kinds = np.ascontiguousarray(ops.kind, np.int8)
+        refs = np.ascontiguousarray(ops.ref, np.int64)
+        ts = np.ascontiguousarray(ops.t, np.float64)
         try:
             t0 = time.perf_counter()
-            for j in range(n):
-                now = time.perf_counter() - t0
-                if ts[j] > now:
-                    if ts[j] - now > 2e-4:
-                        time.sleep(ts[j] - now - 1e-4)
-                    while time.perf_counter() - t0 < ts[j]:
-                        pass
-                    now = time.perf_counter() - t0
-                lag[j] = now - ts[j]
-                kd = kinds[j]
-                if kd == SEARCH:
-                    st = sub_s(h, base + j * row, C.byref(tk))
-                elif kd == INSERT:
-                    st = sub_i(h, base + j * row, refs[j], C.byref(tk))
-                else:
-                    st = sub_d(h, refs[j], C.byref(tk))
-                L.check(st)
+            # the library plays the stream open-loop from this thread: each request
+            # is submitted at its scheduled time and its latency counts from it
+            L.check(L.lib.qk_server_play(h, n, L.ptr(kinds), L.ptr(refs), L.ptr(vec), L.ptr(ts), L.ptr(lag)))
             L.check(L.lib.qk_server_drain(h, 0.0))
             wall = time.perf_counter() - t0
             done = np.zeros(n, np.int32)
@@ -398,7 +385,6 @@ class NativeServer:
         finally:
             L.lib.qk_server_destroy(h)
         assert done.all()
-        lat = lat + lag
         self.out_ids, self.out_dist = ids, dist
         out = {"wall_s": round(wall, 4), "batches": stt.batches, "maintenance_passes": stt.maintenance_passes,
                "update_groups": stt.update_groups, "update_s": round(stt.update_s, 4),

@@ -59,7 +59,11 @@ def test_stream_with_updates_and_maintenance(concurrent):
     assert sorted(got.tolist()) == sorted(live)
 
 
-def test_native_server_results_alone_equal_results_in_the_mix():
+@pytest.mark.parametrize("batched_from", [0, 1, 64])
+def test_native_server_results_alone_equal_results_in_the_mix(batched_from):
+    """Each search's result in a served stream equals the per-query kernel's result for the
+    query alone, whether its batch ran through qk_search (batched_from 0), through the slot's
+    batched APS plan (1), or either, by batch size (64)."""
     from paper_2506_03437_b300.serving import NativeServer, Ops
     X, ids, Q = synth.aps_search(seed=43, n=30_000, d=64, n_comp=40, sigma=1.2, nq=3000)
     levels = kmeans.build_index(X, ids, 150, 8, iters=3, seed=5)
@@ -67,7 +71,7 @@ def test_native_server_results_alone_equal_results_in_the_mix():
     ix = make_index(I, X, ids, levels, f_M_leaf=0.15, f_M_parent=0.5)
     alone = [ix.search(Q[j:j + 1], 10, recall_target=0.9) for j in range(0, 3000, 7)]
     ops = Ops(np.zeros(3000), np.zeros(3000, np.int8), Q, np.full(3000, -1))
-    srv = NativeServer(ix, 64, k=10, recall_target=0.9, max_batch=200, streams=4)
+    srv = NativeServer(ix, 64, k=10, recall_target=0.9, max_batch=200, streams=4, batched_from=batched_from)
     st = srv.run(ops, keep_results=True)
     assert st["batches"] >= 15 and st["search"]["n"] == 3000
     for n, j in enumerate(range(0, 3000, 7)):
