@@ -70,10 +70,10 @@ KERNEL_SOURCES = ["search_impl.cuh", "common.cuh", "capvol.cuh", "index.cuh"]
 # DRAM traffic of the grouped scans of one batched APS step on the full workload
 # (its four launches, one per round, summed: the lane-split layout in round 1,
 # whole rows after it), from the single-pass ncu capture summarised in
-# profiles/aps_batch_launches_1Mx128.md, with tiles (4, 32, 4096, 2) as the
+# profiles/aps_batch_launches_1Mx128.md, with tiles (2, 64, 4096, 2) as the
 # autotuner picks them; it belongs to these sources with this hash.
-SCAN_TRAFFIC_BYTES = (458.28 + 9.26 + 547.06 + 33.83 + 0.219 + 0.217) * 1e6
-SCAN_TRAFFIC_HASH = "62795b5052439e5b"
+SCAN_TRAFFIC_BYTES = (457.27 + 6.97 + 546.75 + 33.60 + 0.219 + 0.217) * 1e6
+SCAN_TRAFFIC_HASH = "8578e79dd54ba8eb"
 SCAN_SOURCES = ["grouped.cuh", "common.cuh", "index.cuh", "aps_batch.cu"]
 
 
