@@ -207,6 +207,7 @@ def run_ours(args):
     storage = {"f32": 0, "bf16": 1, "fp8": 2}[args.storage]
     ix = I.Index(D, n_leaf=N_LEAF, n_parent=N_PARENT, kmeans_iters=ITERS, seed=SEED,
                  f_M_leaf=F_M_LEAF, f_M_parent=F_M_PARENT, storage=storage, rerank=args.rerank)
+    ix.set_search_upper(args.search_upper)
     t0 = time.time()
     ix.build(Xd, idd)
     torch.cuda.synchronize()
@@ -833,6 +834,7 @@ def run_precision(args):
             st = {"f32": L.STORE_F32, "bf16": L.STORE_BF16, "fp8": L.STORE_FP8}[storage]
             ix = I.Index(d, metric=L.METRIC_IP, n_leaf=n_leaf, n_parent=n_parent, kmeans_iters=args.prec_iters,
                          seed=SEED, f_M_leaf=args.prec_fm, f_M_parent=F_M_PARENT, storage=st, rerank=4)
+            ix.set_search_upper(args.search_upper)
             tb = time.time()
             if assign is None:
                 ix.build(Xd, ids)
@@ -898,6 +900,7 @@ def run_precision(args):
                    "kmeans_iters": args.prec_iters, "best_form": best, "forms": forms,
                    "fp32_vs_best_speedup": round(v["qps"] / forms["f32"]["qps"], 3) if "f32" in forms else None,
                    "spread_s": args.prec_spread, "f_M": [args.prec_fm, F_M_PARENT],
+                   "search_upper": args.search_upper,
                    "l2": "no flush: 30.7 GB FP32 arena > 126 MB L2", "data_gen_s": round(gen_s, 1),
                    "ground_truth_s": round(gt_s, 1)},
         "roofline": {"bound": "hbm", "achieved": v["scan_gbs"], "peak": peak, "unit": "GB/s",
@@ -1127,6 +1130,9 @@ def main():
                     help="noise s of the precision mixture: x = normalize(mu + s g / sqrt(d))")
     ap.add_argument("--prec-forms", default="f32,bf16,fp8", help="storage forms of the precision workload")
     ap.add_argument("--prec-fm", type=float, default=0.02, help="f_M of the leaf level (candidate fraction)")
+    ap.add_argument("--search-upper", type=int, default=-1, choices=[-1, 0, 1],
+                    help="qk_set_search_upper mode of the per-query search (aps and precision workloads): "
+                         "-1 auto, 0 in each query's CTA, 1 prepare kernel")
     ap.add_argument("--tiles", default="", help="queries_per_warp,tile_rows,chunk_rows of the grouped scan "
                                                  "(aps and batch workloads) instead of the autotuner's choice")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

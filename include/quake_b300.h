@@ -145,6 +145,15 @@ qk_status qk_load(qk_index* index, const float* x, const int64_t* ids, int64_t n
                   const float* leaf_centroids, const int32_t* leaf_of_row,
                   const float* parent_centroids, const int32_t* parent_of_leaf, void* stream);
 
+/* Where qk_search walks the upper levels (the top partition and APS on the
+ * parent level, Sec. 5) of a two-level index: 1 = a warp-per-query prepare
+ * kernel ahead of the search kernel, 0 = inside each query's CTA, -1
+ * (default) = 1 for d <= 256 (a warp sums 4 rows per step there), else 0.
+ * Both give the same candidates and t_i bit for bit, hence the same
+ * results; qk_search_scanned's upper-level record and the ratio rule always
+ * use 0.  QK_ERR_ARG for another value. */
+qk_status qk_set_search_upper(qk_index* index, int32_t mode);
+
 /*
  * Searches nq queries q (nq x d) for their k nearest neighbours (k <= 1024).
  *

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIME
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = [
-    "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load",
+    "qk_config_default", "qk_create", "qk_destroy", "qk_last_error", "qk_build", "qk_load", "qk_set_search_upper",
     "qk_search", "qk_search_scanned", "qk_stats", "qk_insert", "qk_delete", "qk_check", "qk_info", "qk_export_level", "qk_export_quantized", "qk_get_hits", "qk_cap_fraction",
     "qk_kmeans_step", "qk_kmeans_step_noalloc", "qk_maintain", "qk_nearest_centroids",
     "qk_search_nprobe", "qk_search_ratio", "qk_batch_create", "qk_batch_destroy", "qk_batch_get_tiles", "qk_batch_set_tiles",
@@ -100,6 +100,7 @@ def _load():
     lib = C.CDLL(LIB_PATH)
     vp, i64, i32, f32, f64 = C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_double
     sig = {
+        "qk_set_search_upper": (i32, [vp, i32]),
         "qk_config_default": (None, [C.POINTER(QkConfig)]),
         "qk_create": (i32, [C.POINTER(QkConfig), C.POINTER(vp)]),
         "qk_destroy": (None, [vp]),

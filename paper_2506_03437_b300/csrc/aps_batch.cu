@@ -445,6 +445,17 @@ __global__ void fill_kernel(const int32_t* req, const int32_t* nreq, const int32
 }
 
 }  // namespace ab
+
+int32_t prepare_mcap(const SearchArgs& a) { return ap::mcap_of(a); }
+
+qk_status prepare_upper(const SearchArgs& a, cudaStream_t s) {
+  if (!ap::fits(a)) {
+    set_error("the prepare kernel's buffers do not hold this search's candidate counts");
+    return QK_ERR_UNSUPPORTED;
+  }
+  return ap::launch_prepare(a, s);
+}
+
 }  // namespace qk
 
 // ------------------------------------------------------------------ the plan

@@ -968,7 +968,37 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   a.scan_cap0 = cap0;
   a.scan1 = scan1 ? ds1 : nullptr;
   a.scan_cap1 = cap1;
-  QK_TRY(launch_search(a, s));
+  // Where rows are short (d <= 256: a warp sums 4 rows per step) the upper
+  // levels go to the warp-per-query prepare kernel first: it walks them
+  // bitwise as the query's CTA would, without the CTA's barriers, and the
+  // search kernel imports its candidates and t_i (1M x 128, 1,000 leaves:
+  // 466k -> 494k queries/s).  For longer rows a warp sums one row per step
+  // and the CTA's 8 warps walk faster (d = 768: 265k against 139k).
+  void* xs = nullptr;
+  if (a.L == 2 && !a.scan1 && !(a.ratio_eps > 0.f) &&
+      (ix->upper_mode == 1 || (ix->upper_mode < 0 && ix->cfg.d <= 256))) {
+    SearchArgs pa = a;
+    pa.xs_mcap = prepare_mcap(a);
+    const size_t n = (size_t)nq * (size_t)pa.xs_mcap;
+    const size_t b_t = sizeof(double) * n, b_c = sizeof(int32_t) * n, b_m = sizeof(int32_t) * (size_t)nq;
+    QK_CUDA(cudaMallocAsync(&xs, b_t + b_c + b_m, s));
+    pa.xs_t = static_cast<double*>(xs);
+    pa.xs_cand = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(xs) + b_t);
+    pa.xs_M = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(xs) + b_t + b_c);
+    const qk_status ps = prepare_upper(pa, s);
+    if (ps == QK_OK) {
+      a.im_M = pa.xs_M;
+      a.im_cand = pa.xs_cand;
+      a.im_t = pa.xs_t;
+      a.im_mcap = pa.xs_mcap;
+    } else if (ps != QK_ERR_UNSUPPORTED) {
+      cudaFreeAsync(xs, s);
+      return ps;
+    }
+  }
+  const qk_status ls = launch_search(a, s);
+  if (xs) QK_CUDA(cudaFreeAsync(xs, s));
+  QK_TRY(ls);
   note_readers(ix, s);
   pub.unlock();
   tr.mark("launch");
@@ -985,6 +1015,17 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
     return st;
   }
   return QK_OK;
+}
+
+qk_status qk_set_search_upper(qk_index* ix, int32_t mode) {
+  QK_GUARD_BEGIN
+  if (!ix || mode < -1 || mode > 1) {
+    set_error("upper-level mode is -1 (auto), 0 (in the query's CTA) or 1 (prepare kernel)");
+    return QK_ERR_ARG;
+  }
+  ix->upper_mode = mode;
+  return QK_OK;
+  QK_GUARD_END
 }
 
 qk_status qk_search(qk_index* ix, const float* q, int64_t nq, int32_t k, float recall_target, int32_t nprobe,

@@ -92,6 +92,12 @@ struct SearchArgs {
   int32_t* xs_cand = nullptr;    // nq x xs_mcap leaf candidate partitions, nearest first
   double* xs_t = nullptr;        // nq x xs_mcap their bisector distances t_i
   int32_t xs_mcap = 0;
+  // import: the upper levels were searched by the prepare step (the same walk,
+  // bitwise); per query M, the leaf candidates and their t_i (nq x im_mcap)
+  const int32_t* im_M = nullptr;
+  const int32_t* im_cand = nullptr;
+  const double* im_t = nullptr;
+  int32_t im_mcap = 0;
   int32_t kcap = 16;             // capacity of the result set (>= every k used)
   int32_t mcap = 16;             // capacity of the candidate list
 };
@@ -164,6 +170,7 @@ struct qk_index {
   unsigned long long* hits0 = nullptr;
   unsigned long long* hits1 = nullptr;
   int32_t* work = nullptr;
+  int32_t upper_mode = -1;        // upper levels of qk_search: -1 auto, 0 in the query's CTA, 1 prepare kernel
   int32_t* status = nullptr;
   int64_t* diag = nullptr;
   double beta_a = 0.0, beta_lnB = 0.0;
@@ -213,6 +220,12 @@ int32_t n_candidates(double f, int32_t n);
 // recall target and fixed nprobe (queries, outputs and records not set).
 void base_search_args(qk_index* ix, int32_t k, float recall_target, int32_t nprobe, SearchArgs& a);
 qk_status launch_search(const SearchArgs& a, cudaStream_t stream);
+// The upper levels of a search by the warp-per-query prepare kernel, exporting
+// each query's leaf candidates and t_i into a.xs_*; QK_ERR_UNSUPPORTED when
+// its per-warp buffers cannot hold the search's candidate counts.
+qk_status prepare_upper(const SearchArgs& a, cudaStream_t stream);
+// The xs_mcap a search's export needs.
+int32_t prepare_mcap(const SearchArgs& a);
 
 // Copy-on-write views (views.cu).
 // Records that the work just enqueued on `s` reads the current version

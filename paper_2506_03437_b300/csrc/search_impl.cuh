@@ -633,7 +633,7 @@ struct Block {
   // rho and the "R holds k results" rule use the k-th; krow locates result rows
   // for the inner-product radius; mode selects the scanned rows (see scan_pos).
   __device__ void aps(const DevLevel& lv, int M, int K, int k, double tau, int fixed, unsigned long long* hits,
-                      int mode, const float* krow, double& r_out, int& nprobe_out) {
+                      int mode, const float* krow, double& r_out, int& nprobe_out, bool t_given = false) {
     reset_R(K);
     for (int i = tid; i < M; i += kThreads) csc[i] = 0;
     __syncthreads();
@@ -644,7 +644,7 @@ struct Block {
       nprobe_out = n;
       return;
     }
-    bisector(lv, M);
+    if (!t_given) bisector(lv, M);
     int ns = 0;
     scan_pos(lv, 0, M, K, hits, mode);
     ns = 1;
@@ -868,12 +868,28 @@ __global__ void __launch_bounds__(kThreads, (NV * 4 * TPR <= 256) ? 3 : 2) aps_s
     // partition and the upper levels rank centroids by squared L2; only the
     // base rows use the index's metric (for inner product, -<q, x>).
     b.metric = QK_METRIC_L2;
+    int M = 0;
+    double r = 0.0;
+    int np = 0;
+    const bool imported = args.im_M != nullptr;
+    if (imported) {
+      // the upper levels were walked by the prepare step: its leaf candidates and t_i
+      M = args.im_M[qi];
+      if (M < 1 || M > args.mcap) {   // a query the prepare step refused is refused above
+        if (threadIdx.x == 0) b.report(DEV_BAD_INDEX, 4, M, args.mcap);
+        __syncthreads();
+        continue;
+      }
+      for (int i = threadIdx.x; i < M; i += kThreads) {
+        b.cpart[i] = args.im_cand[qi * args.im_mcap + i];
+        b.ct[i] = args.im_t[qi * args.im_mcap + i];
+      }
+      __syncthreads();
+    } else {
     // top partition: all centroids of the top level
     b.reset_R(args.M_root);
     b.template scan<ElemF32>(reinterpret_cast<const unsigned char*>(args.root), nullptr, 0, args.n_root, args.M_root, 1.f);
-    int M = b.take_candidates();
-    double r = 0.0;
-    int np = 0;
+    M = b.take_candidates();
     if (args.L == 2) {
       // level-1 rows are leaf centroids whose id is the leaf index: x_k = cent0[id]
       if (args.scan1) b.record_start(args.scan1 + qi * args.scan_cap1, args.scan_cap1);
@@ -882,6 +898,7 @@ __global__ void __launch_bounds__(kThreads, (NV * 4 * TPR <= 256) ? 3 : 2) aps_s
       M = b.take_candidates();
     } else if (args.scan1) {
       for (int i = threadIdx.x; i < args.scan_cap1; i += kThreads) args.scan1[qi * args.scan_cap1 + i] = -1;
+    }
     }
     if (args.xs_M) {
       // batched APS: export S_0 with its t_i; the leaf level is scanned in
@@ -900,7 +917,8 @@ __global__ void __launch_bounds__(kThreads, (NV * 4 * TPR <= 256) ? 3 : 2) aps_s
     if (args.ratio_eps > 0.f) fixed = b.ratio_count(M, args.ratio_eps);
     b.metric = args.metric;
     if (args.scan0) b.record_start(args.scan0 + qi * args.scan_cap0, args.scan_cap0);
-    b.aps(args.lv[0], M, args.k0, args.kq, args.tau0, fixed, args.hits0, args.mode0, args.lv[0].vec, r, np);
+    b.aps(args.lv[0], M, args.k0, args.kq, args.tau0, fixed, args.hits0, args.mode0, args.lv[0].vec, r, np,
+          imported);
     if (args.scan0) b.record_finish();
     if (b.aborted) break;
     if (args.mode0 != 0) b.rerank(args.lv[0].vec, args.lv[0].ids);

@@ -90,6 +90,11 @@ class Index:
         L.check(L.lib.qk_load(self._h, L.ptr(x), L.ptr(ids), int(ids.shape[0]), L.ptr(c0), L.ptr(a0),
                               L.ptr(c1), L.ptr(a1), L.stream_ptr(stream)))
 
+    def set_search_upper(self, mode):
+        """Where search walks the upper levels: -1 auto, 0 in each query's CTA, 1 a
+        warp-per-query prepare kernel first (the same results either way)."""
+        L.check(L.lib.qk_set_search_upper(self._h, int(mode)))
+
     def search(self, q, k, recall_target=0.9, nprobe=0, out=None, stream=None):
         """Returns (ids, dist, nprobe, recall_estimate) on the device of `q`."""
         q = _as(q, np.float32)

@@ -139,3 +139,31 @@ def test_precision_shaped_aps_matches_oracle(I):
     gtD, _ = knn.knn(X, ids, Q, 100, metric=knn.IP, bulk=True)
     rec = knn.recall_at_k(out[0], exact_dist(X, Q, out[0], knn.IP), gtD, 100).mean()
     assert rec > 0.5
+
+
+@pytest.mark.parametrize("d,metric,storage", [(768, 1, 2), (768, 1, 0), (128, 0, 0), (128, 0, 1)])
+def test_upper_levels_by_the_prepare_kernel_change_nothing(I, d, metric, storage):
+    """qk_search may walk the upper levels with the warp-per-query prepare kernel and import
+    its candidates and t_i (qk_set_search_upper 1) instead of walking them in each query's
+    CTA (0): ids, distances, nprobe and r must be the same bit for bit, in every storage
+    form and metric."""
+    if metric == 1:
+        X, ids, Q = synth.unit_mixture(seed=1250 + d, n=60_000, d=d, n_comp=60, s=2.0, nq=64)
+    else:
+        X, ids, Q = synth.aps_search(seed=1250 + d, n=60_000, d=d, n_comp=60, sigma=1.0, nq=64)
+    levels = kmeans.build_index(X, ids, 240, 12, iters=3, seed=9)
+    ix = make(I, X, ids, levels, metric=metric, storage=storage, f_M_leaf=0.1, f_M_parent=0.5)
+    k = 100 if metric == 1 else 10
+    ix.set_search_upper(0)
+    a = ix.search(Q, k, recall_target=0.9)
+    ix.set_search_upper(1)
+    b = ix.search(Q, k, recall_target=0.9)
+    ix.set_search_upper(-1)
+    c = ix.search(Q, k, recall_target=0.9)
+    ix.check()
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+        assert np.array_equal(x.view(np.uint8), z.view(np.uint8))
+    assert a[2].max() > 1
+    with pytest.raises(Exception):
+        ix.set_search_upper(2)
