@@ -1036,7 +1036,7 @@ def run_sweep(args):
 
 
 def serve_stream(n_ops, load, server="native", update_wait=0.01, start=2_000_000, maintain_every=100_000,
-                 batched_from=0):
+                 batched_from=0, search_upper=-1):
     """The dynamic skewed stream of the serving workload (start 2M x 128 from 2,000
     components; 90% queries, 5% inserts, 5% deletes; Zipf(1.2) over a hot set of 100
     components rotating every 100,000 operations; maintenance every 100,000 operations),
@@ -1058,6 +1058,7 @@ def serve_stream(n_ops, load, server="native", update_wait=0.01, start=2_000_000
     n_leaf = int(round(n0 ** 0.5))
     ix = I.Index(D, n_leaf=n_leaf, n_parent=int(round(n_leaf ** 0.5)), kmeans_iters=ITERS, seed=SEED,
                  f_M_leaf=F_M_LEAF, f_M_parent=F_M_PARENT)
+    ix.set_search_upper(search_upper)
     ix.build(torch.from_numpy(X).cuda(), torch.from_numpy(ids).cuda())
     # scan latency lambda(s) per (query, partition): 2 us + 45 ns per 128-d FP32 row, from the
     # search kernel's per-CTA scan rate measured by bench.py (about 11 GB/s per resident query)
@@ -1090,7 +1091,7 @@ def run_serve(args):
     import torch
     torch.cuda.set_device(0)
     st, cfg, clocks = serve_stream(args.ops, args.serve_load, args.server, args.update_wait, args.start,
-                                   batched_from=args.serve_batched_from)
+                                   batched_from=args.serve_batched_from, search_upper=args.search_upper)
     line = {"metric": "serving p50/p99 latency and QPS (dynamic skewed stream)",
             "value": st["search_qps"], "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": round(1e3 * st["wall_s"], 3), "higher_is_better": True, "scaling": "weak",
