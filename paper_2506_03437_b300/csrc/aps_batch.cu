@@ -419,6 +419,8 @@ __global__ void __launch_bounds__(kThreads) aps_replay_kernel(ReplayArgs a) {
   extern __shared__ __align__(16) unsigned char s_stage[];   // per warp: stage_bytes(mcap), when staged
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* stage = a.staged ? s_stage + (size_t)warp * stage_bytes(a.mcap) : nullptr;
+  // a round that asked for nothing: every query had finished before it
+  if (a.rstats && a.round >= 0 && a.rstats[2 * a.round] == 0ull) return;
   for (;;) {
     unsigned long long q = 0;
     if (lane == 0) q = atomicAdd(a.next_q, 1ull);
@@ -431,9 +433,10 @@ __global__ void __launch_bounds__(kThreads) aps_replay_kernel(ReplayArgs a) {
 
 // Lists every requested item under its partition, with its position.
 __global__ void fill_kernel(const int32_t* req, const int32_t* nreq, const int32_t* cand, int64_t nq, int mcap,
-                            const int32_t* pstart, int32_t* pcur, int32_t* qlist, int32_t* qpos) {
+                            const int32_t* pstart, int32_t* pcur, int32_t* qlist, int32_t* qpos,
+                            const unsigned long long* asked) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nq * mcap) return;
+  if (i >= nq * mcap || (asked && *asked == 0ull)) return;
   const int64_t q = i / mcap;
   const int j = (int)(i % mcap);
   if (j >= nreq[q]) return;
@@ -728,12 +731,16 @@ qk_status enqueue(qk_aps_batch* b, const float* q, int64_t nq, float recall_targ
     ga.cand_cap = b->cand_cap;
     ga.status = ix->status;
     ga.diag = ix->diag;
+    // the items this round asked for, counted by the replay that asked: a round
+    // with none (every query finished) skips its grouping, fill and replay
+    const unsigned long long* asked = b->rstats ? b->rstats + 2 * rd : nullptr;
+    ga.asked = asked;
     bt::group_kernel<<<1, 1024, 0, s>>>(ga);
     QK_CUDA(cudaGetLastError());
     QK_CUDA(cudaMemsetAsync(b->pcur, 0, sizeof(int32_t) * K, s));
     const int64_t items = nq * mcap;
     ab::fill_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(b->st.req, b->st.nreq, b->st.cand, nq, mcap,
-                                                                   b->pstart, b->pcur, b->qlist, b->qpos);
+                                                                   b->pstart, b->pcur, b->qlist, b->qpos, asked);
     QK_CUDA(cudaGetLastError());
     QK_TRY(mark(3 + 3 * rd));
     // 4. every item's own top-k

@@ -849,11 +849,16 @@ struct GroupArgs {
   int64_t cand_cap = 0;
   int32_t* status = nullptr;
   int64_t* diag = nullptr;
+  const unsigned long long* asked = nullptr;   // items requested for this grouping (null: unknown)
 };
 
 static __global__ void __launch_bounds__(1024) group_kernel(GroupArgs a) {
   __shared__ int64_t s_part[1024];
   __shared__ int64_t s_tot;
+  if (a.asked && *a.asked == 0ull) {   // nothing requested: no units
+    if (threadIdx.x == 0) *a.n_units = 0;
+    return;
+  }
   // query-list offsets per partition (index order)
   for (int p = threadIdx.x; p < a.K; p += blockDim.x) a.tmp[p] = a.pcount[p];
   __syncthreads();
