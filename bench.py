@@ -417,6 +417,7 @@ def run_ours(args):
             line["p50_ms"] = st["search"]["p50_ms"]
             line["p99_ms"] = st["search"]["p99_ms"]
             line["serving"] = {"config": scfg, "search_qps": st["search_qps"], "search": st["search"],
+                               "recall_at_10_sample": st["recall_at_10_sample"],
                                "insert": st.get("insert"), "delete": st.get("delete"),
                                "maintenance_passes": st["maintenance_passes"],
                                "driver_lag_p99_ms": st["driver_lag_p99_ms"], "clocks": sclk,
@@ -429,6 +430,7 @@ def run_ours(args):
                     "batched_from": 256, "saturation_qps": scfg2["saturation_qps"],
                     "arrival_rate_ops": scfg2["arrival_rate_ops"], "search_qps": st2["search_qps"],
                     "search": st2["search"], "insert": st2.get("insert"), "delete": st2.get("delete"),
+                    "recall_at_10_sample": st2["recall_at_10_sample"],
                     "driver_lag_p99_ms": st2["driver_lag_p99_ms"], "clocks": sclk2}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(X, ids, Q, tau, args.cpu_seconds, workers=cpu_workers(args))
@@ -1035,6 +1037,48 @@ def run_sweep(args):
         "clocks": clk.summary()}), flush=True)
 
 
+def serving_recall(X, ids, ops, out_ids, k, frac=0.01, seed=1244, dev="cuda"):
+    """(evaluation only) recall@k of a served stream's searches on a seeded 1% sample, against
+    an FP64 brute force over the rows live when each sampled search arrived: the starting rows,
+    plus the inserts and minus the deletes that precede it in the stream.  The server applies
+    updates in groups (within the group wait), so a search may miss the last few milliseconds of
+    updates; that staleness counts against the recall.  Returns (recall, sampled searches)."""
+    import torch
+    from paper_2506_03437_b300.serving import DELETE, INSERT, SEARCH
+    q_ops = np.flatnonzero(ops.kind == SEARCH)
+    g = np.random.default_rng(seed)
+    pick = np.sort(g.choice(q_ops, size=max(1, int(round(frac * q_ops.size))), replace=False))
+    ins = np.flatnonzero(ops.kind == INSERT)
+    rows = np.concatenate([X, ops.vec[ins]]).astype(np.float32)
+    row_ids = np.concatenate([ids, ops.ref[ins]]).astype(np.int64)
+    born = np.concatenate([np.full(X.shape[0], -1, np.int64), ins.astype(np.int64)])   # op that made the row live
+    died = np.full(rows.shape[0], np.iinfo(np.int64).max, np.int64)                      # op that deleted it
+    order = np.argsort(row_ids, kind="stable")
+    dels = np.flatnonzero(ops.kind == DELETE)
+    at = np.clip(np.searchsorted(row_ids[order], ops.ref[dels]), 0, order.size - 1)
+    ok = row_ids[order][at] == ops.ref[dels]          # stream ids are never reused
+    died[order[at[ok]]] = dels[ok]
+    A = torch.from_numpy(rows).to(dev, torch.float64)
+    an = (A * A).sum(1)
+    born_t, died_t = torch.from_numpy(born).to(dev), torch.from_numpy(died).to(dev)
+    ids_t = torch.from_numpy(row_ids).to(dev)
+    hits = 0
+    for c in range(0, pick.size, 64):
+        js = pick[c:c + 64]
+        Qc = torch.from_numpy(ops.vec[js]).to(dev, torch.float64)
+        dist = (Qc * Qc).sum(1, keepdim=True) - 2.0 * (Qc @ A.T) + an[None, :]
+        jt = torch.from_numpy(js.astype(np.int64)).to(dev)[:, None]
+        live = (born_t[None, :] < jt) & (died_t[None, :] > jt)
+        dist = torch.where(live, dist, torch.full_like(dist, float("inf")))
+        gt = ids_t[torch.topk(dist, k, dim=1, largest=False).indices].cpu().numpy()
+        for r, j in enumerate(js):
+            hits += len(set(gt[r].tolist()) & set(out_ids[j].tolist()))
+    del A, an, born_t, died_t, ids_t
+    if dev == "cuda":
+        torch.cuda.empty_cache()
+    return hits / (k * pick.size), int(pick.size)
+
+
 def serve_stream(n_ops, load, server="native", update_wait=0.01, start=2_000_000, maintain_every=100_000,
                  batched_from=0, search_upper=-1):
     """The dynamic skewed stream of the serving workload (start 2M x 128 from 2,000
@@ -1075,7 +1119,10 @@ def serve_stream(n_ops, load, server="native", update_wait=0.01, start=2_000_000
     srv = Srv(ix, D, k=K, recall_target=0.9, max_batch=2048, streams=4, maintain_every=maintain_every,
               maint_args=maint, update_wait_s=update_wait)
     with Clocks(0) as clk:
-        st = srv.run(ops)
+        st = srv.run(ops, keep_results=True)
+    rec, n_s = serving_recall(X, ids, ops, srv.out_ids, K)
+    st["recall_at_10_sample"] = {"value": round(rec, 4), "searches": n_s,
+                                 "against": "FP64 brute force over the rows live at each search's arrival"}
     cfg = {"workload": f"serve_{n0}x{D}_{n_ops}ops", "start_vectors": n0, "ops": n_ops,
            "load": load, "saturation_qps": sat, "arrival_rate_ops": round(rate, 1),
            "update_wait_s": update_wait, "server": server, "maintain_every": maintain_every,
