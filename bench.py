@@ -423,6 +423,13 @@ def run_ours(args):
                                "driver_lag_p99_ms": st["driver_lag_p99_ms"], "clocks": sclk,
                                "note": ("latency from each request's scheduled arrival to its completion, "
                                         "through the library's serving loop (qk_server_*)")}
+            # the same sample at 90% of the saturation (the stream's second load level)
+            st9, scfg9, sclk9 = serve_stream(args.serve_ops, 0.9, args.server, args.update_wait, args.start,
+                                             maintain_every=args.serve_ops)
+            line["serving"]["at_90pct_load"] = {
+                "arrival_rate_ops": scfg9["arrival_rate_ops"], "search_qps": st9["search_qps"],
+                "search": st9["search"], "insert": st9.get("insert"), "delete": st9.get("delete"),
+                "recall_at_10_sample": st9["recall_at_10_sample"], "clocks": sclk9}
             if args.server == "native":   # the same sample with the slots' batched APS plans
                 st2, scfg2, sclk2 = serve_stream(args.serve_ops, args.serve_load, args.server, args.update_wait,
                                                  args.start, maintain_every=args.serve_ops, batched_from=256)
