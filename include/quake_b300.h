@@ -150,8 +150,10 @@ qk_status qk_load(qk_index* index, const float* x, const int64_t* ids, int64_t n
  * kernel ahead of the search kernel, 0 = inside each query's CTA, -1
  * (default) = 1 for d <= 256 (a warp sums 4 rows per step there), else 0.
  * Both give the same candidates and t_i bit for bit, hence the same
- * results; qk_search_scanned's upper-level record and the ratio rule always
- * use 0.  QK_ERR_ARG for another value. */
+ * results; qk_search_scanned's upper-level record, the ratio rule and
+ * batches whose exported candidates would pass 1 GiB (12 bytes per query
+ * and candidate, stream-ordered scratch) always use 0.  QK_ERR_ARG for
+ * another value. */
 qk_status qk_set_search_upper(qk_index* index, int32_t mode);
 
 /*

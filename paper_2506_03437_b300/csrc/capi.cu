@@ -974,8 +974,11 @@ static qk_status search_impl(qk_index* ix, const float* q, int64_t nq, int32_t k
   // search kernel imports its candidates and t_i (1M x 128, 1,000 leaves:
   // 466k -> 494k queries/s).  For longer rows a warp sums one row per step
   // and the CTA's 8 warps walk faster (d = 768: 265k against 139k).
+  // The exported candidates take 12 bytes per (query, candidate): batches
+  // whose export would pass 1 GiB keep the CTA walk.
   void* xs = nullptr;
-  if (a.L == 2 && !a.scan1 && !(a.ratio_eps > 0.f) &&
+  const size_t xs_bytes = (size_t)nq * ((size_t)prepare_mcap(a) * 12 + 4);
+  if (a.L == 2 && !a.scan1 && !(a.ratio_eps > 0.f) && xs_bytes <= (size_t(1) << 30) &&
       (ix->upper_mode == 1 || (ix->upper_mode < 0 && ix->cfg.d <= 256))) {
     SearchArgs pa = a;
     pa.xs_mcap = prepare_mcap(a);
