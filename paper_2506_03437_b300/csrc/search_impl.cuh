@@ -123,6 +123,13 @@ template <int TPR, int NV>
 struct Block {
   static constexpr int D = NV * 4 * TPR;
   static_assert(TPR == row_lanes(D), "the grouped scans follow this kernel's summation order");
+  // The first lane holding row i of a tile step after the reduce-scatter of rpt rows.
+  static __device__ __forceinline__ constexpr int row_judge(int i, int rpt) {
+    int lane = 0, o = TPR / 2;
+    for (int h = rpt / 2; h >= 1; h >>= 1, o >>= 1)
+      if (i & h) lane += o;
+    return lane;
+  }
   static constexpr int ROWS = kThreads / TPR;
   static constexpr int TILE = ROWS * D;
   static constexpr int STAGES = stages_for(TILE);
@@ -445,18 +452,39 @@ struct Block {
           acc[i] = (a01.x + a01.y) + (a23.x + a23.y);
         }
       }
+      // Reduce-scatter over the row group's TPR lanes: the first log2(RPT)
+      // butterfly levels also split the RPT rows between the two lane halves
+      // (a half keeps its rows and receives the partner's partials of them),
+      // the rest are plain butterfly levels.  Every row's total pairs the same
+      // partials in the same order as the full butterfly; row i ends in the
+      // lanes whose bits TPR/2, TPR/4, ... spell i, and the first of them,
+      // row_judge(i), judges it, so each thread raises at most one flag.
+      float red;
+      {
+        float v[RPT];
 #pragma unroll
-      for (int o = TPR / 2; o > 0; o >>= 1)
+        for (int i = 0; i < RPT; ++i) v[i] = acc[i];
+        int o = TPR / 2;
 #pragma unroll
-        for (int i = 0; i < RPT; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-      // every lane of the group now holds every row's distance; lane sub = i
-      // judges row i, so each thread raises at most one survivor flag
+        for (int h = RPT / 2; h >= 1; h >>= 1, o >>= 1) {
+          const bool up = (sub & o) != 0;
+#pragma unroll
+          for (int m = 0; m < h; ++m) {
+            const float send = up ? v[m] : v[m + h];
+            const float keep = up ? v[m + h] : v[m];
+            v[m] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          }
+        }
+#pragma unroll
+        for (; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        red = v[0];
+      }
       bool surv = false;
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
-        if (sub == i) {
+        if (sub == row_judge(i, RPT)) {
           const int rr = r + ROWS * i;
-          float dist = metric == QK_METRIC_L2 ? acc[i] : -acc[i];
+          float dist = metric == QK_METRIC_L2 ? red : -red;
           surv = !tmo && rr < nr && dist <= s->thr;
           if (surv) {
             int pos = atomicAdd(&s->buf_count, 1);
