@@ -175,7 +175,8 @@ def test_batched_plan_with_searches_in_flight(env):
     old = [t.clone() for t in plan.search(Q, 0.9)[:3]]
     torch.cuda.synchronize()
     sa, sb = torch.cuda.Stream(priority=0), torch.cuda.Stream(priority=-1)
-    pre = [plan.outputs(Q) for _ in range(400)]
+    # enough queued batches that some are still waiting when the insert returns
+    pre = [plan.outputs(Q) for _ in range(2000)]
     torch.cuda.synchronize()
     for o in pre:
         plan.search(Q, 0.9, out=o, stream=sa)
