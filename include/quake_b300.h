@@ -598,9 +598,10 @@ qk_status qk_batch_capture(qk_batch* plan, const float* q, int64_t nq, const int
 qk_status qk_batch_replay(qk_batch* plan, void* stream);
 
 /* Times every valid tile shape (queries_per_warp x tile_rows x chunk_rows
- * from {1,2,4} x {16,32,64} x {1024,4096,16384}) on this batch, reps runs
- * each after one warm-up, keeps the fastest in the plan and returns it.
- * Synchronises the stream. */
+ * from {1,2,4} x {16,32,64} x {1024,4096,16384} with rows_per_thread 0, and
+ * the whole-rows layout with each chunk_rows) on this batch, reps runs each
+ * after one warm-up, keeps the fastest in the plan and returns it.  Every
+ * shape gives the same results.  Synchronises the stream. */
 qk_status qk_batch_autotune(qk_batch* plan, const float* q, int64_t nq, const int32_t* nprobe, int64_t* out_ids,
                             float* out_dist, int32_t reps, qk_batch_tiles* chosen, void* stream);
 
@@ -657,10 +658,11 @@ void qk_aps_batch_destroy(qk_aps_batch* plan);
 /* Number of rounds, 1 to 16 (default 4). */
 qk_status qk_aps_batch_set_rounds(qk_aps_batch* plan, int32_t rounds);
 /* Times the tile shapes (queries_per_warp x tile_rows x chunk_rows from
- * {1,2,4} x {16,32,64} x {1024,4096,16384}) that are valid here, reps
- * batches each after one warm-up, keeps the fastest in the plan and returns
- * it.  Every shape sums each row in the per-query kernel's order, so the
- * results do not depend on the choice.  Synchronises the stream. */
+ * {1,2,4} x {16,32,64} x {1024,4096,16384}, each with rows_per_thread 0 and
+ * 2) that are valid here, reps batches each after one warm-up, keeps the
+ * fastest in the plan and returns it.  Every shape sums each row in the
+ * per-query kernel's order, so the results do not depend on the choice.
+ * Synchronises the stream. */
 qk_status qk_aps_batch_autotune(qk_aps_batch* plan, const float* q, int64_t nq, float recall_target,
                                 int64_t* out_ids, float* out_dist, int32_t reps, qk_batch_tiles* chosen,
                                 void* stream);
