@@ -118,7 +118,10 @@ struct qk_server {
   // statistics
   std::atomic<int64_t> n_search{0}, n_insert{0}, n_delete{0}, batches{0}, drains{0};
   double update_s = 0.0, maint_stall_s = 0.0, maint_prepare_s = 0.0;
+  // the first failure: error is written under err_mu before failed is set,
+  // and read under err_mu by the threads that see failed
   std::atomic<int32_t> failed{0};
+  std::mutex err_mu;
   std::string error;
 };
 
@@ -153,9 +156,22 @@ void finish_slot(qk_server* sv, Slot& s) {
   s.busy = false;
 }
 
+// Stops the server with msg unless an earlier failure did.
+void set_failed(qk_server* sv, const std::string& msg) {
+  std::lock_guard<std::mutex> g(sv->err_mu);
+  if (sv->failed.load()) return;
+  sv->error = msg;
+  sv->failed.store(1);
+}
+
+std::string stopped_error(qk_server* sv) {
+  std::lock_guard<std::mutex> g(sv->err_mu);
+  return "the server stopped after an error: " + sv->error;
+}
+
 bool fail(qk_server* sv, qk_status st, const char* what) {
   if (st == QK_OK) return false;
-  if (!sv->failed.exchange(1)) sv->error = std::string(what) + ": " + qk_last_error();
+  set_failed(sv, std::string(what) + ": " + qk_last_error());
   return true;
 }
 
@@ -291,11 +307,14 @@ void scheduler_body(qk_server* sv) {
       sv->preparer.join();
       const auto c0 = Clock::now();
       if (ps == 2) fail(sv, qk_maintain_commit(sv->ix, sv->maint_stream), "maintain_commit");
-      else if (!sv->failed.exchange(1)) sv->error = "maintain_prepare: " + sv->prep_error;
-      ++sv->passes;
+      else set_failed(sv, "maintain_prepare: " + sv->prep_error);
       sv->searched_since = 0;
-      sv->maint_stall_s += secs(c0, Clock::now());
-      sv->maint_prepare_s += secs(prep_t0, c0);
+      {
+        std::lock_guard<std::mutex> g(sv->upd_mu);   // the statistics read them
+        ++sv->passes;
+        sv->maint_stall_s += secs(c0, Clock::now());
+        sv->maint_prepare_s += secs(prep_t0, c0);
+      }
       sv->prep_state.store(0);
     }
     const bool preparing = sv->prep_state.load() == 1;
@@ -341,8 +360,9 @@ void scheduler_body(qk_server* sv) {
         } else {
           const auto c0 = Clock::now();
           fail(sv, qk_maintain(sv->ix, &sv->maint, nullptr, 0, nullptr, sv->update_stream), "maintain");
-          ++sv->passes;
           sv->searched_since = 0;
+          std::lock_guard<std::mutex> g(sv->upd_mu);
+          ++sv->passes;
           sv->maint_stall_s += secs(c0, Clock::now());
         }
       }
@@ -441,7 +461,7 @@ qk_status submit(qk_server* sv, int kind, const float* x, int64_t id, int64_t* t
     return QK_ERR_ARG;
   }
   if (sv->failed.load()) {
-    set_error("the server stopped after an error: " + sv->error);
+    set_error(stopped_error(sv));
     return QK_ERR_STATE;
   }
   if (kind != 2) {
@@ -666,7 +686,7 @@ qk_status qk_server_drain(qk_server* sv, double timeout_s) {
   const auto t0 = Clock::now();
   for (;;) {
     if (sv->failed.load()) {
-      set_error("the server stopped after an error: " + sv->error);
+      set_error(stopped_error(sv));
       return QK_ERR_STATE;
     }
     int64_t n;
@@ -685,7 +705,7 @@ qk_status qk_server_drain(qk_server* sv, double timeout_s) {
       const int64_t req = ++sv->drain_req;
       while (sv->drain_ack.load() < req) {
         if (sv->failed.load()) {
-          set_error("the server stopped after an error: " + sv->error);
+          set_error(stopped_error(sv));
           return QK_ERR_STATE;
         }
         if (timeout_s > 0 && secs(t0, Clock::now()) > timeout_s) {
@@ -716,13 +736,13 @@ qk_status qk_server_get_stats(const qk_server* sv, qk_server_stats* out) {
   out->deletes = sv->n_delete.load();
   out->batches = sv->batches.load();
   out->update_groups = sv->drains.load();
-  out->maintenance_passes = sv->passes;
   {
     std::lock_guard<std::mutex> lk(sv->upd_mu);
+    out->maintenance_passes = sv->passes;
     out->update_s = sv->update_s;
+    out->maintenance_stall_s = sv->maint_stall_s;
+    out->maintenance_prepare_s = sv->maint_prepare_s;
   }
-  out->maintenance_stall_s = sv->maint_stall_s;
-  out->maintenance_prepare_s = sv->maint_prepare_s;
   return QK_OK;
   QK_GUARD_END
 }

@@ -113,7 +113,10 @@ def test_maintain_needs_statistics(I):
 def test_prepare_then_commit_equals_maintain_and_searches_run_meanwhile(I):
     """qk_maintain_prepare + qk_maintain_commit give the index qk_maintain gives.  Between
     them the index still answers from its old partitions, also from another host thread,
-    and a change of the index discards the prepared pass."""
+    and a change of the index discards the prepared pass.  A prepare on a worker thread
+    while this thread searches leaves those searches on the old partitions too; which of
+    them its statistics count depends on when its copy of the counters runs, so that pass
+    is checked for the vectors it keeps, not against qk_maintain."""
     import threading
     from paper_2506_03437_b300 import _lib as L
     X, ids, Q = scenario()
@@ -121,19 +124,32 @@ def test_prepare_then_commit_equals_maintain_and_searches_run_meanwhile(I):
     kw = dict(tau_us=0.01, alpha=0.9, refine_radius=4, s_min=120, split_iters=8, window=600)
     a = make_index(I, X, ids, levels, f_M_leaf=0.25, f_M_parent=1.0, seed=1234)
     b = make_index(I, X, ids, levels, f_M_leaf=0.25, f_M_parent=1.0, seed=1234)
-    for ix in (a, b):
+    c = make_index(I, X, ids, levels, f_M_leaf=0.25, f_M_parent=1.0, seed=1234)
+    for ix in (a, b, c):
         ix.search(Q, 10, recall_target=0.0, nprobe=2)
     before = b.search(Q[:50], 10, recall_target=0.9)
     log_a = a.maintain([0, 1000], [5.0, 55.0], **kw)
-    # the prepare runs on a worker thread while this thread keeps searching
-    out = {}
-    t = threading.Thread(target=lambda: out.update(log=b.maintain_prepare([0, 1000], [5.0, 55.0], **kw)))
+    # prepared here; searched from another host thread and this one until the commit
+    out = {"log": b.maintain_prepare([0, 1000], [5.0, 55.0], **kw)}
+    res = {}
+    t = threading.Thread(target=lambda: res.update(r=[b.search(Q[:50], 10, recall_target=0.9) for _ in range(3)]))
     t.start()
     during = [b.search(Q[:50], 10, recall_target=0.9) for _ in range(3)]
     t.join()
-    for r in during + [b.search(Q[:50], 10, recall_target=0.9)]:   # still the old partitions
+    for r in during + res["r"] + [b.search(Q[:50], 10, recall_target=0.9)]:   # still the old partitions
         assert np.array_equal(r[0], before[0]) and np.array_equal(r[2], before[2])
     b.maintain_commit()
+    # the prepare on a worker thread while this thread keeps searching
+    before_c = c.search(Q[:50], 10, recall_target=0.9)
+    t = threading.Thread(target=lambda: c.maintain_prepare([0, 1000], [5.0, 55.0], **kw))
+    t.start()
+    during = [c.search(Q[:50], 10, recall_target=0.9) for _ in range(3)]
+    t.join()
+    for r in during:
+        assert np.array_equal(r[0], before_c[0]) and np.array_equal(r[2], before_c[2])
+    c.maintain_commit()
+    sc, _, ic = c.export_level(0)
+    assert sorted(ic[:int(sc.sum())].tolist()) == sorted(ids.tolist())
     assert [(x["level"], x["kind"], x["partition"], x["committed"]) for x in out["log"]] == \
            [(x["level"], x["kind"], x["partition"], x["committed"]) for x in log_a]
     for lv in (0, 1):
