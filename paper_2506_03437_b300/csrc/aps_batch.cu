@@ -175,15 +175,17 @@ __device__ int warp_next(const double* p, const uint8_t* fl, int M, uint8_t skip
 // (bd/bi[0, rn), sorted); returns the new size (<= k).  The scans write a
 // query's candidates in blocks of k, one per scanned unit, every entry of a
 // block tagged with its item's position, so only the blocks whose first tag
-// matches are read.
+// matches are read.  tag0: lane j's block j tag (-1 past the blocks), read
+// once per walk instead of once per step.
 __device__ int take_in(float* bd, int64_t* bi, int rn, int k, const float* cd, const int64_t* ci,
-                       const int32_t* cpos, int cn, int pos, int lane) {
+                       const int32_t* cpos, int cn, int pos, int32_t tag0, int lane) {
   int cnt = rn;
   float kd = rn == k ? bd[k - 1] : INFINITY;
   int64_t kid = rn == k ? bi[k - 1] : INT64_MAX;
   const int nb = cn / k;
   for (int b0 = 0; b0 < nb; b0 += 32) {
-    unsigned mb = __ballot_sync(0xffffffffu, b0 + lane < nb && cpos[(b0 + lane) * k] == pos);
+    const int32_t tag = b0 == 0 ? tag0 : (b0 + lane < nb ? cpos[(b0 + lane) * k] : -1);
+    unsigned mb = __ballot_sync(0xffffffffu, b0 + lane < nb && tag == pos);
     while (mb) {
       const int i = (b0 + __ffs(mb) - 1) * k + lane;
       mb &= mb - 1;
@@ -272,6 +274,7 @@ __device__ void replay_query(const ReplayArgs& a, const int64_t q, float* bd, in
   __syncwarp();
   const int64_t co = a.first ? 0 : a.qcoff[q];
   const int cn = a.first ? 0 : a.qcnt[q];
+  const int32_t tag0 = lane < cn / k ? a.cpos[co + (int64_t)lane * k] : -1;
   int taken = 0;
   bool done = false;
   for (;;) {
@@ -284,7 +287,7 @@ __device__ void replay_query(const ReplayArgs& a, const int64_t q, float* bd, in
       break;
     }
     if (!(fl[nx] & kInFlight)) break;   // not scanned this round: ask for it
-    rn = take_in(bd, bi, rn, k, a.cd + co, a.ci + co, a.cpos + co, cn, nx, lane);
+    rn = take_in(bd, bi, rn, k, a.cd + co, a.ci + co, a.cpos + co, cn, nx, tag0, lane);
     if (lane == 0) {
       fl[nx] = kScanned;
       atomicAdd(&a.hits0[cand[nx]], 1ull);
